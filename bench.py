@@ -1,0 +1,380 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: one full Algorithm 1 fit (steps A1-A6) on the
+2000 x 2000 planted-sparse-line workload, through the C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  A step is one fit of a fresh-in-HBM, seeded
+2000 x 2000 float32 matrix (lambda = 0.5): ratio staging, every (jhat, k)
+weighted median, residuals, per-jhat objectives and the argmin.  The metric is
+(jhat, k) weighted-median pairs per second (m (m - 1) pairs per fit); fits/s
+rides along.  L2 is flushed (a 512 MiB write) before every timed step.
+
+Under torchrun each rank fits its own seeded instance on its own GPU (weak
+scaling, no collective on the data path); the job's value is all ranks' pairs
+divided by the slowest rank's time.
+
+--impl reference times the CPU oracle (C, OpenMP over jhat) on the machine's host
+cores, on a bounded sample of the same workload (a subset of the jhat columns,
+all k), in the same unit.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_ROWS, N_COLS, LAMBDA = 2000, 2000, 0.5
+METRIC = "(jhat,k) weighted-median pairs/s (full m^2 scan, Algorithm 1 fit)"
+UNIT = "pairs/s"
+WORKLOAD = ("planted sparse line, n=2000 points x m=2000 coords, float32, 20-sparse unit-l1 "
+            "v*, Laplace(0,0.1) noise, 5% N(0,100 I) outlier rows, lambda=0.5, full m^2 scan")
+# Algorithmic issue count per (pair, row) element: load x_ik, ratio (one
+# multiply by a per-column reciprocal), key, one pivot compare + weight add,
+# residual fma + abs-add.  The ALU roofline divides by the SM issue rate.
+ALG_INSTR_PER_ELEM = 8
+SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("k_pairs.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2402_16712_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _profile_traffic():
+    """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_pairs_paper_size_f32.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m_hash = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    m_bytes = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", txt)
+    if not m_hash or not m_bytes or m_hash.group(1) != _src_hash():
+        return None
+    return float(m_bytes.group(1))
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = f"/tmp/l1line_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(X, lam, target_s=12.0):
+    """The oracle as it stands on the host cores, on a bounded sample: the first
+    J jhat columns (all k), J grown until the run takes a few seconds."""
+    import oracle
+    nth = oracle.max_threads()
+    J = max(1, nth)
+    while True:
+        t0 = time.perf_counter()
+        oracle.fit(X, [lam], jlist=list(range(J)), nthreads=nth, want_all=False)
+        dt = time.perf_counter() - t0
+        if dt >= target_s / 4 or J >= X.shape[1]:
+            break
+        J = min(X.shape[1], int(J * max(2.0, target_s / 4 / max(dt, 1e-3))))
+    m = X.shape[1]
+    pairs = J * (m - 1)
+    return {"value": pairs / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
+            "sample": f"{J} of {m} jhat columns x all {m - 1} k (one lambda), {dt:.2f} s",
+            "seconds": dt, "fits_per_s": (pairs / dt) / (m * (m - 1))}
+
+
+def run_reference(args):
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return 0
+    from paper_2402_16712_gb300 import datagen
+    import oracle
+    X, lams, _ = datagen.paper_size("float32")
+    lam = float(lams[0])
+    nth = oracle.max_threads()
+    m = X.shape[1]
+    # each step: a sample of jhat columns sized to a couple of seconds
+    J = nth
+    t0 = time.perf_counter()
+    oracle.fit(X, [lam], jlist=list(range(J)), nthreads=nth, want_all=False)
+    dt = time.perf_counter() - t0
+    J = max(1, min(m, int(J * 2.0 / max(dt, 1e-3))))
+    for _ in range(args.warmup):
+        oracle.fit(X, [lam], jlist=list(range(J)), nthreads=nth, want_all=False)
+    times = []
+    for s in range(args.steps):
+        cols = [(s * J + q) % m for q in range(J)]
+        t0 = time.perf_counter()
+        oracle.fit(X, [lam], jlist=cols, nthreads=nth, want_all=False)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    value = args.steps * J * (m - 1) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": N_ROWS, "m": N_COLS, "lambda": LAMBDA,
+                   "parallelism": "host cores (OpenMP over jhat)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nth, "kind": "oracle",
+                         "sample": f"each step: {J} of {m} jhat columns x all k"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    l1line.load()
+
+    X, lams, _ = datagen.paper_size("float32", seed=rank)
+    n, m = X.shape
+    pairs = m * (m - 1)
+    stream = torch.cuda.Stream(device=dev)
+    Xd = torch.from_numpy(X).to(dev)
+    ws = l1line.Workspace.for_shape(torch.float32, n, m, 1, dev)
+    out = (torch.empty((1, m), dtype=torch.float32, device=dev),
+           torch.empty(1, dtype=torch.float64, device=dev),
+           torch.empty(1, dtype=torch.int32, device=dev))
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    with torch.cuda.stream(stream):
+        for a, b in ev + kev:  # create the events
+            a.record(stream)
+            b.record(stream)
+        for _ in range(args.warmup):
+            l1line.fit(Xd, lams, workspace=ws, stream=stream, out=out)
+    stream.synchronize()
+    rc = l1line.status(ws, stream)
+    if rc != l1line.OK:
+        raise SystemExit(f"fit failed on the device: {l1line.status_string(rc)}")
+    launches_per_fit = l1line.last_launch_count()
+
+    # ---- timed region: K fits, L2 flushed before each ----------------------
+    clk = Clocks(dev.index)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clk.start()
+    with torch.cuda.stream(stream):
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)
+            l1line.profile_events(*kev[s])
+            ev[s][0].record(stream)
+            l1line.fit(Xd, lams, workspace=ws, stream=stream, out=out)
+            ev[s][1].record(stream)
+    l1line.profile_events()
+    torch.cuda.synchronize(dev)
+    clocks = clk.stop()
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    kern_ms = [a.elapsed_time(b) for a, b in kev]
+    tot_ms = sum(step_ms)
+    rc = l1line.status(ws, stream)
+    if rc != l1line.OK:
+        raise SystemExit(f"fit failed on the device: {l1line.status_string(rc)}")
+    if dist is not None:
+        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    value = world * args.steps * pairs / (tot_ms * 1e-3)
+
+    # ---- float64 input, same workload (reported beside the headline) -------
+    X64 = X.astype(np.float64)
+    Xd64 = torch.from_numpy(X64).to(dev)
+    ws64 = l1line.Workspace.for_shape(torch.float64, n, m, 1, dev)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            l1line.fit(Xd64, lams, workspace=ws64, stream=stream)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k64 = max(2, args.steps // 4)
+        e0.record(stream)
+        for _ in range(k64):
+            l1line.fit(Xd64, lams, workspace=ws64, stream=stream)
+        e1.record(stream)
+    stream.synchronize()
+    ms64 = e0.elapsed_time(e1) / k64
+
+    # ---- end to end through the ABI with host buffers ----------------------
+    Xh = torch.from_numpy(X).pin_memory()
+    vh = torch.empty((1, m), dtype=torch.float32).pin_memory()
+    oh = torch.empty(1, dtype=torch.float64).pin_memory()
+    jh = torch.empty(1, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, args.steps // 2)
+    with torch.cuda.stream(stream):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            Xd.copy_(Xh, non_blocking=True)
+            l1line.fit(Xd, lams, workspace=ws, stream=stream, out=out)
+            vh.copy_(out[0], non_blocking=True)
+            oh.copy_(out[1], non_blocking=True)
+            jh.copy_(out[2], non_blocking=True)
+        e1.record(stream)
+    stream.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    d2h = vh.numel() * 4 + 8 + 4
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    kms = statistics.mean(kern_ms)
+    instr = ALG_INSTR_PER_ELEM * pairs * n
+    peak = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = instr / (kms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "m": m, "lambda": float(lams[0]),
+                   "pairs_per_fit": pairs, "parallelism": f"replicas x{world} (one instance per GPU)",
+                   "l2": "flushed before every timed step (512 MiB write)"},
+        "fits_per_s": world * args.steps / (tot_ms * 1e-3),
+        "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
+                     "frac": achieved / peak, "traffic": _profile_traffic(),
+                     "kernel": "k_pairs<float>", "kernel_ms": kms,
+                     "basis": f"{ALG_INSTR_PER_ELEM} lane-instructions per (pair,row) element; "
+                              f"peak = {SMS} SMs x {LANES_PER_SM_CLK} lanes x {SM_MAX_MHZ:.0f} MHz"},
+        "e2e": {"value": pairs / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches_per_fit * args.steps,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = {k: v for k, v in cpu_baseline(X, float(lams[0])).items()
+                                if k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_profile_case(args):
+    """A plain run of a few fits at a given shape (no timing), for ncu."""
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+    import __graft_entry__
+    __graft_entry__.build()
+    dt = "float32" if args.dtype == "f32" else "float64"
+    X, lams, _ = datagen.paper_size(dt, n=args.n, m=args.m)
+    Xd = torch.from_numpy(X).cuda()
+    ws = l1line.Workspace.for_shape(Xd.dtype, args.n, args.m, 1)
+    for _ in range(args.fits):
+        l1line.fit(Xd, lams, workspace=ws)
+    rc = l1line.status(ws)
+    print(f"profile case n={args.n} m={args.m} {dt}: status={l1line.status_string(rc)}")
+    return 0 if rc == l1line.OK else 1
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="run --fits plain fits of an n x m instance (for ncu), no timing")
+    ap.add_argument("--n", type=int, default=N_ROWS)
+    ap.add_argument("--m", type=int, default=N_COLS)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--fits", type=int, default=2)
+    args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,144 @@
+/*
+ * l1line.h -- C ABI of the GB300 (sm_103a) hot path of the l1-norm
+ * regularised l1-norm best-fit line (Ling & Brooks, arXiv 2402.16712).
+ *
+ * The method (Lemma 1 and Algorithm 1 of the paper): for data points x_i in
+ * R^m (the n rows of X) and a penalty lambda >= 0, every coordinate jhat is
+ * tried as the preserved coordinate with v_jhat = 1; for every other
+ * coordinate k, v_k is the weighted median of the ratios x_ik / x_ijhat
+ * (rows with x_ijhat != 0, weights |x_ijhat|) together with a penalty point at
+ * 0 of weight lambda; the score of jhat is
+ *     z_jhat = sum_i sum_k |x_ik - v_k x_ijhat| + lambda * sum_k |v_k|
+ * and the fit returns the v of the smallest z (smallest jhat on ties).
+ *
+ * Conventions shared by every entry point
+ *  - X is a DEVICE pointer to a row-major n x m matrix (row i = point x_i),
+ *    n >= 1, m >= 1, all entries finite.  Pointers to device memory must be
+ *    aligned to their element size.
+ *  - lambdas is a HOST pointer to n_lambda >= 1 finite values >= 0; the
+ *    values are copied into the launch parameters, so the host array may be
+ *    reused as soon as the call returns.
+ *  - Ratios are IEEE round-to-nearest divisions in the input precision; -0 is
+ *    treated as +0.  The weighted-median decision "the weight at or below t
+ *    exceeds half the total" is taken exactly (no rounding), so v is
+ *    bit-identical to an exact evaluation of the definition.  When the
+ *    minimiser is an interval, v_k is its right end point (Algorithm 1's
+ *    half-open test, last index wins).  A column jhat that is all zero gets
+ *    v = e_jhat (Algorithm 1's initial v_k = 0).
+ *  - Objectives are double; per-pair residuals are accumulated in the input
+ *    precision and combined in double.
+ *  - workspace is a DEVICE buffer owned by the caller, at least
+ *    l1line_workspace_bytes(...) bytes, 256-byte aligned; the library never
+ *    allocates memory.  One workspace must not be used by two calls that run
+ *    concurrently.
+ *  - stream is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *    asynchronous on it.  Argument errors are reported by the return value
+ *    before anything is launched.  Errors found on the device (non-finite
+ *    input, an internal invariant) are recorded in the workspace and read with
+ *    l1line_status(), which synchronises the stream.
+ *  - Return values are l1l_status codes; none of the calls aborts.
+ */
+#ifndef L1LINE_H
+#define L1LINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    L1L_OK = 0,
+    L1L_ERR_ARG = -1,         /* bad argument (null, size, lambda < 0 / NaN / inf) */
+    L1L_ERR_NONFINITE = -2,   /* X holds NaN or inf (reported by l1line_status)   */
+    L1L_ERR_CUDA = -3,        /* a CUDA runtime call failed                        */
+    L1L_ERR_WORKSPACE = -4,   /* workspace missing, too small or misaligned        */
+    L1L_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out                */
+    L1L_ERR_UNSUPPORTED = -6, /* size beyond what the kernels support (see below)  */
+    L1L_ERR_INTERNAL = -7     /* a device-side invariant failed                    */
+} l1l_status;
+
+enum { L1L_DTYPE_F32 = 0, L1L_DTYPE_F64 = 1 };
+
+/* Flags for the *_ex entry points. */
+enum {
+    /* decide every pair with the exact wide-accumulator path instead of the
+       fixed-point fast path (testing aid; same results, much slower) */
+    L1L_FLAG_FORCE_EXACT = 1u << 0
+};
+
+/* Largest n (rows) the shared-memory pair kernels accept, per dtype.  Larger
+ * n, m > 2^31 - 1 or n_lambda > 65535 return L1L_ERR_UNSUPPORTED. */
+int64_t l1line_max_rows(int dtype);
+
+/* Bytes of device workspace needed by l1line_scan_* and l1line_fit_* for the
+ * given shape; 0 on a bad argument.  Includes the per-(lambda, jhat, k) tables
+ * the fit keeps internally. */
+size_t l1line_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t n_lambda);
+
+/*
+ * Steps A1-A5 for every (lambda, jhat, k): the weighted median v^jhat_k
+ * (Lemma 1; Algorithm 1 inner loops) and z_jhat (Algorithm 1, objective line).
+ *   v_all  DEVICE [n_lambda][m][m] in the input dtype: row (t, jhat) is v^jhat
+ *          for lambdas[t], with v^jhat_jhat = 1.  May be NULL.
+ *   s_all  DEVICE [n_lambda][m][m] double: per-pair residual
+ *          sum_i |x_ik - v_k x_ijhat| + lambda |v_k|; the diagonal holds
+ *          lambda (v_jhat = 1, zero residual), so z_jhat is the row sum.
+ *          May be NULL.
+ *   z_all  DEVICE [n_lambda][m] double: z_jhat.  May be NULL.
+ */
+int l1line_scan_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                    int64_t n_lambda, float *v_all, double *s_all, double *z_all,
+                    void *workspace, size_t workspace_bytes, void *stream);
+int l1line_scan_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                    int64_t n_lambda, double *v_all, double *s_all, double *z_all,
+                    void *workspace, size_t workspace_bytes, void *stream);
+/* Same with flags (L1L_FLAG_*). */
+int l1line_scan_ex_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                       int64_t n_lambda, float *v_all, double *s_all, double *z_all,
+                       void *workspace, size_t workspace_bytes, void *stream,
+                       uint32_t flags);
+int l1line_scan_ex_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                       int64_t n_lambda, double *v_all, double *s_all, double *z_all,
+                       void *workspace, size_t workspace_bytes, void *stream,
+                       uint32_t flags);
+
+/*
+ * Algorithm 1 for each lambda (steps A1-A6): the fitted line.
+ *   out_v     DEVICE [n_lambda][m]  v* for lambdas[t] (v*[jhat*] = 1)
+ *   out_obj   DEVICE [n_lambda]     z* = min_jhat z_jhat (double)
+ *   out_jstar DEVICE [n_lambda]     jhat* (0-based; smallest index on ties,
+ *                                   from Algorithm 1's strict "z < z*")
+ */
+int l1line_fit_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                   int64_t n_lambda, float *out_v, double *out_obj, int32_t *out_jstar,
+                   void *workspace, size_t workspace_bytes, void *stream);
+int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                   int64_t n_lambda, double *out_v, double *out_obj, int32_t *out_jstar,
+                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Synchronise `stream` and return the device-side status recorded in the
+ * workspace by the last call that used it (L1L_OK, L1L_ERR_NONFINITE,
+ * L1L_ERR_TIMEOUT or L1L_ERR_INTERNAL), or L1L_ERR_CUDA. */
+int l1line_status(void *workspace, void *stream);
+
+/* Human-readable text of a status code (static storage). */
+const char *l1line_status_string(int status);
+
+/* Number of kernels the most recent scan or fit call launched (for launch
+ * accounting); host-side counter, per calling thread. */
+int l1line_last_launch_count(void);
+
+/* Measurement hook: when both are non-NULL (cudaEvent_t), later scan and fit
+ * calls from this thread record `start` on their stream just before the pair
+ * kernel (steps A2-A4) is launched and `stop` just after it, so the caller can
+ * time that kernel alone with cudaEventElapsedTime.  With more than 256
+ * lambdas the bracket spans every pair-kernel launch and the exact-path
+ * launches between them.  Pass NULLs to switch it off.  Returns L1L_OK. */
+int l1line_profile_events(void *start, void *stop);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* L1LINE_H */

@@ -1,0 +1,250 @@
+// common.cuh -- shared device helpers of the sm_103a hot path.
+//
+// Notation follows the paper (Lemma 1, Algorithm 1): X is n x m with rows the
+// points x_i; jhat is the preserved coordinate, k another coordinate;
+// r_i = x_ik / x_ijhat, w_i = |x_ijhat|, lambda the penalty.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace l1l {
+
+// ---------------------------------------------------------------------------
+// Status bits written to the workspace status word (atomicOr).
+// ---------------------------------------------------------------------------
+enum : uint32_t {
+    ST_NONFINITE = 1u << 0,
+    ST_INTERNAL = 1u << 1,
+    ST_TIMEOUT = 1u << 2,
+};
+
+// ---------------------------------------------------------------------------
+// Order-preserving integer image of a ratio ("key").  -0 maps like +0, so the
+// zero ratio and the penalty point share one key.  Negative values map below
+// KEY0 (the key of 0), positive above.  The all-ones key never arises from a
+// finite or infinite ratio and marks "no element".
+// ---------------------------------------------------------------------------
+template <typename T> struct Traits;
+
+template <> struct Traits<float> {
+    using K = uint32_t;
+    static constexpr K KEY0 = 0x80000000u;
+    static constexpr K NONE = 0xFFFFFFFFu;
+    static constexpr int KEY_BITS = 32;
+    static __device__ __forceinline__ K key(float r) {
+        uint32_t u = __float_as_uint(r);
+        if (u == 0x80000000u) u = 0u;
+        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    }
+    static __device__ __forceinline__ float value(K k) {
+        uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+        return __uint_as_float(u);
+    }
+    static __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+};
+
+template <> struct Traits<double> {
+    using K = uint64_t;
+    static constexpr K KEY0 = 0x8000000000000000ull;
+    static constexpr K NONE = 0xFFFFFFFFFFFFFFFFull;
+    static constexpr int KEY_BITS = 64;
+    static __device__ __forceinline__ K key(double r) {
+        uint64_t u = (uint64_t)__double_as_longlong(r);
+        if (u == 0x8000000000000000ull) u = 0ull;
+        return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
+    }
+    static __device__ __forceinline__ double value(K k) {
+        uint64_t u = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+        return __longlong_as_double((long long)u);
+    }
+    static __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+};
+
+// ---------------------------------------------------------------------------
+// Fixed-point weights.  Per column jhat a scale sigma is chosen so that every
+// weight w_i = |x_ijhat| maps to q_i = floor(w_i * 2^sigma) < 2^(61 - L) with
+// L = ceil(log2(n_valid + 1)); the column total Q = sum q_i then stays below
+// 2^61 and 2*S - Q fits an int64 with room to spare.  A weight whose lowest
+// set bit lies below 2^-sigma loses bits ("inexact"); the column records how
+// many did, and the decision logic widens its certainty margin by that count.
+// ---------------------------------------------------------------------------
+struct ColInfo {
+    int64_t Q;          // sum of q_i over valid rows
+    int32_t sigma;      // scale exponent
+    int32_t n_valid;    // rows with x_ijhat != 0
+    int32_t n_inexact;  // rows whose q_i was truncated
+    int32_t pad;
+};
+
+__device__ __forceinline__ int64_t fixq(float w, int sigma, int &inexact) {
+    uint32_t u = __float_as_uint(w) & 0x7FFFFFFFu;
+    uint32_t be = u >> 23;
+    uint32_t mant = u & 0x7FFFFFu;
+    if (be) mant |= 0x800000u;
+    int s = (be ? (int)be : 1) - 150 + sigma;
+    if (s >= 0) return (int64_t)((uint64_t)mant << s);
+    int rs = -s;
+    if (rs >= 32) {
+        inexact |= (mant != 0);
+        return 0;
+    }
+    inexact |= ((mant & ((1u << rs) - 1u)) != 0);
+    return (int64_t)(mant >> rs);
+}
+
+__device__ __forceinline__ int64_t fixq(double w, int sigma, int &inexact) {
+    uint64_t u = (uint64_t)__double_as_longlong(w) & 0x7FFFFFFFFFFFFFFFull;
+    uint64_t be = u >> 52;
+    uint64_t mant = u & 0xFFFFFFFFFFFFFull;
+    if (be) mant |= 0x10000000000000ull;
+    int s = (be ? (int)be : 1) - 1075 + sigma;
+    if (s >= 0) return (int64_t)(mant << s);
+    int rs = -s;
+    if (rs >= 64) {
+        inexact |= (mant != 0);
+        return 0;
+    }
+    inexact |= ((mant & ((1ull << rs) - 1ull)) != 0);
+    return (int64_t)(mant >> rs);
+}
+
+// floor(log2(w)) for finite w != 0, read off the bit pattern (subnormals
+// included).
+__device__ __forceinline__ int ilog2_pos(float w) {
+    uint32_t u = __float_as_uint(w) & 0x7FFFFFFFu;
+    int be = (int)(u >> 23);
+    if (be) return be - 127;
+    return (31 - __clz((int)u)) - 149;
+}
+__device__ __forceinline__ int ilog2_pos(double w) {
+    uint64_t u = (uint64_t)__double_as_longlong(w) & 0x7FFFFFFFFFFFFFFFull;
+    int be = (int)(u >> 52);
+    if (be) return be - 1023;
+    return (63 - __clzll((long long)u)) - 1074;
+}
+
+// ---------------------------------------------------------------------------
+// Exact decision.  With S = (fixed-point) weight of valid rows whose key is
+// <= t, the test of Lemma 1 "weight at or below t exceeds W/2", W including
+// lambda and the penalty point counted when t >= 0, reads
+//     t <  0:  2 S - Q  >  lambda'        t >= 0:  2 S - Q  >  -lambda'
+// with lambda' = lambda * 2^sigma.  For integer D = 2S - Q this is
+// D > floor(y).  When some weights were truncated (e = n_inexact > 0) the
+// true D lies in (D - e, D + 2e) and the answer is certain only outside that
+// band; otherwise the pair is handed to the exact wide-accumulator path.
+// ---------------------------------------------------------------------------
+struct Decide {
+    int64_t Q;
+    int64_t Lf;  // floor(lambda'), saturated at 2^62
+    int64_t Lc;  // ceil(lambda'),  saturated at 2^62
+    int64_t e;   // n_inexact
+
+    __device__ __forceinline__ void init(const ColInfo &ci, double lambda) {
+        Q = ci.Q;
+        e = ci.n_inexact;
+        const int64_t SAT = (int64_t)1 << 62;
+        if (lambda == 0.0) {
+            Lf = Lc = 0;
+        } else {
+            double lp = ldexp(lambda, ci.sigma);
+            if (!(lp < 4611686018427387904.0)) {
+                Lf = Lc = SAT;
+            } else if (lp < 1.0) {
+                Lf = 0;
+                Lc = 1;
+            } else {
+                Lf = (int64_t)floor(lp);
+                Lc = (int64_t)ceil(lp);
+            }
+        }
+    }
+    // 1 = true, 0 = false, -1 = undecidable at this precision.
+    __device__ __forceinline__ int cond(int64_t S, bool t_nonneg) const {
+        int64_t D = 2 * S - Q;
+        if (e == 0) return t_nonneg ? (D > -Lc) : (D > Lf);
+        if (t_nonneg) {
+            if (D - e >= -Lf) return 1;
+            if (D + 2 * e <= -Lc) return 0;
+        } else {
+            if (D - e >= Lc) return 1;
+            if (D + 2 * e <= Lf) return 0;
+        }
+        return -1;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Warp helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t warp_sum_i64(int64_t x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+__device__ __forceinline__ int warp_sum_i32(int x) { return __reduce_add_sync(0xFFFFFFFFu, x); }
+__device__ __forceinline__ float warp_sum_f32(float x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+__device__ __forceinline__ double warp_sum_f64(double x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+    return x;
+}
+
+// Pair-list entry for the exact slow path.
+struct SlowEntry {
+    int32_t t;  // lambda index
+    int32_t j;  // jhat
+    int32_t k;
+    int32_t inst;  // instance (batched calls), 0 otherwise
+};
+
+// Shapes and device pointers of one scan, passed by value to every kernel.
+template <typename T> struct ScanArgs {
+    const T *Xt;       // [m][ldn] column-major copy of X
+    const ColInfo *ci;  // [m]
+    int64_t n, m, ldn;
+    int32_t n_lambda;
+    T *v_all;          // [n_lambda][m][m]
+    double *s_all;     // [n_lambda][m][m]
+    uint32_t *status;  // workspace status word
+    uint32_t *slow_count;
+    SlowEntry *slow;   // capacity n_lambda * m * m
+    int force_exact;
+};
+
+constexpr int MAX_LAMBDA_PER_LAUNCH = 256;
+struct LambdaPack {
+    double lam[MAX_LAMBDA_PER_LAUNCH];
+};
+
+}  // namespace l1l
+
+namespace l1l {
+
+// ---------------------------------------------------------------------------
+// Per-pair residual of Algorithm 1's objective line, one warp:
+//   sum_i |x_ik - v x_ijhat|   (all rows; rows with x_ijhat = 0 give |x_ik|)
+// computed as |fma(-v, x_ijhat, x_ik)| (one rounding per term) and summed in
+// the input precision with two accumulators per lane, then across the warp.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T warp_residual(const T *__restrict__ xk, const T *xj, int n, T v,
+                                           int lane) {
+    T acc0 = T(0), acc1 = T(0);
+    int i = lane;
+    for (; i + 32 < n; i += 64) {
+        acc0 += fabs(fma(-v, xj[i], xk[i]));
+        acc1 += fabs(fma(-v, xj[i + 32], xk[i + 32]));
+    }
+    if (i < n) acc0 += fabs(fma(-v, xj[i], xk[i]));
+    T s = acc0 + acc1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    return s;
+}
+
+}  // namespace l1l

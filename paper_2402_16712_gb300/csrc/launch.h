@@ -1,0 +1,44 @@
+// launch.h -- host-side launchers of the kernels (internal to the library).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace l1l {
+
+template <typename T>
+cudaError_t launch_prep(const T *X, T *Xt, ColInfo *ci, int64_t n, int64_t m, int64_t ldn,
+                        uint32_t *status, cudaStream_t st, int &launches);
+
+// Shared-memory plan of the pair kernel for a given n; warps == 0 if n is too
+// large for the kernel.
+struct PairPlan {
+    int warps;
+    size_t smem;
+    int kchunk;
+    int kchunks;
+};
+template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms);
+template <typename T> int64_t max_rows_pairs();
+
+// One launch of the pair kernel for lambdas[t0 .. t0+nlc) (nlc <= MAX_LAMBDA_PER_LAUNCH).
+template <typename T>
+cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
+                         const PairPlan &plan, cudaStream_t st, int &launches);
+
+// Exact path for the pairs listed by the preceding pair launch (same chunk).
+template <typename T>
+cudaError_t launch_exact(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
+                         int num_sms, cudaStream_t st, int &launches);
+
+cudaError_t launch_zreduce(const double *s_all, double *z_all, int64_t m, int64_t n_lambda,
+                           cudaStream_t st, int &launches);
+
+template <typename T>
+cudaError_t launch_argmin(const double *z_all, const T *v_all, int64_t m, int64_t n_lambda,
+                          T *out_v, double *out_obj, int32_t *out_jstar, cudaStream_t st,
+                          int &launches);
+
+}  // namespace l1l

@@ -1,0 +1,188 @@
+"""Python binding of the C ABI in ``include/l1line.h`` (argument marshalling only).
+
+Every step of the path runs in the CUDA library ``libl1line.so``; PyTorch only
+supplies device memory (``tensor.data_ptr()``) and streams.  There is no CPU
+fallback: if the library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libl1line.so")
+
+OK, ERR_ARG, ERR_NONFINITE, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_INTERNAL = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+DTYPE_F32, DTYPE_F64 = 0, 1
+FLAG_FORCE_EXACT = 1
+
+# Exported symbols and their ctypes signatures (mirrors include/l1line.h).
+_P, _I64, _U32, _SZ, _I = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t,
+                           ctypes.c_int)
+SIGNATURES = {
+    "l1line_max_rows": (_I64, [_I]),
+    "l1line_workspace_bytes": (_SZ, [_I, _I64, _I64, _I64]),
+    "l1line_scan_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_scan_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_scan_ex_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P, _U32]),
+    "l1line_scan_ex_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P, _U32]),
+    "l1line_fit_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_fit_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_status": (_I, [_P, _P]),
+    "l1line_status_string": (ctypes.c_char_p, [_I]),
+    "l1line_last_launch_count": (_I, []),
+    "l1line_profile_events": (_I, [_P, _P]),
+}
+
+_lib = None
+
+
+class L1LineError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code) if _lib else code} ({code})")
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                f"g.build()\"` (there is no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def status_string(code: int) -> str:
+    return load().l1line_status_string(int(code)).decode()
+
+
+def max_rows(dtype) -> int:
+    return int(load().l1line_max_rows(_dt(dtype)))
+
+
+def workspace_bytes(dtype, n: int, m: int, n_lambda: int) -> int:
+    return int(load().l1line_workspace_bytes(_dt(dtype), n, m, n_lambda))
+
+
+def last_launch_count() -> int:
+    return int(load().l1line_last_launch_count())
+
+
+def _dt(dtype) -> int:
+    import torch
+    if dtype in (torch.float32, np.float32, "float32", DTYPE_F32):
+        return DTYPE_F32
+    if dtype in (torch.float64, np.float64, "float64", DTYPE_F64):
+        return DTYPE_F64
+    raise TypeError(f"unsupported dtype {dtype}")
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_x(X):
+    import torch
+    if not isinstance(X, torch.Tensor) or not X.is_cuda:
+        raise TypeError("X must be a CUDA tensor")
+    if X.dtype not in (torch.float32, torch.float64) or X.dim() != 2 or not X.is_contiguous():
+        raise TypeError("X must be a contiguous 2-D float32/float64 CUDA tensor")
+
+
+def _lams(lambdas) -> np.ndarray:
+    return np.ascontiguousarray(np.atleast_1d(np.asarray(lambdas, dtype=np.float64)))
+
+
+class Workspace:
+    """Caller-owned device workspace (a torch uint8 buffer, 256-byte aligned)."""
+
+    def __init__(self, nbytes: int, device=None):
+        import torch
+        self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        base = self.buf.data_ptr()
+        self.ptr = (base + 255) & ~255
+        self.nbytes = nbytes
+
+    @classmethod
+    def for_shape(cls, dtype, n, m, n_lambda, device=None):
+        nb = workspace_bytes(dtype, n, m, n_lambda)
+        if nb == 0:
+            raise ValueError("bad shape for the workspace")
+        return cls(nb, device)
+
+
+def scan(X, lambdas, workspace: Optional[Workspace] = None, stream=None, flags: int = 0,
+         out=None):
+    """A1-A5: v_all [nl, m, m], s_all [nl, m, m] (double), z_all [nl, m] (double)."""
+    import torch
+    _check_x(X)
+    lam = _lams(lambdas)
+    n, m = X.shape
+    nl = lam.size
+    ws = workspace or Workspace.for_shape(X.dtype, n, m, nl, X.device)
+    if out is None:
+        v_all = torch.empty((nl, m, m), dtype=X.dtype, device=X.device)
+        s_all = torch.empty((nl, m, m), dtype=torch.float64, device=X.device)
+        z_all = torch.empty((nl, m), dtype=torch.float64, device=X.device)
+    else:
+        v_all, s_all, z_all = out
+    f = load().l1line_scan_ex_f32 if X.dtype == torch.float32 else load().l1line_scan_ex_f64
+    rc = f(X.data_ptr(), n, m, lam.ctypes.data_as(ctypes.c_void_p), nl, v_all.data_ptr(),
+           s_all.data_ptr(), z_all.data_ptr(), ctypes.c_void_p(ws.ptr), ws.nbytes,
+           _stream_ptr(stream), flags)
+    if rc != OK:
+        raise L1LineError(rc, "l1line_scan")
+    return v_all, s_all, z_all, ws
+
+
+def fit(X, lambdas, workspace: Optional[Workspace] = None, stream=None, out=None):
+    """Algorithm 1 per lambda: v [nl, m], obj [nl] (double), jstar [nl] (int32)."""
+    import torch
+    _check_x(X)
+    lam = _lams(lambdas)
+    n, m = X.shape
+    nl = lam.size
+    ws = workspace or Workspace.for_shape(X.dtype, n, m, nl, X.device)
+    if out is None:
+        v = torch.empty((nl, m), dtype=X.dtype, device=X.device)
+        obj = torch.empty(nl, dtype=torch.float64, device=X.device)
+        js = torch.empty(nl, dtype=torch.int32, device=X.device)
+    else:
+        v, obj, js = out
+    f = load().l1line_fit_f32 if X.dtype == torch.float32 else load().l1line_fit_f64
+    rc = f(X.data_ptr(), n, m, lam.ctypes.data_as(ctypes.c_void_p), nl, v.data_ptr(),
+           obj.data_ptr(), js.data_ptr(), ctypes.c_void_p(ws.ptr), ws.nbytes,
+           _stream_ptr(stream))
+    if rc != OK:
+        raise L1LineError(rc, "l1line_fit")
+    return v, obj, js, ws
+
+
+def status(ws: Workspace, stream=None) -> int:
+    """Synchronise and return the device-side status of the last call on ws."""
+    return int(load().l1line_status(ctypes.c_void_p(ws.ptr), _stream_ptr(stream)))
+
+
+def profile_events(start=None, stop=None) -> None:
+    """Have later calls record torch.cuda.Event `start`/`stop` around the pair
+    kernel (steps A2-A4) on their stream; call with no arguments to stop."""
+    if start is None or stop is None:
+        load().l1line_profile_events(None, None)
+    else:
+        load().l1line_profile_events(ctypes.c_void_p(start.cuda_event),
+                                     ctypes.c_void_p(stop.cuda_event))

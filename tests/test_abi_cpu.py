@@ -1,0 +1,94 @@
+"""CPU-side checks of the C ABI: the library builds, loads without a GPU,
+exports every function declared in include/l1line.h, and rejects bad
+arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_2402_16712_gb300 import l1line
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    __graft_entry__.build()
+    return l1line.load()
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(l1line_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 10
+    for nm in names:
+        assert hasattr(lib, nm), nm
+        assert nm in l1line.SIGNATURES, f"{nm} has no ctypes signature in the binding"
+
+
+def test_status_strings(lib):
+    for code in range(0, -8, -1):
+        s = l1line.status_string(code)
+        assert s and s != "unknown status"
+    assert l1line.status_string(5) == "unknown status"
+
+
+def test_workspace_and_limits(lib):
+    a = l1line.workspace_bytes(np.float32, 2000, 2000, 1)
+    b = l1line.workspace_bytes(np.float64, 2000, 2000, 1)
+    assert 0 < a < b
+    assert l1line.workspace_bytes(np.float32, 0, 10, 1) == 0
+    assert l1line.workspace_bytes(np.float32, 10, 10, 0) == 0
+    assert l1line.workspace_bytes(np.float32, 1 << 40, 1 << 40, 1) == 0  # overflow caught
+    assert l1line.max_rows(np.float32) >= 5000 and l1line.max_rows(np.float64) >= 5000
+    assert lib.l1line_max_rows(7) == 0
+
+
+def _scan(lib, X=256, n=4, m=3, lam=(0.5,), nl=None, ws=1024, wsb=1 << 30, flags=0):
+    lam = np.asarray(lam, dtype=np.float64)
+    return lib.l1line_scan_ex_f32(X, n, m, lam.ctypes.data_as(ctypes.c_void_p),
+                                  lam.size if nl is None else nl, None, None, None, ws, wsb,
+                                  None, flags)
+
+
+def test_argument_errors_return_before_launch(lib):
+    # pointers here are never dereferenced: validation fails first
+    assert _scan(lib, X=None) == l1line.ERR_ARG
+    assert _scan(lib, n=0) == l1line.ERR_ARG
+    assert _scan(lib, m=0) == l1line.ERR_ARG
+    assert _scan(lib, nl=0) == l1line.ERR_ARG
+    assert _scan(lib, lam=(-1.0,)) == l1line.ERR_ARG
+    assert _scan(lib, lam=(float("nan"),)) == l1line.ERR_ARG
+    assert _scan(lib, lam=(float("inf"),)) == l1line.ERR_ARG
+    assert _scan(lib, X=258) == l1line.ERR_ARG  # misaligned float pointer
+    assert _scan(lib, n=10 ** 7) == l1line.ERR_UNSUPPORTED
+    assert _scan(lib, ws=None) == l1line.ERR_WORKSPACE
+    assert _scan(lib, ws=1024 + 16) == l1line.ERR_WORKSPACE  # not 256-aligned
+    assert _scan(lib, wsb=16) == l1line.ERR_WORKSPACE
+    v = ctypes.c_void_p(512)
+    lam = np.array([0.1])
+    assert lib.l1line_fit_f64(256, 4, 3, lam.ctypes.data_as(ctypes.c_void_p), 1, None, v, v,
+                              1024, 1 << 30, None) == l1line.ERR_ARG
+    assert lib.l1line_status(None, None) == l1line.ERR_WORKSPACE
+
+
+def test_binding_has_no_cpu_fallback(tmp_path):
+    with pytest.raises(RuntimeError):
+        saved = l1line._lib
+        try:
+            l1line._lib = None
+            l1line.load(str(tmp_path / "missing.so"))
+        finally:
+            l1line._lib = saved
