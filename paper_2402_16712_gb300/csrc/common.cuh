@@ -74,8 +74,19 @@ struct ColInfo {
     int32_t sigma;      // scale exponent
     int32_t n_valid;    // rows with x_ijhat != 0
     int32_t n_inexact;  // rows whose q_i was truncated
-    int32_t pad;
+    int32_t flags;      // COL_WIDE: magnitudes outside the approximate-key range
 };
+
+// A column is "wide" when some nonzero |x| lies outside the range in which the
+// reciprocal-multiply approximation of a ratio is within the guard band of
+// the correctly rounded ratio (float: 2^-126 <= |x_ijhat| < 2^126, so 1/x is a
+// normal float; double: 2^-60 <= |x| < 2^60 for both columns of a pair, so
+// every float intermediate stays normal).  Pairs touching such a column take
+// the exact path.
+enum : int32_t { COL_WIDE = 1 };
+template <typename T> struct WideRange;
+template <> struct WideRange<float> { static constexpr int lo = -126, hi = 125; };
+template <> struct WideRange<double> { static constexpr int lo = -60, hi = 59; };
 
 __device__ __forceinline__ int64_t fixq(float w, int sigma, int &inexact) {
     uint32_t u = __float_as_uint(w) & 0x7FFFFFFFu;
@@ -196,10 +207,11 @@ __device__ __forceinline__ double warp_sum_f64(double x) {
 
 // Pair-list entry for the exact slow path.
 struct SlowEntry {
-    int32_t t;  // lambda index
-    int32_t j;  // jhat
+    int32_t t;       // lambda index
+    int32_t j;       // jhat
     int32_t k;
-    int32_t inst;  // instance (batched calls), 0 otherwise
+    int16_t inst;    // instance (batched calls), 0 otherwise
+    int16_t reason;  // why the fast path gave up (SEL_* code), for diagnostics
 };
 
 // Shapes and device pointers of one scan, passed by value to every kernel.
@@ -234,14 +246,17 @@ namespace l1l {
 template <typename T>
 __device__ __forceinline__ T warp_residual(const T *__restrict__ xk, const T *xj, int n, T v,
                                            int lane) {
-    T acc0 = T(0), acc1 = T(0);
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
     int i = lane;
-    for (; i + 32 < n; i += 64) {
-        acc0 += fabs(fma(-v, xj[i], xk[i]));
-        acc1 += fabs(fma(-v, xj[i + 32], xk[i + 32]));
+    for (; i + 96 < n; i += 128) {
+        const T a0 = xk[i], a1 = xk[i + 32], a2 = xk[i + 64], a3 = xk[i + 96];
+        acc0 += fabs(fma(-v, xj[i], a0));
+        acc1 += fabs(fma(-v, xj[i + 32], a1));
+        acc2 += fabs(fma(-v, xj[i + 64], a2));
+        acc3 += fabs(fma(-v, xj[i + 96], a3));
     }
-    if (i < n) acc0 += fabs(fma(-v, xj[i], xk[i]));
-    T s = acc0 + acc1;
+    for (; i < n; i += 32) acc0 += fabs(fma(-v, xj[i], xk[i]));
+    T s = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
     return s;

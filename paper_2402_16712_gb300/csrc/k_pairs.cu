@@ -1,21 +1,39 @@
 // k_pairs.cu -- steps A2-A4 for every (lambda, jhat, k): ratios, exact
 // weighted median (Lemma 1) and per-pair residual (Algorithm 1).
 //
-// Layout: one CTA per (jhat, k-chunk); column jhat (x_ijhat and its
-// fixed-point weights q_i) is staged once in shared memory and shared by the
-// CTA's warps; each warp owns one k at a time.  Per pair the warp
-//   1. forms key_i = key(fl(x_ik / x_ijhat)) for every row (A2) into its
-//      shared-memory key array (the penalty point is implicit, see Decide);
-//   2. per lambda, finds the weighted median by sample-pivot narrowing (A3):
-//      32 candidate keys are sorted across the warp, two pivots bracketing the
-//      estimated crossing are taken, the exact fixed-point weight below and
-//      between them is summed with warp reductions, the side holding the
-//      median is decided exactly and compacted; at <= 31 candidates a final
-//      warp sort + prefix scan picks the smallest key whose cumulative weight
-//      passes half the total;
-//   3. sums the residual |x_ik - v x_ijhat| over all rows (A4).
-// A decision that the truncated fixed-point weights cannot settle sends the
-// pair to the exact wide-accumulator kernel (k_exact.cu).
+// Layout: one CTA per (jhat, k-chunk).  Column jhat is staged once in shared
+// memory -- x_ijhat, its float reciprocal and its fixed-point weight q_i -- and
+// shared by the CTA's warps; each warp owns one k at a time and keeps a short
+// candidate list of its own.
+//
+// Per pair the warp never divides per row.  It orders rows by a COARSE key,
+// the 32-bit order-preserving image of the ratio rounded to float, and
+// approximates it by one multiply, fl(x_ik * fl(1/x_ijhat)) (both rounded to
+// float first for double input).  The approximation is within G keys of the
+// coarse key of the correctly rounded ratio (G = 8 float, 16 double; the bound
+// is derived in the design notes), so a row whose approximate key is more than
+// G away from a pivot is classified exactly without dividing; the few rows
+// inside a guard band, and the final <= 31 candidates, are divided exactly.
+//
+//   level 0  64 sampled rows are keyed and sorted across the warp; two pivots
+//            bracketing the estimated crossing of half the weight are taken;
+//            one pass over all rows sums the exact fixed-point weight below
+//            the lower pivot and compacts the rows between the pivots (guard
+//            bands included) into the candidate list;
+//   resolve  guard-band candidates are divided exactly; the exact weight below
+//            and between the pivots decides whether the median lies between
+//            them (else level 0 repeats on the indicated side);
+//   levels   on the candidate list: sample 32, sort, two pivots, count, decide,
+//            compact, until <= 31 candidates or one coarse key remains;
+//   final    exact keys (double: 64-bit) of the candidates plus the penalty
+//            point's key are sorted across the warp; a prefix scan of the
+//            weights finds the smallest key whose cumulative weight passes
+//            half the total (the test of Lemma 1, decided exactly);
+//   residual sum_i |x_ik - v x_ijhat| over all rows (Algorithm 1, objective).
+//
+// A decision the truncated fixed-point weights cannot settle, a column whose
+// magnitudes fall outside the approximation's range, or a candidate list that
+// cannot be narrowed sends the pair to the exact wide-accumulator kernel.
 #include <algorithm>
 
 #include "common.cuh"
@@ -25,244 +43,490 @@ namespace l1l {
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <typename T> struct PairSmem {
-    using K = typename Traits<T>::K;
-    __host__ __device__ static size_t col_bytes(int64_t npad) { return al16(npad * sizeof(T)) + al16(npad * 8); }
-    __host__ __device__ static size_t warp_bytes(int64_t npad) {
-        return 2 * al16(npad * sizeof(K)) + al16(npad * sizeof(uint16_t));
+__device__ __forceinline__ uint32_t ckey(float r) { return Traits<float>::key(r); }
+// Key of an approximate ratio: -0 is not folded onto +0 (the two keys are
+// adjacent, well inside the guard band), which saves two instructions.
+__device__ __forceinline__ uint32_t akey(float r) {
+    const uint32_t u = __float_as_uint(r);
+    return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
+}
+
+template <typename T> struct Approx;
+template <> struct Approx<float> {
+    static constexpr uint32_t G = 8;
+    static __device__ __forceinline__ float inv_of(float b) { return __frcp_rn(b); }
+    static __device__ __forceinline__ float a32(float a) { return a; }
+    static __device__ __forceinline__ uint32_t exact_ck(float a, float b) {
+        return ckey(__fdiv_rn(a, b));
+    }
+};
+template <> struct Approx<double> {
+    static constexpr uint32_t G = 16;
+    static __device__ __forceinline__ float inv_of(double b) {
+        return __frcp_rn(__double2float_rn(b));
+    }
+    static __device__ __forceinline__ float a32(double a) { return __double2float_rn(a); }
+    static __device__ __forceinline__ uint32_t exact_ck(double a, double b) {
+        return ckey(__double2float_rn(__ddiv_rn(a, b)));
     }
 };
 
-template <typename K>
-__device__ __forceinline__ void warp_sort32(K &key, int64_t &q, int lane) {
+constexpr int NSAMP = 64;   // weight-proportional sample rows per column
+constexpr int NBINS = 128;  // candidate-key histogram bins per warp
+
+template <typename T> struct PairSmem {
+    // per CTA: x_ijhat (T), 1/x_ijhat (float, 0 marks x_ijhat == 0), q_i (int64),
+    // the 64 sample rows (uint16)
+    __host__ __device__ static size_t col_bytes(int64_t npad) {
+        return al16(npad * sizeof(T)) + al16(npad * 4) + al16(npad * 8) + al16(NSAMP * 2);
+    }
+    // per warp: candidate keys (uint32), row indices (uint16; bit 15 = exact key)
+    // and the histogram (uint32)
+    __host__ __device__ static size_t warp_bytes(int64_t cap) {
+        return al16(cap * 4) + al16(cap * 2) + al16(NBINS * 4);
+    }
+};
+
+constexpr uint16_t EXACT_BIT = 0x8000u;
+constexpr uint32_t CK0 = 0x80000000u;      // coarse key of 0
+constexpr uint32_t CKMAX = 0xFFFFFFFEu;    // largest usable coarse key
+constexpr uint32_t CKNONE = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Warp sorts.
+// ---------------------------------------------------------------------------
+template <typename K, typename W>
+__device__ __forceinline__ void warp_sort32(K &key, W &w, int lane) {
 #pragma unroll
     for (int size = 2; size <= 32; size <<= 1) {
 #pragma unroll
         for (int stride = size >> 1; stride > 0; stride >>= 1) {
             K ok = __shfl_xor_sync(0xFFFFFFFFu, key, stride);
-            int64_t oq = __shfl_xor_sync(0xFFFFFFFFu, q, stride);
+            W ow = __shfl_xor_sync(0xFFFFFFFFu, w, stride);
             bool up = (lane & size) == 0 || size == 32;
             bool lower = (lane & stride) == 0;
             bool take = lower == up ? (ok < key) : (ok > key);
             if (take) {
                 key = ok;
-                q = oq;
+                w = ow;
             }
         }
     }
 }
 
-__device__ __forceinline__ int64_t warp_scan_i64(int64_t x, int lane) {
+// 64 keys, element g = e*32 + lane held in slot e; ascending in g.
+__device__ __forceinline__ void warp_sort64(uint32_t (&k)[2], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {  // only in the final merge: ascending
+                const uint32_t lo = min(k[0], k[1]), hi = max(k[0], k[1]);
+                k[0] = lo;
+                k[1] = hi;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t ok = __shfl_xor_sync(0xFFFFFFFFu, k[e], stride);
+                    const int g = e * 32 + lane;
+                    const bool up = (g & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    k[e] = (lower == up) ? min(ok, k[e]) : max(ok, k[e]);
+                }
+            }
+        }
+    }
+}
+
+template <typename V> __device__ __forceinline__ V warp_scan_add(V x, int lane) {
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        int64_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        V y = __shfl_up_sync(0xFFFFFFFFu, x, o);
         if (lane >= o) x += y;
     }
     return x;
 }
 
-enum { SEL_OK = 0, SEL_SLOW = 1, SEL_INTERNAL = 2 };
+// Outcomes of select_v2.  Every code >= SEL_SLOW hands the pair to the exact
+// path; the code says why (kept in the slow list for diagnostics).
+enum {
+    SEL_OK = 0,
+    SEL_INTERNAL = 1,
+    SEL_SLOW = 2,        // column outside the approximate-key range / forced
+    SEL_SLOW_TRIES,      // level 0 kept missing the median
+    SEL_SLOW_CAP,        // too many rows between the closest pivots
+    SEL_SLOW_BAND,       // truncated weights cannot settle a decision
+    SEL_SLOW_LEVELS,     // candidate list did not shrink
+    SEL_SLOW_TIE         // double: one coarse key holds distinct exact keys
+};
 
-// Weighted median over the warp's keys (row-indexed, NONE = row excluded).
+__device__ __forceinline__ uint32_t sat_sub(uint32_t a, uint32_t b) { return a > b ? a - b : 0u; }
+__device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
+    return a < CKNONE - b ? a + b : CKNONE;
+}
+
+// Estimated index (0..ns-1) of the first sorted sample whose scaled cumulative
+// weight passes the crossing target; targets are relative to L.
+// Pivot estimates are float: they only steer the search (every decision that
+// matters is exact, in int64), and this GPU's double pipe is narrow.
+__device__ __forceinline__ float target_for(uint32_t key, float hneg, float hpos) {
+    return key >= CK0 ? hpos : hneg;
+}
+
+// ---------------------------------------------------------------------------
+// Weighted median of one pair.  Returns SEL_* and the exact key in tstar.
+//
+// The candidate list is kept as 32 interleaved per-lane segments: lane l's
+// j-th candidate sits at slot j*32 + l (bank l, so every access is free of bank
+// conflicts) and each lane counts its own candidates against a quota of
+// qt = cap/32 slots.  No ballot or cross-lane compaction is needed; only the
+// final <= 31 candidates are gathered across the warp.
+// ---------------------------------------------------------------------------
 template <typename T>
-__device__ int warp_select(const typename Traits<T>::K *keys, const int64_t *colq,
-                           typename Traits<T>::K *ck, uint16_t *ci, int n, int n_valid,
-                           const Decide &dc, typename Traits<T>::K &tstar, int lane) {
+__device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *inv,
+                         const int64_t *colq, const uint16_t *samp, int qshift, uint32_t *lk,
+                         uint16_t *li, uint32_t *hist, int qt, int n, const Decide &dc,
+                         typename Traits<T>::K &tstar, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
-    const K KEY0 = Tr::KEY0, NONE = Tr::NONE;
+    using A = Approx<T>;
+    constexpr uint32_t G = A::G;
     const unsigned FULL = 0xFFFFFFFFu;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    const int npad_m1 = ((n + 31) & ~31) - 1;
+    const float Qf = (float)dc.Q;
+    const float hneg0 = 0.5f * (Qf + (float)dc.Lf), hpos0 = 0.5f * (Qf - (float)dc.Lc);
 
-    K lo = 0, hi = NONE - 1;  // invariant: the median key lies in [lo, hi]
-    int64_t L = 0;            // exact weight of valid rows with key < lo
-    int64_t Sc = dc.Q;        // weight of the current candidates
-    int c = 0;                // candidate count (when !from_full)
-    bool from_full = true;
-    int d = 3;
+    // ---------------- level 0 -------------------------------------------
+    // 64 rows drawn in proportion to their weight (each stands for Q/64), so the
+    // sorted sample keys estimate the weighted quantiles directly.
+    uint32_t sk[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = samp[e * 32 + lane];
+        sk[e] = akey(__fmul_rn(A::a32(xk[i]), inv[i]));
+    }
+    warp_sort64(sk, lane);
+    int jx;
+    {
+        const float unit = Qf * (1.0f / 64.0f);
+        const bool c0 = (float)(lane + 1) * unit > target_for(sk[0], hneg0, hpos0);
+        const bool c1 = (float)(lane + 33) * unit > target_for(sk[1], hneg0, hpos0);
+        const unsigned m0 = __ballot_sync(FULL, c0), m1 = __ballot_sync(FULL, c1);
+        jx = m0 ? __ffs(m0) - 1 : (m1 ? 32 + __ffs(m1) - 1 : 63);
+    }
+    auto sample_key = [&](int g) -> uint32_t {
+        const uint32_t a0 = __shfl_sync(FULL, sk[0], g & 31);
+        const uint32_t a1 = __shfl_sync(FULL, sk[1], g & 31);
+        return g < 32 ? a0 : a1;
+    };
+    // the median's coarse key is known to lie in [lo0, hi0]; pivots stay inside
+    uint32_t lo0 = 0, hi0 = CKMAX;
+    auto pick = [&](int g, uint32_t dflt) -> uint32_t {
+        uint32_t kk = (g < 0 || g > 63) ? dflt : sample_key(g);
+        if (kk > CKMAX) kk = dflt;
+        return min(max(kk, lo0), hi0);
+    };
+    int d0 = 8;
+    uint32_t P1 = pick(jx - d0, lo0);
+    uint32_t P2 = pick(jx + d0, hi0);
+    if (P1 > P2) P1 = P2;
 
-    for (int level = 0;; ++level) {
-        if (level >= 64) return SEL_SLOW;
-        const int ctot = from_full ? n_valid : c;
-        if (ctot <= 31) {
-            if (from_full) {  // compact every valid row
-                int base = 0;
-                for (int i0 = 0; i0 < n; i0 += 32) {
-                    int i = i0 + lane;
-                    K kk = i < n ? keys[i] : NONE;
-                    bool keep = kk != NONE;
-                    unsigned msk = __ballot_sync(FULL, keep);
-                    if (keep) {
-                        int pos = base + __popc(msk & lt_mask);
-                        ck[pos] = kk;
-                        ci[pos] = (uint16_t)i;
-                    }
-                    base += __popc(msk);
-                }
-                c = base;
-                from_full = false;
-                __syncwarp();
-            }
-            break;
+    int64_t L = 0;   // exact weight of rows with coarse key < lo
+    int64_t Sc = 0;  // weight of the candidates
+    uint32_t lo = 0, hi = CKMAX;
+    int cnt = 0;     // this lane's candidates
+    bool placed = false;
+    for (int attempt = 0; attempt < 8 && !placed; ++attempt) {
+        const uint32_t bt = sat_sub(P1, G);  // certain below: key' < bt
+        const uint32_t at = sat_add(P2, G);  // certain above: key' > at
+        int64_t Sb = 0;
+        cnt = 0;
+        // rows are visited in batches of 4 per lane; the global loads of the next
+        // batch are issued before the current one is classified, so the L2
+        // latency overlaps the work
+        constexpr int U = 4;
+        T an[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = u * 32 + lane;
+            an[u] = i < n ? xk[i] : T(0);
         }
-        // ---- sample 32 candidates, sort them, estimate the crossing --------
-        K sk;
-        int64_t sq;
-        if (from_full) {
-            int i = (int)(((int64_t)lane * n) >> 5);
-            sk = keys[i];
-            sq = sk == NONE ? 0 : colq[i];
-        } else {
-            int p = (int)(((int64_t)lane * c) >> 5);
-            sk = ck[p];
-            sq = colq[ci[p]];
-        }
-        warp_sort32<K>(sk, sq, lane);
-        int64_t P = warp_scan_i64(sq, lane);
-        int64_t P31 = __shfl_sync(FULL, P, 31);
-        double scale = P31 > 0 ? (double)Sc / (double)P31 : 0.0;
-        double est = (double)P * scale;
-        double hneg = 0.5 * ((double)dc.Q + (double)dc.Lf) - (double)L;
-        double hpos = 0.5 * ((double)dc.Q - (double)dc.Lc) - (double)L;
-        bool crossed = sk != NONE && est > (sk >= KEY0 ? hpos : hneg);
-        unsigned cm_ = __ballot_sync(FULL, crossed);
-        int jx = cm_ ? __ffs(cm_) - 1 : 31;
-        K p1 = __shfl_sync(FULL, sk, max(jx - d, 0));
-        K p2 = __shfl_sync(FULL, sk, min(jx + d, 31));
-        if (p1 == NONE) p1 = hi;
-        if (p2 == NONE) p2 = hi;
-        p1 = p1 < lo ? lo : (p1 > hi ? hi : p1);
-        p2 = p2 < lo ? lo : (p2 > hi ? hi : p2);
-        if (p1 > p2) p1 = p2;
-
-        // ---- exact weight below p1 and within [p1, p2] ---------------------
-        int64_t Sb = 0, Sm = 0;
-        int cb = 0, cmid = 0;
-        if (from_full) {
-            for (int i = lane; i < n; i += 32) {
-                K kk = keys[i];
-                if (kk == NONE) continue;
-                int64_t q = colq[i];
-                if (kk < p1) {
-                    Sb += q;
-                    cb++;
-                } else if (kk <= p2) {
-                    Sm += q;
-                    cmid++;
+        for (int i0 = 0; i0 < n; i0 += 32 * U) {
+            T ac[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) ac[u] = an[u];
+            if (i0 + 32 * U < n) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + 32 * U + u * 32 + lane;
+                    an[u] = i < n ? xk[i] : T(0);
                 }
             }
-        } else {
-            for (int p = lane; p < c; p += 32) {
-                K kk = ck[p];
-                int64_t q = colq[ci[p]];
-                if (kk < p1) {
-                    Sb += q;
-                    cb++;
-                } else if (kk <= p2) {
-                    Sm += q;
-                    cmid++;
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                // branch-free; rows past n are clamped to a readable slot and masked
+                const int i = i0 + u * 32 + lane;
+                const int ic = min(i, npad_m1);
+                const float iv = inv[ic];
+                const uint32_t kk = akey(__fmul_rn(A::a32(ac[u]), iv));
+                const bool valid = i < n && iv != 0.0f;
+                const bool below = valid && kk < bt;
+                const bool cand = valid && !below && kk <= at;
+                const int64_t q = colq[ic];
+                Sb += below ? q : 0;
+                // speculative store: the slot is only kept when cnt advances
+                if (cnt < qt) {
+                    lk[cnt * 32 + lane] = kk;
+                    li[cnt * 32 + lane] = (uint16_t)ic;
                 }
+                cnt += cand ? 1 : 0;
             }
         }
         Sb = warp_sum_i64(Sb);
+        __syncwarp();
+        if (__any_sync(FULL, cnt > qt)) {  // a lane overflowed: pull the pivots closer
+            if (d0 == 0) return SEL_SLOW_CAP;
+            d0 >>= 1;
+            P1 = pick(jx - d0, lo0);
+            P2 = pick(jx + d0, hi0);
+            if (P1 > P2) P1 = P2;
+            continue;
+        }
+        // resolve the guard bands exactly; weight below P1 and within [P1, P2]
+        const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
+        int64_t Sb2 = 0, Sm = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            uint32_t kk = lk[p];
+            const uint16_t id = li[p];
+            if (kk < g1 || kk > g2) {
+                kk = A::exact_ck(xk[id], colb[id]);
+                lk[p] = kk;
+                li[p] = id | EXACT_BIT;
+            }
+            const int64_t q = colq[id];
+            Sb2 += kk < P1 ? q : 0;
+            Sm += (kk >= P1 && kk <= P2) ? q : 0;
+        }
+        Sb = Sb + warp_sum_i64(Sb2);
         Sm = warp_sum_i64(Sm);
-        cb = warp_sum_i32(cb);
-        cmid = warp_sum_i32(cmid);
-
-        // ---- decide which part holds the median (exact) --------------------
-        int part, newc;
-        int r1 = (p1 == lo) ? 0 : dc.cond(L + Sb, (K)(p1 - 1) >= KEY0);
-        if (r1 < 0) return SEL_SLOW;
-        if (r1 == 1) {
-            part = 0;
-            hi = p1 - 1;
-            Sc = Sb;
-            newc = cb;
-        } else {
-            int r2 = dc.cond(L + Sb + Sm, p2 >= KEY0);
-            if (r2 < 0) return SEL_SLOW;
-            if (r2 == 1) {
-                part = 1;
-                lo = p1;
-                hi = p2;
-                L += Sb;
-                Sc = Sm;
-                newc = cmid;
-            } else {
-                if (p2 == hi) return SEL_INTERNAL;
-                part = 2;
-                lo = p2 + 1;
-                L += Sb + Sm;
-                Sc = Sc - Sb - Sm;
-                newc = ctot - cb - cmid;
-            }
+        __syncwarp();
+        const int r1 = P1 == lo0 ? 0 : dc.cond(Sb, (P1 - 1) >= CK0);
+        if (r1 < 0) return SEL_SLOW_BAND;
+        if (r1 == 1) {  // median below P1: retry under P1
+            hi0 = P1 - 1;
+            P2 = hi0;
+            P1 = pick(jx - 3 * max(d0, 1) - 1, lo0);
+            if (P1 > P2) P1 = lo0;
+            continue;
         }
-        if (lo == hi) {
-            tstar = lo;
-            return SEL_OK;
+        const int r2 = dc.cond(Sb + Sm, P2 >= CK0);
+        if (r2 < 0) return SEL_SLOW_BAND;
+        if (r2 == 0) {  // median above P2: retry over P2
+            if (P2 >= hi0) return SEL_INTERNAL;
+            lo0 = P2 + 1;
+            P1 = lo0;
+            P2 = pick(jx + 3 * max(d0, 1) + 1, hi0);
+            if (P2 < P1) P2 = hi0;
+            continue;
         }
-        d = (newc == ctot) ? 0 : 3;
-
-        // ---- compact the chosen part (stable; in place on the candidates) --
-        int base = 0;
-        const int lim = from_full ? n : c;
-        for (int p0 = 0; p0 < lim; p0 += 32) {
-            int p = p0 + lane;
-            K kk = NONE;
-            uint16_t idx = 0;
-            if (p < lim) {
-                if (from_full) {
-                    kk = keys[p];
-                    idx = (uint16_t)p;
-                } else {
-                    kk = ck[p];
-                    idx = ci[p];
-                }
-            }
-            bool keep = kk != NONE &&
-                        (part == 0 ? kk < p1 : (part == 1 ? (kk >= p1 && kk <= p2) : kk > p2));
-            unsigned msk = __ballot_sync(FULL, keep);
-            if (keep) {
-                int pos = base + __popc(msk & lt_mask);
-                ck[pos] = kk;
-                ci[pos] = idx;
-            }
-            base += __popc(msk);
+        // median in [P1, P2]: keep those candidates (lane-local, in place)
+        int w = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            const uint32_t kk = lk[p];
+            const uint16_t id = li[p];
+            lk[w * 32 + lane] = kk;  // w <= j: kept only if w advances
+            li[w * 32 + lane] = id;
+            w += (kk >= P1 && kk <= P2) ? 1 : 0;
         }
         __syncwarp();
-        c = base;
-        from_full = false;
+        cnt = w;
+        L = Sb;
+        Sc = Sm;
+        lo = P1;
+        hi = P2;
+        placed = true;
+    }
+    if (!placed) return SEL_SLOW_TRIES;
+
+    // ---------------- levels on the candidate list -------------------------
+    int c = __reduce_add_sync(FULL, cnt);
+    for (int level = 0; c > 31 && lo < hi; ++level) {
+        if (level >= 40) return SEL_SLOW_LEVELS;
+        // weight histogram of the candidates' keys over <= 128 bins of [lo, hi]
+        const uint32_t span = hi - lo;
+        const int shift = span >= 128u ? (32 - __clz((int)span)) - 7 : 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) hist[lane * 4 + q] = 0u;
+        __syncwarp();
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            const uint32_t kk = min(max(lk[p], lo), hi);
+            atomicAdd(&hist[(kk - lo) >> shift], (uint32_t)(colq[li[p] & 0x7FFF] >> qshift));
+        }
+        __syncwarp();
+        uint32_t hb[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) hb[q] = hist[lane * 4 + q];
+        __syncwarp();
+        const uint32_t lsum = hb[0] + hb[1] + hb[2] + hb[3];
+        const uint32_t incl = warp_scan_add(lsum, lane);
+        const uint32_t htot = __shfl_sync(FULL, incl, 31);
+        const float scale = htot > 0 ? __fdividef((float)Sc, (float)htot) : 0.0f;
+        // targets relative to L, formed exactly in int64 before rounding to float
+        const float hneg_r = 0.5f * (float)(dc.Q + dc.Lf - 2 * L);
+        const float hpos_r = 0.5f * (float)(dc.Q - dc.Lc - 2 * L);
+        const uint32_t run = incl - lsum;
+        int bsel = 4;
+#pragma unroll
+        for (int q = 3; q >= 0; --q) {
+            const uint32_t before = run + (q > 0 ? hb[0] : 0u) + (q > 1 ? hb[1] : 0u) +
+                                    (q > 2 ? hb[2] : 0u);
+            const uint32_t bin = (uint32_t)(lane * 4 + q);
+            const uint64_t bhi64 = (uint64_t)lo + ((uint64_t)(bin + 1) << shift) - 1;
+            const uint32_t bhi = bhi64 > hi ? hi : (uint32_t)bhi64;
+            const uint32_t blo = lo + (bin << shift);
+            const float cum = (float)(before + hb[q]) * scale;
+            // an empty bin can hold the median only through the penalty point at 0
+            const bool eligible =
+                hb[q] != 0u || (bin <= (span >> shift) && blo <= CK0 && CK0 <= bhi);
+            if (eligible && cum > target_for(bhi, hneg_r, hpos_r)) bsel = q;
+        }
+        const unsigned cmask = __ballot_sync(FULL, bsel < 4);
+        int b_star;
+        if (cmask) {
+            const int ln = __ffs(cmask) - 1;
+            b_star = ln * 4 + __shfl_sync(FULL, bsel, ln);
+        } else {
+            b_star = (int)(span >> shift);
+        }
+        uint32_t Q1 = lo + ((uint32_t)b_star << shift);
+        const uint64_t q2_64 = (uint64_t)lo + ((uint64_t)(b_star + 1) << shift) - 1;
+        uint32_t Q2 = q2_64 > hi ? hi : (uint32_t)q2_64;
+        if (Q1 > hi) Q1 = hi;
+        const uint32_t bt = sat_sub(Q1, G), g1 = sat_add(Q1, G);
+        const uint32_t g2 = sat_sub(Q2, G), at = sat_add(Q2, G);
+        int64_t Sb = 0, Sm = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            uint32_t kk = lk[p];
+            uint16_t id = li[p];
+            if (!(id & EXACT_BIT) && ((kk >= bt && kk < g1) || (kk > g2 && kk <= at))) {
+                kk = A::exact_ck(xk[id], colb[id]);
+                lk[p] = kk;
+                id = id | EXACT_BIT;
+                li[p] = id;
+            }
+            const int64_t q = colq[id & 0x7FFF];
+            Sb += kk < Q1 ? q : 0;
+            Sm += (kk >= Q1 && kk <= Q2) ? q : 0;
+        }
+        Sb = warp_sum_i64(Sb);
+        Sm = warp_sum_i64(Sm);
+        __syncwarp();
+        int part;
+        const int r1 = (Q1 == lo) ? 0 : dc.cond(L + Sb, (Q1 - 1) >= CK0);
+        if (r1 < 0) return SEL_SLOW_BAND;
+        if (r1 == 1) {
+            part = 0;
+            hi = Q1 - 1;
+            Sc = Sb;
+        } else {
+            const int r2 = dc.cond(L + Sb + Sm, Q2 >= CK0);
+            if (r2 < 0) return SEL_SLOW_BAND;
+            if (r2 == 1) {
+                part = 1;
+                lo = Q1;
+                hi = Q2;
+                L += Sb;
+                Sc = Sm;
+            } else {
+                if (Q2 >= hi) return SEL_INTERNAL;
+                part = 2;
+                lo = Q2 + 1;
+                L += Sb + Sm;
+                Sc = Sc - Sb - Sm;
+            }
+        }
+        int w = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            const uint32_t kk = lk[p];
+            const uint16_t id = li[p];
+            const bool keep =
+                part == 0 ? kk < Q1 : (part == 1 ? (kk >= Q1 && kk <= Q2) : kk > Q2);
+            lk[w * 32 + lane] = kk;  // w <= j: kept only if w advances
+            li[w * 32 + lane] = id;
+            w += keep ? 1 : 0;
+        }
+        __syncwarp();
+        cnt = w;
+        c = __reduce_add_sync(FULL, cnt);
     }
 
-    // ---- final: <= 31 candidates (+ the penalty point's key if in range) ---
-    K fk = NONE;
+    // ---------------- final: exact keys of the candidates ------------------
+    if (sizeof(T) == 4 && lo == hi) {  // coarse keys are the exact keys for float
+        tstar = (K)lo;
+        return SEL_OK;
+    }
+    if (c > 31) {  // one coarse key left, many rows: all exact keys equal?
+        K kmin = Tr::NONE, kmax = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int row = li[j * 32 + lane] & 0x7FFF;
+            const K ke = Tr::key(Tr::div_rn(xk[row], colb[row]));
+            kmin = min(kmin, ke);
+            kmax = max(kmax, ke);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+        }
+        const bool zero_in = lo <= CK0 && CK0 <= hi;
+        if (kmin == kmax && !(zero_in && kmin != Tr::KEY0)) {
+            tstar = kmin;
+            return SEL_OK;
+        }
+        return SEL_SLOW_TIE;
+    }
+    // gather the <= 31 candidate rows into lanes 0..c-1 (via the histogram buffer)
+    {
+        const int excl = warp_scan_add(cnt, lane) - cnt;
+        uint16_t *stage = reinterpret_cast<uint16_t *>(hist);
+        for (int j = 0; j < cnt; ++j) stage[excl + j] = li[j * 32 + lane] & 0x7FFF;
+    }
+    __syncwarp();
+    K fk = Tr::NONE;
     int64_t fq = 0;
     if (lane < c) {
-        fk = ck[lane];
-        fq = colq[ci[lane]];
-    } else if (lane == c && lo <= KEY0 && KEY0 <= hi) {
-        fk = KEY0;
+        const int row = reinterpret_cast<const uint16_t *>(hist)[lane];
+        fk = Tr::key(Tr::div_rn(xk[row], colb[row]));
+        fq = colq[row];
+    } else if (lane == c && lo <= CK0 && CK0 <= hi) {
+        fk = Tr::KEY0;
         fq = 0;
     }
-    warp_sort32<K>(fk, fq, lane);
-    int64_t P = warp_scan_i64(fq, lane);
-    K nxt = __shfl_down_sync(FULL, fk, 1);
-    bool last = (lane == 31) || (nxt != fk);
+    __syncwarp();
+    warp_sort32(fk, fq, lane);
+    const int64_t P = warp_scan_add(fq, lane);
+    const K nxt = __shfl_down_sync(FULL, fk, 1);
+    const bool last = (lane == 31) || (nxt != fk);
     int r = -2;
-    if (last && fk != NONE) r = dc.cond(L + P, fk >= KEY0);
-    unsigned okm = __ballot_sync(FULL, r == 1);
-    unsigned unm = __ballot_sync(FULL, r == -1);
-    unsigned any = okm | unm;
+    if (last && fk != Tr::NONE) r = dc.cond(L + P, fk >= Tr::KEY0);
+    const unsigned okm = __ballot_sync(FULL, r == 1);
+    const unsigned unm = __ballot_sync(FULL, r == -1);
+    const unsigned any = okm | unm;
     if (!any) return SEL_INTERNAL;
-    int first = __ffs(any) - 1;
-    if ((unm >> first) & 1u) return SEL_SLOW;
+    const int first = __ffs(any) - 1;
+    if ((unm >> first) & 1u) return SEL_SLOW_BAND;
     tstar = __shfl_sync(FULL, fk, first);
     return SEL_OK;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_pairs(ScanArgs<T> a, LambdaPack lp, int t0, int nlc,
-                                               int kchunk) {
+__global__ void __launch_bounds__(256, 3) k_pairs(ScanArgs<T> a, LambdaPack lp, int t0, int nlc,
+                                               int kchunk, int cap) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -272,24 +536,66 @@ __global__ void __launch_bounds__(256) k_pairs(ScanArgs<T> a, LambdaPack lp, int
     const int j = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
-    T *colx = reinterpret_cast<T *>(smem);
-    int64_t *colq = reinterpret_cast<int64_t *>(smem + al16((size_t)npad * sizeof(T)));
-    unsigned char *wbase = smem + PairSmem<T>::col_bytes(npad) +
-                           (size_t)warp * PairSmem<T>::warp_bytes(npad);
-    K *keys = reinterpret_cast<K *>(wbase);
-    K *ck = reinterpret_cast<K *>(wbase + al16((size_t)npad * sizeof(K)));
-    uint16_t *ci = reinterpret_cast<uint16_t *>(wbase + 2 * al16((size_t)npad * sizeof(K)));
+    T *colb = reinterpret_cast<T *>(smem);
+    size_t off = al16((size_t)npad * sizeof(T));
+    float *inv = reinterpret_cast<float *>(smem + off);
+    off += al16((size_t)npad * 4);
+    int64_t *colq = reinterpret_cast<int64_t *>(smem + off);
+    off += al16((size_t)npad * 8);
+    uint16_t *samp = reinterpret_cast<uint16_t *>(smem + off);
+    unsigned char *wbase =
+        smem + PairSmem<T>::col_bytes(npad) + (size_t)warp * PairSmem<T>::warp_bytes(cap);
+    uint32_t *lk = reinterpret_cast<uint32_t *>(wbase);
+    uint16_t *li = reinterpret_cast<uint16_t *>(wbase + al16((size_t)cap * 4));
+    uint32_t *hist = reinterpret_cast<uint32_t *>(wbase + al16((size_t)cap * 4) +
+                                                  al16((size_t)cap * 2));
+    // prologue scratch: the first 256 bytes of warp 0's candidate list
+    long long *s_wsum = reinterpret_cast<long long *>(smem + PairSmem<T>::col_bytes(npad));
 
     const ColInfo cinfo = a.ci[j];
     const T *xj = a.Xt + (int64_t)j * ldn;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        T b = xj[i];
-        colx[i] = b;
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+        const T b = i < n ? xj[i] : T(0);
+        colb[i] = b;
+        inv[i] = b != T(0) ? Approx<T>::inv_of(b) : 0.0f;
         int e = 0;
         colq[i] = b != T(0) ? fixq(b < T(0) ? -b : b, cinfo.sigma, e) : 0;
     }
+    for (int q = threadIdx.x; q < NSAMP; q += blockDim.x) samp[q] = 0;  // always a valid row
+    __syncthreads();
+    // Systematic weight-proportional sample of the rows of column jhat: sample
+    // s is the row whose cumulative weight interval contains (s + 1/2) Q / 64.
+    if (cinfo.n_valid > 0) {
+        const int nt = blockDim.x;
+        const int chunk = (n + nt - 1) / nt;
+        const int r0 = min(n, threadIdx.x * chunk), r1 = min(n, r0 + chunk);
+        long long mine = 0;
+        for (int r = r0; r < r1; ++r) mine += colq[r];
+        long long incl = warp_scan_add(mine, lane);
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        long long before = incl - mine;
+        for (int w = 0; w < warp; ++w) before += s_wsum[w];
+        const double per = (double)NSAMP / (double)cinfo.Q;
+        for (int r = r0; r < r1; ++r) {
+            const long long after = before + colq[r];
+            const double x0 = (double)before * per - 0.5, x1 = (double)after * per - 0.5;
+            int s0 = (int)floor(x0) + 1, s1 = (int)floor(x1);
+            s0 = max(s0, 0);
+            s1 = min(s1, NSAMP - 1);
+            for (int sidx = s0; sidx <= s1; ++sidx) samp[sidx] = (uint16_t)r;
+            before = after;
+        }
+        __syncthreads();
+    }
+    const int qshift = max(0, 45 - (cinfo.n_valid > 0 ? 32 - __clz(cinfo.n_valid) : 0));
+    // per-lambda thresholds of the exact test depend on (jhat, lambda) only
+    constexpr int NDEC = 16;
+    __shared__ Decide s_dec[NDEC];
+    for (int tl = threadIdx.x; tl < min(nlc, NDEC); tl += blockDim.x) s_dec[tl].init(cinfo, lp.lam[tl]);
     __syncthreads();
 
+    const bool jwide = (cinfo.flags & COL_WIDE) != 0;
     const int64_t k0 = (int64_t)blockIdx.y * kchunk;
     const int64_t k1 = min(m, k0 + kchunk);
     for (int64_t k = k0 + warp; k < k1; k += nw) {
@@ -302,27 +608,26 @@ __global__ void __launch_bounds__(256) k_pairs(ScanArgs<T> a, LambdaPack lp, int
             continue;
         }
         const T *xk = a.Xt + k * ldn;
-        if (cinfo.n_valid > 0 && !a.force_exact) {
-            for (int i = lane; i < n; i += 32) {
-                T b = colx[i];
-                keys[i] = b != T(0) ? Tr::key(Tr::div_rn(xk[i], b)) : Tr::NONE;
-            }
-            __syncwarp();
-        }
+        const bool slow_pair = a.force_exact || jwide ||
+                               (sizeof(T) == 8 && (a.ci[k].flags & COL_WIDE));
         for (int tl = 0; tl < nlc; ++tl) {
             const int t = t0 + tl;
             const double lam = lp.lam[tl];
             const int64_t o = ((int64_t)t * m + j) * m + k;
             K ts = Tr::KEY0;
             int st = SEL_OK;
-            if (a.force_exact) {
+            if (slow_pair) {
                 st = SEL_SLOW;
             } else if (cinfo.n_valid > 0) {
                 Decide dc;
-                dc.init(cinfo, lam);
-                st = warp_select<T>(keys, colq, ck, ci, n, cinfo.n_valid, dc, ts, lane);
+                if (tl < NDEC)
+                    dc = s_dec[tl];
+                else
+                    dc.init(cinfo, lam);
+                st = select_v2<T>(xk, colb, inv, colq, samp, qshift, lk, li, hist, cap / 32, n,
+                                  dc, ts, lane);
             }
-            if (st == SEL_SLOW) {
+            if (st >= SEL_SLOW) {
                 if (lane == 0) {
                     uint32_t slot = atomicAdd(a.slow_count, 1u);
                     SlowEntry e;
@@ -330,6 +635,7 @@ __global__ void __launch_bounds__(256) k_pairs(ScanArgs<T> a, LambdaPack lp, int
                     e.j = j;
                     e.k = (int32_t)k;
                     e.inst = 0;
+                    e.reason = (int16_t)st;
                     a.slow[slot] = e;
                 }
                 continue;
@@ -343,7 +649,7 @@ __global__ void __launch_bounds__(256) k_pairs(ScanArgs<T> a, LambdaPack lp, int
                 continue;
             }
             const T v = Tr::value(ts);
-            const T res = warp_residual<T>(xk, colx, n, v, lane);
+            const T res = warp_residual<T>(xk, colb, n, v, lane);
             if (lane == 0) {
                 a.v_all[o] = v;
                 a.s_all[o] = (double)res + lam * (double)fabs(v);
@@ -353,40 +659,51 @@ __global__ void __launch_bounds__(256) k_pairs(ScanArgs<T> a, LambdaPack lp, int
     }
 }
 
+// Candidate slots per warp (a multiple of 32: 32 lanes x quota).  About 40% of
+// the rows, at least 512 (small n: every row fits).
+template <typename T> static int cap_for(int64_t npad) {
+    int64_t c = std::max<int64_t>(512, (npad * 2 / 5 + 31) & ~int64_t(31));
+    return (int)(std::min<int64_t>(npad, c) & ~int64_t(31));
+}
+
 template <typename T> int64_t max_rows_pairs() {
-    // one warp must fit: column (T + int64) + one warp's arrays
     const size_t budget = 227 * 1024;
     int64_t n = 32;
-    while (PairSmem<T>::col_bytes(n + 32) + PairSmem<T>::warp_bytes(n + 32) <= budget &&
-           n + 32 <= 65535)
+    while (n + 32 <= 32767 &&
+           PairSmem<T>::col_bytes(n + 32) + PairSmem<T>::warp_bytes(cap_for<T>(n + 32)) <= budget)
         n += 32;
     return n;
 }
 
 template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms) {
-    PairPlan p{0, 0, 0, 0};
+    PairPlan p{0, 0, 0, 0, 0};
     const int64_t npad = (n + 31) & ~int64_t(31);
     if (n > max_rows_pairs<T>()) return p;
-    const size_t cb = PairSmem<T>::col_bytes(npad), wb = PairSmem<T>::warp_bytes(npad);
-    // prefer two CTAs per SM (<= ~113 KB each) with as many warps as fit, up to 8
+    int cap = cap_for<T>(npad);
+    const size_t cb = PairSmem<T>::col_bytes(npad);
+    // 8 warps per CTA; the register budget allows three such CTAs per SM, so
+    // shrink the candidate lists (not below 256 slots) to fit three in shared
+    // memory (228 KB per SM, 1 KB reserved per CTA, static arrays included)
+    {
+        const int64_t per_cta = 233472 / 3 - 1024 - 1024;
+        const int64_t fit = ((per_cta - (int64_t)cb) / 8 - NBINS * 4) / 6;
+        const int64_t fit32 = fit & ~int64_t(31);
+        if (fit32 >= std::min<int64_t>(npad, 256)) cap = (int)std::min<int64_t>(cap, fit32);
+    }
+    const size_t wb = PairSmem<T>::warp_bytes(cap);
     int w = 0;
     for (int cand = 8; cand >= 1; --cand)
-        if (cb + cand * wb <= 113 * 1024) {
+        if (cb + cand * wb <= 227 * 1024) {
             w = cand;
             break;
         }
-    if (w == 0)
-        for (int cand = 8; cand >= 1; --cand)
-            if (cb + cand * wb <= 227 * 1024) {
-                w = cand;
-                break;
-            }
     if (w == 0) return p;
     p.warps = w;
     p.smem = cb + (size_t)w * wb;
-    // split k so that there are enough CTAs to fill the GPU
+    p.cap = cap;
     int64_t want_ctas = (int64_t)num_sms * 4;
-    int64_t chunks = std::max<int64_t>(1, std::min<int64_t>((m + w - 1) / w, (want_ctas + m - 1) / m));
+    int64_t chunks =
+        std::max<int64_t>(1, std::min<int64_t>((m + w - 1) / w, (want_ctas + m - 1) / m));
     p.kchunk = (int)((m + chunks - 1) / chunks);
     p.kchunks = (int)((m + p.kchunk - 1) / p.kchunk);
     return p;
@@ -401,7 +718,7 @@ cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, in
     dim3 grid((unsigned)a.m, (unsigned)plan.kchunks);
     LambdaPack lp;
     for (int q = 0; q < nlc; ++q) lp.lam[q] = lambdas[t0 + q];
-    k_pairs<T><<<grid, plan.warps * 32, plan.smem, st>>>(a, lp, t0, nlc, plan.kchunk);
+    k_pairs<T><<<grid, plan.warps * 32, plan.smem, st>>>(a, lp, t0, nlc, plan.kchunk, plan.cap);
     launches++;
     return cudaGetLastError();
 }

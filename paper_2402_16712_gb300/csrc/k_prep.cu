@@ -46,30 +46,36 @@ __global__ void __launch_bounds__(256) k_colprep(const T *__restrict__ Xt, ColIn
     const int64_t j = blockIdx.x;
     const T *col = Xt + j * ldn;
     __shared__ int s_max[8];
+    __shared__ int s_min[8];
     __shared__ int s_cnt[8];
     __shared__ long long s_q[8];
     __shared__ int s_inx[8];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    int emax = -100000, cnt = 0;
+    int emax = -100000, emin = 100000, cnt = 0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
         T b = col[i];
         if (b != T(0)) {
             cnt++;
-            emax = max(emax, ilog2_pos(b));
+            const int e = ilog2_pos(b);
+            emax = max(emax, e);
+            emin = min(emin, e);
         }
     }
     cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
     emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    emin = __reduce_min_sync(0xFFFFFFFFu, emin);
     if (lane == 0) {
         s_max[warp] = emax;
+        s_min[warp] = emin;
         s_cnt[warp] = cnt;
     }
     __syncthreads();
-    int nv = 0, E = -100000;
+    int nv = 0, E = -100000, Emin = 100000;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
         nv += s_cnt[w];
         E = max(E, s_max[w]);
+        Emin = min(Emin, s_min[w]);
     }
     const int Lbits = nv > 0 ? 32 - __clz(nv) : 0;
     const int sigma = nv > 0 ? 60 - E - Lbits : 0;
@@ -103,7 +109,7 @@ __global__ void __launch_bounds__(256) k_colprep(const T *__restrict__ Xt, ColIn
         c.sigma = sigma;
         c.n_valid = nv;
         c.n_inexact = I;
-        c.pad = 0;
+        c.flags = (nv > 0 && (Emin < WideRange<T>::lo || E > WideRange<T>::hi)) ? COL_WIDE : 0;
         ci[j] = c;
     }
 }

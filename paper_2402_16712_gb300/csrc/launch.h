@@ -19,6 +19,7 @@ struct PairPlan {
     size_t smem;
     int kchunk;
     int kchunks;
+    int cap;  // per-warp candidate-list capacity
 };
 template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms);
 template <typename T> int64_t max_rows_pairs();
