@@ -118,6 +118,38 @@ int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, double *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * No-allocation fit (the paper has no counterpart: this is an interface
+ * convenience of the library).
+ *
+ * Some callers cannot call cudaMalloc at all: code embedded in an application
+ * whose device memory is owned by its own allocator, a plugin given no access
+ * to one, or a latency-critical loop that must not pay for the implicit
+ * synchronisation of an allocation.  For them this entry point does what
+ * l1line_fit_f32 does, with the same arguments, results and status codes, but
+ * takes no workspace: it uses a fixed scratch array of
+ * L1L_NOALLOC_SCRATCH_BYTES that the library declares in device memory, which
+ * every GPU that loads the library holds until the process exits.
+ *  - Sizes whose workspace (l1line_workspace_bytes(L1L_DTYPE_F32, n, m,
+ *    n_lambda)) exceeds L1L_NOALLOC_SCRATCH_BYTES return L1L_ERR_UNSUPPORTED
+ *    before anything is launched.
+ *  - The first call on a device looks up the scratch's device address for
+ *    that device (cudaGetSymbolAddress, with the device current); make that
+ *    first call before any stream capture.  Later calls reuse the address.
+ *  - Every call, from every thread and stream, shares the one scratch array:
+ *    calls that overlap on the GPU race and corrupt each other's results.
+ *    Serialise them (one stream, or events).  Each call resets the parts of
+ *    the scratch that must start at zero and overwrites the rest.
+ *  - Device-side status (a non-finite X) is recorded in the scratch, which is
+ *    not exposed; such input gives meaningless results.
+ * X, out_v, out_obj and out_jstar are device pointers as for l1line_fit_f32;
+ * lambdas is a host pointer.  Nothing is allocated or freed.
+ */
+#define L1L_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                           int64_t n_lambda, float *out_v, double *out_obj,
+                           int32_t *out_jstar, void *stream);
+
 /* Synchronise `stream` and return the device-side status recorded in the
  * workspace by the last call that used it (L1L_OK, L1L_ERR_NONFINITE,
  * L1L_ERR_TIMEOUT or L1L_ERR_INTERNAL), or L1L_ERR_CUDA. */

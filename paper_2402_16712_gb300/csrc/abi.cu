@@ -5,6 +5,7 @@
 // never synchronises, except in l1line_status().
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/l1line.h"
 #include "common.cuh"
@@ -252,3 +253,49 @@ int l1line_profile_events(void *start, void *stop) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// No-allocation fit: the workspace is a fixed array in device memory declared
+// by this file.  Host code never uses the array's name as an address (on the
+// host it is only a stand-in for the symbol); the device address is looked up
+// once per device with cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[L1L_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 128;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+int noalloc_scratch_address(void **out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return L1L_ERR_CUDA;
+    if (dev < 0 || dev >= kMaxDevices) return L1L_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return L1L_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return L1L_OK;
+}
+
+}  // namespace
+
+extern "C" int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m,
+                                      const double *lambdas, int64_t n_lambda, float *out_v,
+                                      double *out_obj, int32_t *out_jstar, void *stream) {
+    if (!X || !lambdas || !out_v || !out_obj || !out_jstar || n < 1 || m < 1 || n_lambda < 1)
+        return L1L_ERR_ARG;
+    const size_t need = l1line_workspace_bytes(L1L_DTYPE_F32, n, m, n_lambda);
+    if (need == 0 || need > L1L_NOALLOC_SCRATCH_BYTES) return L1L_ERR_UNSUPPORTED;
+    void *ws = nullptr;
+    const int rc = noalloc_scratch_address(&ws);
+    if (rc != L1L_OK) return rc;
+    // the status word and the exact-path counter are zeroed by the fit itself;
+    // every other region of the workspace is fully overwritten before it is read
+    return fit_impl<float>(X, n, m, lambdas, n_lambda, out_v, out_obj, out_jstar, ws,
+                           L1L_NOALLOC_SCRATCH_BYTES, stream);
+}

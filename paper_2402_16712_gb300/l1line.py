@@ -36,7 +36,9 @@ SIGNATURES = {
     "l1line_status_string": (ctypes.c_char_p, [_I]),
     "l1line_last_launch_count": (_I, []),
     "l1line_profile_events": (_I, [_P, _P]),
+    "l1line_fit_noalloc_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P]),
 }
+NOALLOC_SCRATCH_BYTES = 32 << 20  # L1L_NOALLOC_SCRATCH_BYTES in include/l1line.h
 
 _lib = None
 
