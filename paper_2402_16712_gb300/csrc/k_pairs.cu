@@ -35,6 +35,7 @@
 // magnitudes fall outside the approximation's range, or a candidate list that
 // cannot be narrowed sends the pair to the exact wide-accumulator kernel.
 #include <algorithm>
+#include <cmath>
 
 #include "common.cuh"
 #include "launch.h"
@@ -72,7 +73,7 @@ template <> struct Approx<double> {
 };
 
 constexpr int NSAMP = 64;   // weight-proportional sample rows per column
-constexpr int NBINS = 128;  // candidate-key histogram bins per warp
+constexpr int HIST_WORDS = 4 * 64;  // per-warp exact histogram (4 chunks x 64 bins)
 
 template <typename T> struct PairSmem {
     // per CTA: x_ijhat (T), 1/x_ijhat (float, 0 marks x_ijhat == 0), q_i (int64),
@@ -83,7 +84,7 @@ template <typename T> struct PairSmem {
     // per warp: candidate keys (uint32), row indices (uint16; bit 15 = exact key)
     // and the histogram (uint32)
     __host__ __device__ static size_t warp_bytes(int64_t cap) {
-        return al16(cap * 4) + al16(cap * 2) + al16(NBINS * 4);
+        return al16(cap * 4) + al16(cap * 2) + al16(HIST_WORDS * 4);
     }
 };
 
@@ -174,18 +175,74 @@ __device__ __forceinline__ float target_for(uint32_t key, float hneg, float hpos
 }
 
 // ---------------------------------------------------------------------------
+// Exact weight histogram: XB bins, each an int64 sum kept as four 16-bit
+// chunks in 32-bit shared-memory counters (exact for up to 65,535 rows per
+// bin; 64-bit shared atomics are several times slower on this GPU).
+// ---------------------------------------------------------------------------
+constexpr int XB = 64;
+constexpr uint16_t ROW_MASK = 0x7FFFu;
+
+__device__ __forceinline__ void hist_zero(uint32_t *h, int lane) {
+#pragma unroll
+    for (int q = 0; q < (4 * XB) / 32; ++q) h[q * 32 + lane] = 0u;
+}
+__device__ __forceinline__ void hist_add(uint32_t *h, int bin, int64_t q) {
+    const uint64_t u = (uint64_t)q;
+    atomicAdd(&h[bin], (uint32_t)(u & 0xFFFFu));
+    atomicAdd(&h[XB + bin], (uint32_t)((u >> 16) & 0xFFFFu));
+    atomicAdd(&h[2 * XB + bin], (uint32_t)((u >> 32) & 0xFFFFu));
+    atomicAdd(&h[3 * XB + bin], (uint32_t)(u >> 48));
+}
+__device__ __forceinline__ int64_t hist_get(const uint32_t *h, int bin) {
+    return (int64_t)h[bin] + ((int64_t)h[XB + bin] << 16) + ((int64_t)h[2 * XB + bin] << 32) +
+           ((int64_t)h[3 * XB + bin] << 48);
+}
+
+// Among bins 0..nbins-1 of [base, top] (bin b = keys base + [b, b+1) << sh),
+// find the first whose upper key passes the exact test with S = Sbase + weight
+// of bins <= b.  Returns the bin (-1: none passes, -2: undecidable) and the
+// weight below it in *below.
+__device__ __forceinline__ int hist_cross(const uint32_t *h, int nbins, uint32_t base,
+                                          uint32_t top, int sh, int64_t Sbase,
+                                          const Decide &dc, int64_t *below, int lane) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int b0 = 2 * lane, b1 = 2 * lane + 1;
+    const int64_t s0 = b0 < nbins ? hist_get(h, b0) : 0;
+    const int64_t s1 = b1 < nbins ? hist_get(h, b1) : 0;
+    const int64_t incl = warp_scan_add(s0 + s1, lane);
+    const int64_t ex = incl - s0 - s1;
+    auto bhi = [&](int b) -> uint32_t {
+        const uint64_t v = (uint64_t)base + ((uint64_t)(b + 1) << sh) - 1;
+        return v > top ? top : (uint32_t)v;
+    };
+    const int c0 = b0 < nbins ? dc.cond(Sbase + ex + s0, bhi(b0) >= CK0) : 0;
+    const int c1 = b1 < nbins ? dc.cond(Sbase + ex + s0 + s1, bhi(b1) >= CK0) : 0;
+    const unsigned m0 = __ballot_sync(FULL, c0 != 0), m1 = __ballot_sync(FULL, c1 != 0);
+    const unsigned any = m0 | m1;
+    if (!any) return -1;
+    const int ln = __ffs(any) - 1;
+    const bool first_is_b0 = (m0 >> ln) & 1u;
+    const int bsel = 2 * ln + (first_is_b0 ? 0 : 1);
+    const int csel = __shfl_sync(FULL, first_is_b0 ? c0 : c1, ln);
+    const int64_t bel = __shfl_sync(FULL, first_is_b0 ? ex : ex + s0, ln);
+    if (csel < 0) return -2;
+    *below = Sbase + bel;
+    return bsel;
+}
+
+// ---------------------------------------------------------------------------
 // Weighted median of one pair.  Returns SEL_* and the exact key in tstar.
 //
 // The candidate list is kept as 32 interleaved per-lane segments: lane l's
 // j-th candidate sits at slot j*32 + l (bank l, so every access is free of bank
 // conflicts) and each lane counts its own candidates against a quota of
-// qt = cap/32 slots.  No ballot or cross-lane compaction is needed; only the
-// final <= 31 candidates are gathered across the warp.
+// qt = cap/32 slots; only the final <= 31 candidates are gathered across the
+// warp.  Row indices carry a flag bit, EXACT: the stored key is exact.
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *inv,
-                         const int64_t *colq, const uint16_t *samp, int qshift, uint32_t *lk,
-                         uint16_t *li, uint32_t *hist, int qt, int n, const Decide &dc,
+                         const int64_t *colq, const uint16_t *samp, uint32_t *lk, uint16_t *li,
+                         uint32_t *hist, int qt, int n, const Decide &dc,
                          typename Traits<T>::K &tstar, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
@@ -226,17 +283,89 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
         if (kk > CKMAX) kk = dflt;
         return min(max(kk, lo0), hi0);
     };
-    int d0 = 8;
+    int d0 = 6;  // +-6 of 64 samples: ~15% of the rows in the bracket, ~1.5% misses
     uint32_t P1 = pick(jx - d0, lo0);
     uint32_t P2 = pick(jx + d0, hi0);
     if (P1 > P2) P1 = P2;
+    bool sampled = true;     // the bracket still comes from the sample
+    bool count_pass = false;  // next attempt: narrow by a histogram over all rows
 
     int64_t L = 0;   // exact weight of rows with coarse key < lo
-    int64_t Sc = 0;  // weight of the candidates
     uint32_t lo = 0, hi = CKMAX;
     int cnt = 0;     // this lane's candidates
     bool placed = false;
-    for (int attempt = 0; attempt < 8 && !placed; ++attempt) {
+    for (int attempt = 0; attempt < 12 && !placed; ++attempt) {
+        if (count_pass) {
+            // One pass over all rows straight into the exact histogram of
+            // [P1, P2] (rows near a bin edge are divided on the spot); nothing
+            // is stored, so it cannot overflow.  The median's bin becomes the
+            // next bracket, 1/64 of this one.
+            const uint32_t span = P2 - P1;
+            const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
+            const uint32_t bmask = (1u << sh) - 1u;
+            const int nbins = (int)(span >> sh) + 1;
+            const uint32_t bt = sat_sub(P1, G), at = sat_add(P2, G);
+            const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
+            hist_zero(hist, lane);
+            __syncwarp();
+            int64_t Sb = 0;
+            for (int i = lane; i < n; i += 32) {
+                const float iv = inv[i];
+                if (iv == 0.0f) continue;
+                uint32_t kk = akey(__fmul_rn(A::a32(xk[i]), iv));
+                if (kk < bt) {
+                    Sb += colq[i];
+                    continue;
+                }
+                if (kk > at) continue;
+                const uint32_t off = (kk - P1) & bmask;
+                if (!(kk >= g1 && kk <= g2 && off >= G && off + G <= bmask))
+                    kk = A::exact_ck(xk[i], colb[i]);
+                if (kk < P1)
+                    Sb += colq[i];
+                else if (kk <= P2)
+                    hist_add(hist, (int)((kk - P1) >> sh), colq[i]);
+            }
+            Sb = warp_sum_i64(Sb);
+            __syncwarp();
+            const int r1 = P1 == lo0 ? 0 : dc.cond(Sb, (P1 - 1) >= CK0);
+            if (r1 < 0) return SEL_SLOW_BAND;
+            if (r1 == 1) {
+                hi0 = P1 - 1;
+                P1 = lo0;
+                P2 = hi0;
+                continue;
+            }
+            int64_t below = 0;
+            const int bs = hist_cross(hist, nbins, P1, P2, sh, Sb, dc, &below, lane);
+            __syncwarp();
+            if (bs == -2) return SEL_SLOW_BAND;
+            if (bs < 0) {
+                if (P2 >= hi0) return SEL_INTERNAL;
+                lo0 = P2 + 1;
+                P1 = lo0;
+                P2 = hi0;
+                continue;
+            }
+            const uint32_t K1 = P1 + ((uint32_t)bs << sh);
+            const uint32_t K2 = min(P2, K1 + bmask);
+            lo0 = K1;
+            hi0 = K2;
+            P1 = K1;
+            P2 = K2;
+            sampled = false;
+            count_pass = false;
+            if (K1 == K2) {  // one coarse key holds the median
+                if (sizeof(T) == 4) {
+                    tstar = (K)K1;
+                    return SEL_OK;
+                }
+                return SEL_SLOW_CAP;  // double: its exact keys are not known here
+            }
+            continue;
+        }
+        // one pass over all rows: exact weight of rows certainly below P1; rows
+        // whose approximate key is within G of [P1, P2] become candidates
         const uint32_t bt = sat_sub(P1, G);  // certain below: key' < bt
         const uint32_t at = sat_add(P2, G);  // certain above: key' > at
         int64_t Sb = 0;
@@ -284,53 +413,64 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
         }
         Sb = warp_sum_i64(Sb);
         __syncwarp();
-        if (__any_sync(FULL, cnt > qt)) {  // a lane overflowed: pull the pivots closer
-            if (d0 == 0) return SEL_SLOW_CAP;
-            d0 >>= 1;
-            P1 = pick(jx - d0, lo0);
-            P2 = pick(jx + d0, hi0);
-            if (P1 > P2) P1 = P2;
+        if (__any_sync(FULL, cnt > qt)) {  // a lane overflowed: narrow by a count pass
+            if (P1 == P2) return SEL_SLOW_CAP;
+            count_pass = true;
             continue;
         }
-        // resolve the guard bands exactly; weight below P1 and within [P1, P2]
+        // exact histogram of the candidates over [P1, P2]; rows near P1, P2 or a
+        // bin edge are divided exactly first; Sb2 = exact weight below P1
+        const uint32_t span = P2 - P1;
+        const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
+        const uint32_t bmask = (1u << sh) - 1u;
+        const int nbins = (int)(span >> sh) + 1;
         const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
-        int64_t Sb2 = 0, Sm = 0;
+        hist_zero(hist, lane);
+        __syncwarp();
+        int64_t Sb2 = 0;
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             uint32_t kk = lk[p];
             const uint16_t id = li[p];
-            if (kk < g1 || kk > g2) {
+            const uint32_t off = (kk - P1) & bmask;
+            const bool clear = kk >= g1 && kk <= g2 && off >= G && off + G <= bmask;
+            if (!clear) {
                 kk = A::exact_ck(xk[id], colb[id]);
                 lk[p] = kk;
                 li[p] = id | EXACT_BIT;
             }
             const int64_t q = colq[id];
-            Sb2 += kk < P1 ? q : 0;
-            Sm += (kk >= P1 && kk <= P2) ? q : 0;
+            if (kk < P1)
+                Sb2 += q;
+            else if (kk <= P2)
+                hist_add(hist, (int)((kk - P1) >> sh), q);
         }
-        Sb = Sb + warp_sum_i64(Sb2);
-        Sm = warp_sum_i64(Sm);
+        Sb += warp_sum_i64(Sb2);
         __syncwarp();
         const int r1 = P1 == lo0 ? 0 : dc.cond(Sb, (P1 - 1) >= CK0);
         if (r1 < 0) return SEL_SLOW_BAND;
         if (r1 == 1) {  // median below P1: retry under P1
             hi0 = P1 - 1;
             P2 = hi0;
-            P1 = pick(jx - 3 * max(d0, 1) - 1, lo0);
+            P1 = sampled ? pick(jx - 3 * max(d0, 1) - 1, lo0) : lo0;
             if (P1 > P2) P1 = lo0;
             continue;
         }
-        const int r2 = dc.cond(Sb + Sm, P2 >= CK0);
-        if (r2 < 0) return SEL_SLOW_BAND;
-        if (r2 == 0) {  // median above P2: retry over P2
+        int64_t below = 0;
+        const int bs = hist_cross(hist, nbins, P1, P2, sh, Sb, dc, &below, lane);
+        __syncwarp();
+        if (bs == -2) return SEL_SLOW_BAND;
+        if (bs < 0) {  // median above P2: retry over P2
             if (P2 >= hi0) return SEL_INTERNAL;
             lo0 = P2 + 1;
             P1 = lo0;
-            P2 = pick(jx + 3 * max(d0, 1) + 1, hi0);
+            P2 = sampled ? pick(jx + 3 * max(d0, 1) + 1, hi0) : hi0;
             if (P2 < P1) P2 = hi0;
             continue;
         }
-        // median in [P1, P2]: keep those candidates (lane-local, in place)
+        // the median is in bin bs: keep its candidates (lane-local, in place)
+        const uint32_t K1 = P1 + ((uint32_t)bs << sh);
+        const uint32_t K2 = min(P2, K1 + bmask);
         int w = 0;
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
@@ -338,130 +478,63 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
             const uint16_t id = li[p];
             lk[w * 32 + lane] = kk;  // w <= j: kept only if w advances
             li[w * 32 + lane] = id;
-            w += (kk >= P1 && kk <= P2) ? 1 : 0;
+            w += (kk >= K1 && kk <= K2) ? 1 : 0;
         }
         __syncwarp();
         cnt = w;
-        L = Sb;
-        Sc = Sm;
-        lo = P1;
-        hi = P2;
+        L = below;
+        lo = K1;
+        hi = K2;
         placed = true;
     }
     if (!placed) return SEL_SLOW_TRIES;
 
-    // ---------------- levels on the candidate list -------------------------
+    // ---------------- levels on the candidate list: exact histograms ------
     int c = __reduce_add_sync(FULL, cnt);
     for (int level = 0; c > 31 && lo < hi; ++level) {
-        if (level >= 40) return SEL_SLOW_LEVELS;
-        // weight histogram of the candidates' keys over <= 128 bins of [lo, hi]
+        if (level >= 8) return SEL_SLOW_LEVELS;
         const uint32_t span = hi - lo;
-        const int shift = span >= 128u ? (32 - __clz((int)span)) - 7 : 0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) hist[lane * 4 + q] = 0u;
+        const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
+        const uint32_t bmask = (1u << sh) - 1u;
+        const int nbins = (int)(span >> sh) + 1;
+        hist_zero(hist, lane);
         __syncwarp();
-        for (int j = 0; j < cnt; ++j) {
-            const int p = j * 32 + lane;
-            const uint32_t kk = min(max(lk[p], lo), hi);
-            atomicAdd(&hist[(kk - lo) >> shift], (uint32_t)(colq[li[p] & 0x7FFF] >> qshift));
-        }
-        __syncwarp();
-        uint32_t hb[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) hb[q] = hist[lane * 4 + q];
-        __syncwarp();
-        const uint32_t lsum = hb[0] + hb[1] + hb[2] + hb[3];
-        const uint32_t incl = warp_scan_add(lsum, lane);
-        const uint32_t htot = __shfl_sync(FULL, incl, 31);
-        const float scale = htot > 0 ? __fdividef((float)Sc, (float)htot) : 0.0f;
-        // targets relative to L, formed exactly in int64 before rounding to float
-        const float hneg_r = 0.5f * (float)(dc.Q + dc.Lf - 2 * L);
-        const float hpos_r = 0.5f * (float)(dc.Q - dc.Lc - 2 * L);
-        const uint32_t run = incl - lsum;
-        int bsel = 4;
-#pragma unroll
-        for (int q = 3; q >= 0; --q) {
-            const uint32_t before = run + (q > 0 ? hb[0] : 0u) + (q > 1 ? hb[1] : 0u) +
-                                    (q > 2 ? hb[2] : 0u);
-            const uint32_t bin = (uint32_t)(lane * 4 + q);
-            const uint64_t bhi64 = (uint64_t)lo + ((uint64_t)(bin + 1) << shift) - 1;
-            const uint32_t bhi = bhi64 > hi ? hi : (uint32_t)bhi64;
-            const uint32_t blo = lo + (bin << shift);
-            const float cum = (float)(before + hb[q]) * scale;
-            // an empty bin can hold the median only through the penalty point at 0
-            const bool eligible =
-                hb[q] != 0u || (bin <= (span >> shift) && blo <= CK0 && CK0 <= bhi);
-            if (eligible && cum > target_for(bhi, hneg_r, hpos_r)) bsel = q;
-        }
-        const unsigned cmask = __ballot_sync(FULL, bsel < 4);
-        int b_star;
-        if (cmask) {
-            const int ln = __ffs(cmask) - 1;
-            b_star = ln * 4 + __shfl_sync(FULL, bsel, ln);
-        } else {
-            b_star = (int)(span >> shift);
-        }
-        uint32_t Q1 = lo + ((uint32_t)b_star << shift);
-        const uint64_t q2_64 = (uint64_t)lo + ((uint64_t)(b_star + 1) << shift) - 1;
-        uint32_t Q2 = q2_64 > hi ? hi : (uint32_t)q2_64;
-        if (Q1 > hi) Q1 = hi;
-        const uint32_t bt = sat_sub(Q1, G), g1 = sat_add(Q1, G);
-        const uint32_t g2 = sat_sub(Q2, G), at = sat_add(Q2, G);
-        int64_t Sb = 0, Sm = 0;
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             uint32_t kk = lk[p];
             uint16_t id = li[p];
-            if (!(id & EXACT_BIT) && ((kk >= bt && kk < g1) || (kk > g2 && kk <= at))) {
-                kk = A::exact_ck(xk[id], colb[id]);
+            const uint32_t off = (kk - lo) & bmask;
+            if (!(id & EXACT_BIT) && (off < G || off + G > bmask)) {
+                const int row = id & ROW_MASK;
+                kk = A::exact_ck(xk[row], colb[row]);
                 lk[p] = kk;
-                id = id | EXACT_BIT;
+                id = (uint16_t)row | EXACT_BIT;
                 li[p] = id;
             }
-            const int64_t q = colq[id & 0x7FFF];
-            Sb += kk < Q1 ? q : 0;
-            Sm += (kk >= Q1 && kk <= Q2) ? q : 0;
+            hist_add(hist, (int)((kk - lo) >> sh), colq[id & ROW_MASK]);
         }
-        Sb = warp_sum_i64(Sb);
-        Sm = warp_sum_i64(Sm);
         __syncwarp();
-        int part;
-        const int r1 = (Q1 == lo) ? 0 : dc.cond(L + Sb, (Q1 - 1) >= CK0);
-        if (r1 < 0) return SEL_SLOW_BAND;
-        if (r1 == 1) {
-            part = 0;
-            hi = Q1 - 1;
-            Sc = Sb;
-        } else {
-            const int r2 = dc.cond(L + Sb + Sm, Q2 >= CK0);
-            if (r2 < 0) return SEL_SLOW_BAND;
-            if (r2 == 1) {
-                part = 1;
-                lo = Q1;
-                hi = Q2;
-                L += Sb;
-                Sc = Sm;
-            } else {
-                if (Q2 >= hi) return SEL_INTERNAL;
-                part = 2;
-                lo = Q2 + 1;
-                L += Sb + Sm;
-                Sc = Sc - Sb - Sm;
-            }
-        }
+        int64_t below = 0;
+        const int bs = hist_cross(hist, nbins, lo, hi, sh, L, dc, &below, lane);
+        __syncwarp();
+        if (bs == -2) return SEL_SLOW_BAND;
+        if (bs < 0) return SEL_INTERNAL;
+        const uint32_t K1 = lo + ((uint32_t)bs << sh);
+        const uint32_t K2 = min(hi, K1 + bmask);
         int w = 0;
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             const uint32_t kk = lk[p];
             const uint16_t id = li[p];
-            const bool keep =
-                part == 0 ? kk < Q1 : (part == 1 ? (kk >= Q1 && kk <= Q2) : kk > Q2);
-            lk[w * 32 + lane] = kk;  // w <= j: kept only if w advances
+            lk[w * 32 + lane] = kk;
             li[w * 32 + lane] = id;
-            w += keep ? 1 : 0;
+            w += (kk >= K1 && kk <= K2) ? 1 : 0;
         }
         __syncwarp();
         cnt = w;
+        L = below;
+        lo = K1;
+        hi = K2;
         c = __reduce_add_sync(FULL, cnt);
     }
 
@@ -473,7 +546,7 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
     if (c > 31) {  // one coarse key left, many rows: all exact keys equal?
         K kmin = Tr::NONE, kmax = 0;
         for (int j = 0; j < cnt; ++j) {
-            const int row = li[j * 32 + lane] & 0x7FFF;
+            const int row = li[j * 32 + lane] & ROW_MASK;
             const K ke = Tr::key(Tr::div_rn(xk[row], colb[row]));
             kmin = min(kmin, ke);
             kmax = max(kmax, ke);
@@ -494,7 +567,7 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
     {
         const int excl = warp_scan_add(cnt, lane) - cnt;
         uint16_t *stage = reinterpret_cast<uint16_t *>(hist);
-        for (int j = 0; j < cnt; ++j) stage[excl + j] = li[j * 32 + lane] & 0x7FFF;
+        for (int j = 0; j < cnt; ++j) stage[excl + j] = li[j * 32 + lane] & ROW_MASK;
     }
     __syncwarp();
     K fk = Tr::NONE;
@@ -588,7 +661,6 @@ __global__ void __launch_bounds__(256, 3) k_pairs(ScanArgs<T> a, LambdaPack lp, 
         }
         __syncthreads();
     }
-    const int qshift = max(0, 45 - (cinfo.n_valid > 0 ? 32 - __clz(cinfo.n_valid) : 0));
     // per-lambda thresholds of the exact test depend on (jhat, lambda) only
     constexpr int NDEC = 16;
     __shared__ Decide s_dec[NDEC];
@@ -624,8 +696,8 @@ __global__ void __launch_bounds__(256, 3) k_pairs(ScanArgs<T> a, LambdaPack lp, 
                     dc = s_dec[tl];
                 else
                     dc.init(cinfo, lam);
-                st = select_v2<T>(xk, colb, inv, colq, samp, qshift, lk, li, hist, cap / 32, n,
-                                  dc, ts, lane);
+                st = select_v2<T>(xk, colb, inv, colq, samp, lk, li, hist, cap / 32, n, dc, ts,
+                                  lane);
             }
             if (st >= SEL_SLOW) {
                 if (lane == 0) {
@@ -669,7 +741,7 @@ template <typename T> static int cap_for(int64_t npad) {
 template <typename T> int64_t max_rows_pairs() {
     const size_t budget = 227 * 1024;
     int64_t n = 32;
-    while (n + 32 <= 32767 &&
+    while (n + 32 <= (int64_t)ROW_MASK + 1 &&
            PairSmem<T>::col_bytes(n + 32) + PairSmem<T>::warp_bytes(cap_for<T>(n + 32)) <= budget)
         n += 32;
     return n;
@@ -679,28 +751,34 @@ template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms) {
     PairPlan p{0, 0, 0, 0, 0};
     const int64_t npad = (n + 31) & ~int64_t(31);
     if (n > max_rows_pairs<T>()) return p;
-    int cap = cap_for<T>(npad);
     const size_t cb = PairSmem<T>::col_bytes(npad);
-    // 8 warps per CTA; the register budget allows three such CTAs per SM, so
-    // shrink the candidate lists (not below 256 slots) to fit three in shared
-    // memory (228 KB per SM, 1 KB reserved per CTA, static arrays included)
-    {
-        const int64_t per_cta = 233472 / 3 - 1024 - 1024;
-        const int64_t fit = ((per_cta - (int64_t)cb) / 8 - NBINS * 4) / 6;
-        const int64_t fit32 = fit & ~int64_t(31);
-        if (fit32 >= std::min<int64_t>(npad, 256)) cap = (int)std::min<int64_t>(cap, fit32);
-    }
-    const size_t wb = PairSmem<T>::warp_bytes(cap);
-    int w = 0;
-    for (int cand = 8; cand >= 1; --cand)
-        if (cb + cand * wb <= 227 * 1024) {
-            w = cand;
-            break;
+    // Per-lane candidate quota wanted: the level-0 bracket holds ~15% of the
+    // rows, i.e. mu = 0.15 n/32 per lane; ask for mu + 3.5 sqrt(mu) + 1 so that
+    // the busiest of 32 lanes rarely overflows (an overflow costs one more pass).
+    const double mu = 0.15 * (double)npad / 32.0;
+    const int64_t qt_need = std::min<int64_t>(npad / 32, (int64_t)ceil(mu + 3.5 * sqrt(mu) + 1.0));
+    // Up to three 8-warp CTAs per SM fit the register budget (80 registers x
+    // 256 threads).  Over 1-3 CTAs per SM and 1-8 warps per CTA, keep the plan
+    // with the most resident warps whose lists meet the quota in 228 KB of
+    // shared memory (1 KB reserved per CTA, static arrays included).
+    int w = 0, cap = 0, best = 0;
+    for (int ctas = 3; ctas >= 1; --ctas) {
+        const int64_t per_cta = 233472 / ctas - 1024 - 1024;
+        for (int cand = 8; cand >= 1; --cand) {
+            if (ctas * cand <= best || ctas * cand > 24) continue;
+            const int64_t fit = ((per_cta - (int64_t)cb) / cand - HIST_WORDS * 4) / 6;
+            const int64_t c32 = std::min<int64_t>(npad, fit) & ~int64_t(31);
+            if (fit > 0 && c32 >= 32 * qt_need) {
+                w = cand;
+                cap = (int)c32;
+                best = ctas * cand;
+            }
         }
+    }
     if (w == 0) return p;
     p.warps = w;
-    p.smem = cb + (size_t)w * wb;
     p.cap = cap;
+    p.smem = cb + (size_t)w * PairSmem<T>::warp_bytes(cap);
     int64_t want_ctas = (int64_t)num_sms * 4;
     int64_t chunks =
         std::max<int64_t>(1, std::min<int64_t>((m + w - 1) / w, (want_ctas + m - 1) / m));
