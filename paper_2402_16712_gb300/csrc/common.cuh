@@ -231,6 +231,7 @@ template <typename T> struct ScanArgs {
 constexpr int MAX_LAMBDA_PER_LAUNCH = 256;
 struct LambdaPack {
     double lam[MAX_LAMBDA_PER_LAUNCH];
+    int tl_min, tl_max;  // positions of the smallest and largest lambda of the launch
 };
 
 }  // namespace l1l

@@ -161,6 +161,7 @@ template <typename T>
 cudaError_t launch_exact(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
                          int num_sms, cudaStream_t st, int &launches) {
     LambdaPack lp;
+    lp.tl_min = lp.tl_max = 0;
     for (int q = 0; q < nlc; ++q) lp.lam[q] = lambdas[t0 + q];
     k_exact<T><<<num_sms * 2, 128, 0, st>>>(a, lp, t0);
     launches++;

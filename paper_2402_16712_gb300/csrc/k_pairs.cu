@@ -597,6 +597,214 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
     return SEL_OK;
 }
 
+// Everything one warp needs to solve the pairs of its CTA's column jhat.
+template <typename T> struct WarpCtx {
+    const T *colb;
+    const float *inv;
+    const int64_t *colq;
+    const uint16_t *samp;
+    uint32_t *lk;
+    uint16_t *li;
+    uint32_t *hist;
+    const Decide *s_dec;  // per-lambda thresholds for the first NDEC lambdas
+    int qt, n;
+    ColInfo cinfo;
+};
+constexpr int NDEC = 32;
+
+template <typename T>
+__device__ __forceinline__ Decide decide_for(const WarpCtx<T> &w, const LambdaPack &lp, int tl) {
+    Decide dc;
+    if (tl < NDEC)
+        dc = w.s_dec[tl];
+    else
+        dc.init(w.cinfo, lp.lam[tl]);
+    return dc;
+}
+
+// Writes v and s of (lambda t0+tl, jhat, k), or lists the pair for the exact path.
+template <typename T>
+__device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int st,
+                          typename Traits<T>::K ts, const T *xk, const T *colb, int n,
+                          double lam, int lane) {
+    using Tr = Traits<T>;
+    const int64_t m = a.m;
+    const int64_t o = ((int64_t)t * m + j) * m + k;
+    if (st >= SEL_SLOW) {
+        if (lane == 0) {
+            uint32_t slot = atomicAdd(a.slow_count, 1u);
+            SlowEntry e;
+            e.t = t;
+            e.j = (int32_t)j;
+            e.k = (int32_t)k;
+            e.inst = 0;
+            e.reason = (int16_t)st;
+            a.slow[slot] = e;
+        }
+        return;
+    }
+    if (st == SEL_INTERNAL) {
+        if (lane == 0) {
+            atomicOr(a.status, ST_INTERNAL);
+            a.v_all[o] = T(NAN);
+            a.s_all[o] = NAN;
+        }
+        return;
+    }
+    const T v = Tr::value(ts);
+    const T res = warp_residual<T>(xk, colb, n, v, lane);
+    if (lane == 0) {
+        a.v_all[o] = v;
+        a.s_all[o] = (double)res + lam * (double)fabs(v);
+    }
+}
+
+// One lambda of one pair: the full selection.
+template <typename T>
+__device__ void solve_one(const ScanArgs<T> &a, const LambdaPack &lp, int t0, int tl, int64_t j,
+                          int64_t k, const T *xk, const WarpCtx<T> &w, bool slow_pair,
+                          int lane) {
+    using Tr = Traits<T>;
+    typename Tr::K ts = Tr::KEY0;
+    int st = SEL_OK;
+    if (slow_pair) {
+        st = SEL_SLOW;
+    } else if (w.cinfo.n_valid > 0) {
+        const Decide dc = decide_for(w, lp, tl);
+        st = select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, dc,
+                          ts, lane);
+    }
+    emit_pair<T>(a, t0 + tl, j, k, st, ts, xk, w.colb, w.n, lp.lam[tl], lane);
+}
+
+// Lambda batch (step A7).  The weighted median moves monotonically toward 0
+// as lambda grows (the penalty point only gains weight), so every lambda's
+// median lies between those of the smallest and the largest lambda.  Solve
+// those two fully, collect the rows whose exact keys lie between them (one
+// pass, exact divisions only near the bounds) together with the exact weight
+// below, and decide every lambda from one sort and prefix scan of those rows.
+// Returns false (nothing written) when more than 31 rows lie between.
+template <typename T>
+__device__ bool lambda_path(const ScanArgs<T> &a, const LambdaPack &lp, int t0, int nlc, int64_t j,
+                            int64_t k, const T *__restrict__ xk, const WarpCtx<T> &w, int lane) {
+    using Tr = Traits<T>;
+    using K = typename Tr::K;
+    using A = Approx<T>;
+    constexpr uint32_t G = A::G;
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int n = w.n;
+    K Ka = Tr::KEY0, Kb = Tr::KEY0;
+    {
+        const Decide da = decide_for(w, lp, lp.tl_min);
+        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, da, Ka,
+                         lane) != SEL_OK)
+            return false;
+        const Decide db = decide_for(w, lp, lp.tl_max);
+        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, db, Kb,
+                         lane) != SEL_OK)
+            return false;
+    }
+    const K Klo = min(Ka, Kb), Khi = max(Ka, Kb);
+    const uint32_t cl = ckey((float)Tr::value(Klo)), ch = ckey((float)Tr::value(Khi));
+    const uint32_t bt = sat_sub(cl, G), at = sat_add(ch, G);
+    int64_t Sb = 0;  // exact weight of rows with key < Klo
+    int cnt = 0;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(w.hist);
+    int c = 0;
+    constexpr int U = 4;  // loads of the next batch in flight while this one is classified
+    T an[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int i = u * 32 + lane;
+        an[u] = i < n ? xk[i] : T(0);
+    }
+    for (int i0 = 0; i0 < n; i0 += 32 * U) {
+        T ac[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) ac[u] = an[u];
+        if (i0 + 32 * U < n) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + 32 * U + u * 32 + lane;
+                an[u] = i < n ? xk[i] : T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * 32 + lane;
+            bool take = false;
+            if (i < n) {
+                const float iv = w.inv[i];
+                if (iv != 0.0f) {
+                    const uint32_t kk = akey(__fmul_rn(A::a32(ac[u]), iv));
+                    if (kk < bt) {
+                        Sb += w.colq[i];
+                    } else if (kk <= at) {
+                        const K ke = Tr::key(Tr::div_rn(ac[u], w.colb[i]));
+                        if (ke < Klo)
+                            Sb += w.colq[i];
+                        else if (ke <= Khi)
+                            take = true;
+                    }
+                }
+            }
+            const unsigned msk = __ballot_sync(FULL, take);
+            if (take) {
+                const int pos = c + __popc(msk & ((1u << lane) - 1u));
+                if (pos < 31) stage[pos] = (uint16_t)i;
+            }
+            c += __popc(msk);
+            cnt += take ? 1 : 0;
+        }
+    }
+    (void)cnt;
+    Sb = warp_sum_i64(Sb);
+    __syncwarp();
+    if (c > 31) return false;
+    K fk = Tr::NONE;
+    int64_t fq = 0;
+    if (lane < c) {
+        const int row = stage[lane];
+        fk = Tr::key(Tr::div_rn(xk[row], w.colb[row]));
+        fq = w.colq[row];
+    } else if (lane == c && Klo <= Tr::KEY0 && Tr::KEY0 <= Khi) {
+        fk = Tr::KEY0;
+    }
+    __syncwarp();
+    warp_sort32(fk, fq, lane);
+    const int64_t P = warp_scan_add(fq, lane);
+    const K nxt = __shfl_down_sync(FULL, fk, 1);
+    const bool last = (lane == 31) || (nxt != fk);
+    K prev = Tr::NONE;
+    T prev_res = T(0);
+    for (int tl = 0; tl < nlc; ++tl) {
+        const Decide dc = decide_for(w, lp, tl);
+        int r = -2;
+        if (last && fk != Tr::NONE) r = dc.cond(Sb + P, fk >= Tr::KEY0);
+        const unsigned okm = __ballot_sync(FULL, r == 1);
+        const unsigned unm = __ballot_sync(FULL, r == -1);
+        const unsigned any = okm | unm;
+        const int first = any ? __ffs(any) - 1 : 0;
+        if (!any || ((unm >> first) & 1u)) {  // undecided here: full selection
+            solve_one<T>(a, lp, t0, tl, j, k, xk, w, false, lane);
+            prev = Tr::NONE;
+            continue;
+        }
+        const K ts = __shfl_sync(FULL, fk, first);
+        const T v = Tr::value(ts);
+        if (ts != prev) {
+            prev_res = warp_residual<T>(xk, w.colb, n, v, lane);
+            prev = ts;
+        }
+        if (lane == 0) {
+            const int64_t o = ((int64_t)(t0 + tl) * a.m + j) * a.m + k;
+            a.v_all[o] = v;
+            a.s_all[o] = (double)prev_res + lp.lam[tl] * (double)fabs(v);
+        }
+    }
+    return true;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256, 3) k_pairs(ScanArgs<T> a, LambdaPack lp, int t0, int nlc,
                                                int kchunk, int cap) {
@@ -662,10 +870,21 @@ __global__ void __launch_bounds__(256, 3) k_pairs(ScanArgs<T> a, LambdaPack lp, 
         __syncthreads();
     }
     // per-lambda thresholds of the exact test depend on (jhat, lambda) only
-    constexpr int NDEC = 16;
     __shared__ Decide s_dec[NDEC];
     for (int tl = threadIdx.x; tl < min(nlc, NDEC); tl += blockDim.x) s_dec[tl].init(cinfo, lp.lam[tl]);
     __syncthreads();
+    WarpCtx<T> wc;
+    wc.colb = colb;
+    wc.inv = inv;
+    wc.colq = colq;
+    wc.samp = samp;
+    wc.lk = lk;
+    wc.li = li;
+    wc.hist = hist;
+    wc.s_dec = s_dec;
+    wc.qt = cap / 32;
+    wc.n = n;
+    wc.cinfo = cinfo;
 
     const bool jwide = (cinfo.flags & COL_WIDE) != 0;
     const int64_t k0 = (int64_t)blockIdx.y * kchunk;
@@ -682,51 +901,12 @@ __global__ void __launch_bounds__(256, 3) k_pairs(ScanArgs<T> a, LambdaPack lp, 
         const T *xk = a.Xt + k * ldn;
         const bool slow_pair = a.force_exact || jwide ||
                                (sizeof(T) == 8 && (a.ci[k].flags & COL_WIDE));
-        for (int tl = 0; tl < nlc; ++tl) {
-            const int t = t0 + tl;
-            const double lam = lp.lam[tl];
-            const int64_t o = ((int64_t)t * m + j) * m + k;
-            K ts = Tr::KEY0;
-            int st = SEL_OK;
-            if (slow_pair) {
-                st = SEL_SLOW;
-            } else if (cinfo.n_valid > 0) {
-                Decide dc;
-                if (tl < NDEC)
-                    dc = s_dec[tl];
-                else
-                    dc.init(cinfo, lam);
-                st = select_v2<T>(xk, colb, inv, colq, samp, lk, li, hist, cap / 32, n, dc, ts,
-                                  lane);
-            }
-            if (st >= SEL_SLOW) {
-                if (lane == 0) {
-                    uint32_t slot = atomicAdd(a.slow_count, 1u);
-                    SlowEntry e;
-                    e.t = t;
-                    e.j = j;
-                    e.k = (int32_t)k;
-                    e.inst = 0;
-                    e.reason = (int16_t)st;
-                    a.slow[slot] = e;
-                }
-                continue;
-            }
-            if (st == SEL_INTERNAL) {
-                if (lane == 0) {
-                    atomicOr(a.status, ST_INTERNAL);
-                    a.v_all[o] = T(NAN);
-                    a.s_all[o] = NAN;
-                }
-                continue;
-            }
-            const T v = Tr::value(ts);
-            const T res = warp_residual<T>(xk, colb, n, v, lane);
-            if (lane == 0) {
-                a.v_all[o] = v;
-                a.s_all[o] = (double)res + lam * (double)fabs(v);
-            }
+        if (nlc >= 3 && !slow_pair && cinfo.n_valid > 0 &&
+            lambda_path<T>(a, lp, t0, nlc, j, k, xk, wc, lane)) {
+            __syncwarp();
+            continue;
         }
+        for (int tl = 0; tl < nlc; ++tl) solve_one<T>(a, lp, t0, tl, j, k, xk, wc, slow_pair, lane);
         __syncwarp();
     }
 }
@@ -795,7 +975,12 @@ cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, in
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)a.m, (unsigned)plan.kchunks);
     LambdaPack lp;
-    for (int q = 0; q < nlc; ++q) lp.lam[q] = lambdas[t0 + q];
+    lp.tl_min = lp.tl_max = 0;
+    for (int q = 0; q < nlc; ++q) {
+        lp.lam[q] = lambdas[t0 + q];
+        if (lp.lam[q] < lp.lam[lp.tl_min]) lp.tl_min = q;
+        if (lp.lam[q] > lp.lam[lp.tl_max]) lp.tl_max = q;
+    }
     k_pairs<T><<<grid, plan.warps * 32, plan.smem, st>>>(a, lp, t0, nlc, plan.kchunk, plan.cap);
     launches++;
     return cudaGetLastError();

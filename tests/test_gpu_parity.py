@@ -155,3 +155,13 @@ def test_paper_size_sampled(dtype):
     assert abs(obj[0] - ref["z_all"][0, js0]) <= (1e-5 if dtype == np.float32 else 1e-12) * obj[0]
     # the GPU's jhat* is no worse than any sampled jhat under the oracle's z
     assert ref["z_all"][0, js0] <= np.nanmin(ref["z_all"][0, sample]) * (1 + 1e-5)
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_lambda_batch_unsorted_and_repeated(dtype):
+    """Lambdas in arbitrary order, with repeats: results follow the caller's order."""
+    X, _, _ = datagen.planted(datagen.Planted(257, 15, 3, 0.1, 0.1, 5.0, 8, np.dtype(dtype).name))
+    rng = np.random.default_rng(2)
+    lams = rng.permutation(np.concatenate([np.logspace(-3, 1.5, 12), [0.0, 0.3, 0.3]]))
+    _, _, ref = check_scan(X, lams, where="unsorted lambdas")
+    check_fit(X, lams, ref, where="unsorted lambdas")
