@@ -119,6 +119,37 @@ int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                    void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Batched fit (step A7 over independent instances; BASELINE's uneven-batch
+ * workload): `batch` (1..256) independent problems, instance b with its own
+ * X_b (DEVICE pointer, row-major ns[b] x ms[b]) and lambdas
+ * lambdas[lambda_offsets[b] .. lambda_offsets[b+1]) (HOST arrays; at most 512
+ * lambdas in total, lambda_offsets[0] = 0).  Each instance is fitted exactly
+ * as l1line_fit_* would fit it.  Outputs are concatenated in instance order:
+ *   out_v     DEVICE  instance b's [n_lambda_b][ms[b]] block starts at
+ *                     sum_{b'<b} n_lambda_b' * ms[b']
+ *   out_obj   DEVICE  instance b's n_lambda_b values start at lambda_offsets[b]
+ *   out_jstar DEVICE  likewise (0-based jhat* per lambda)
+ * The pair work runs in one persistent launch whose blocks take (instance,
+ * jhat) units from an atomic counter, largest instances first.  All launch
+ * parameters are passed by value; after one call with a given shape the
+ * sequence issues only stream operations.  Workspace: see
+ * l1line_batched_workspace_bytes (0 on a bad argument); l1line_status reads
+ * its device status.
+ */
+size_t l1line_batched_workspace_bytes(int dtype, int64_t batch, const int64_t *ns,
+                                      const int64_t *ms, const int64_t *lambda_offsets);
+int l1line_fit_batched_f32(int64_t batch, const float *const *Xs, const int64_t *ns,
+                           const int64_t *ms, const double *lambdas,
+                           const int64_t *lambda_offsets, float *out_v, double *out_obj,
+                           int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                           void *stream);
+int l1line_fit_batched_f64(int64_t batch, const double *const *Xs, const int64_t *ns,
+                           const int64_t *ms, const double *lambdas,
+                           const int64_t *lambda_offsets, double *out_v, double *out_obj,
+                           int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
+/*
  * No-allocation fit (the paper has no counterpart: this is an interface
  * convenience of the library).
  *

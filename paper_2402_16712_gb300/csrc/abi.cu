@@ -3,9 +3,13 @@
 // Host code only: validates arguments, carves the caller's workspace and
 // enqueues the kernels on the caller's stream.  It never allocates memory and
 // never synchronises, except in l1line_status().
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <numeric>
+#include <vector>
 
 #include "../../include/l1line.h"
 #include "common.cuh"
@@ -109,6 +113,7 @@ int scan_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t n
     a.slow_count = reinterpret_cast<uint32_t *>(base + L.slow_count);
     a.slow = reinterpret_cast<SlowEntry *>(base + L.slow);
     a.force_exact = (flags & L1L_FLAG_FORCE_EXACT) ? 1 : 0;
+    a.inst = 0;
     double *z = z_all ? z_all : reinterpret_cast<double *>(base + L.z_all);
 
     int launches = 0;
@@ -250,6 +255,176 @@ int l1line_profile_events(void *start, void *stop) {
         g_ev_start = g_ev_stop = nullptr;
     }
     return L1L_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched fit
+// ---------------------------------------------------------------------------
+namespace {
+
+struct BatchShape {
+    std::vector<int> order;  // processing order (largest work first) -> caller index
+    size_t ws_total = 0;
+    int64_t max_n = 0;
+    bool multi = false;
+};
+
+// Validates the shapes and lambda offsets; fills `sh`.  Returns an l1l_status.
+int batch_shape(int dtype, int64_t batch, const int64_t *ns, const int64_t *ms,
+                const int64_t *loff, BatchShape &sh) {
+    if (batch < 1 || !ns || !ms || !loff) return L1L_ERR_ARG;
+    if (batch > MAX_BATCH) return L1L_ERR_UNSUPPORTED;
+    if (loff[0] != 0) return L1L_ERR_ARG;
+    const int64_t es = dtype == L1L_DTYPE_F32 ? 4 : 8;
+    const int64_t maxr = dtype == L1L_DTYPE_F32 ? max_rows_pairs<float>() : max_rows_pairs<double>();
+    int64_t units = 0, ztasks = 0, pairs = 0;
+    size_t regions = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        const int64_t nl = loff[b + 1] - loff[b];
+        if (ns[b] < 1 || ms[b] < 1 || nl < 1) return L1L_ERR_ARG;
+        if (ns[b] > maxr || ms[b] > (1 << 20)) return L1L_ERR_UNSUPPORTED;
+        const int64_t ldn = (ns[b] + 31) & ~int64_t(31);
+        units += ms[b];
+        ztasks += nl * ms[b];
+        pairs += nl * ms[b] * ms[b];
+        regions += inst_layout(ms[b], ldn, nl, (size_t)es).total;
+        sh.max_n = std::max(sh.max_n, ns[b]);
+        sh.multi = sh.multi || nl >= 3;
+    }
+    if (loff[batch] > MAX_BATCH_LAMBDAS) return L1L_ERR_UNSUPPORTED;
+    if (units > 0x7FFFFFFF || ztasks > 0x7FFFFFFF || pairs > ((int64_t)1 << 40))
+        return L1L_ERR_UNSUPPORTED;
+    sh.ws_total = BATCH_HEAD + al256((size_t)pairs * sizeof(SlowEntry)) + regions;
+    sh.order.resize((size_t)batch);
+    std::iota(sh.order.begin(), sh.order.end(), 0);
+    std::stable_sort(sh.order.begin(), sh.order.end(), [&](int x, int y) {
+        const double cx = (double)ns[x] * ms[x] * ms[x] * (loff[x + 1] - loff[x]);
+        const double cy = (double)ns[y] * ms[y] * ms[y] * (loff[y + 1] - loff[y]);
+        return cx > cy;
+    });
+    return L1L_OK;
+}
+
+template <typename T>
+int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const int64_t *ms,
+                     const double *lambdas, const int64_t *loff, T *out_v, double *out_obj,
+                     int32_t *out_jstar, void *ws, size_t ws_bytes, void *stream, uint32_t flags) {
+    g_last_launches = 0;
+    if (!Xs || !lambdas || !out_v || !out_obj || !out_jstar) return L1L_ERR_ARG;
+    BatchShape sh;
+    int rc = batch_shape(dtype_of<T>(), batch, ns, ms, loff, sh);
+    if (rc != L1L_OK) return rc;
+    for (int64_t t = 0; t < loff[batch]; ++t)
+        if (!(lambdas[t] >= 0.0) || std::isinf(lambdas[t])) return L1L_ERR_ARG;
+    for (int64_t b = 0; b < batch; ++b)
+        if (!Xs[b] || (reinterpret_cast<uintptr_t>(Xs[b]) % sizeof(T)) != 0) return L1L_ERR_ARG;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < sh.ws_total)
+        return L1L_ERR_WORKSPACE;
+    const int sms = num_sms();
+    if (sms <= 0) return L1L_ERR_CUDA;
+    const PairPlan plan = plan_pairs<T>(sh.max_n, 1, sms);
+    if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
+
+    std::unique_ptr<BatchDesc<T>> bd(new BatchDesc<T>());
+    std::memset(bd.get(), 0, sizeof(BatchDesc<T>));
+    // caller-order output offsets
+    std::vector<int64_t> vo((size_t)batch), to((size_t)batch);
+    int64_t acc_v = 0, acc_t = 0;
+    for (int64_t b = 0; b < batch; ++b) {
+        vo[(size_t)b] = acc_v;
+        to[(size_t)b] = acc_t;
+        const int64_t nl = loff[b + 1] - loff[b];
+        acc_v += nl * ms[b];
+        acc_t += nl;
+    }
+    size_t off = BATCH_HEAD;
+    int64_t pairs = 0;
+    for (int64_t b = 0; b < batch; ++b) pairs += (loff[b + 1] - loff[b]) * ms[b] * ms[b];
+    off += al256((size_t)pairs * sizeof(SlowEntry));
+    bd->count = (int32_t)batch;
+    bd->lay_npad = (int32_t)((sh.max_n + 31) & ~int64_t(31));
+    bd->cap = plan.cap;
+    bd->force_exact = (flags & L1L_FLAG_FORCE_EXACT) ? 1 : 0;
+    int64_t units = 0, tiles = 0, ztasks = 0, lams = 0;
+    for (int64_t p = 0; p < batch; ++p) {
+        const int b = sh.order[(size_t)p];
+        const int64_t n = ns[b], m = ms[b], nl = loff[b + 1] - loff[b];
+        const int64_t ldn = (n + 31) & ~int64_t(31);
+        BatchInst<T> &in = bd->inst[p];
+        in.X = Xs[b];
+        in.ws_off = (int64_t)off;
+        in.out_v_off = vo[(size_t)b];
+        in.out_t_off = (int32_t)to[(size_t)b];
+        in.n = (int32_t)n;
+        in.m = (int32_t)m;
+        in.ldn = (int32_t)ldn;
+        in.nl = (int32_t)nl;
+        int tmin = 0, tmax = 0;
+        for (int64_t t = 0; t < nl; ++t) {
+            const double l = lambdas[loff[b] + t];
+            bd->lam[lams + t] = l;
+            if (l < lambdas[loff[b] + tmin]) tmin = (int)t;
+            if (l > lambdas[loff[b] + tmax]) tmax = (int)t;
+        }
+        in.tl_min = (int16_t)tmin;
+        in.tl_max = (int16_t)tmax;
+        bd->unit_begin[p] = units;
+        bd->tile_begin[p] = (int32_t)tiles;
+        bd->ztask_begin[p] = (int32_t)ztasks;
+        bd->lam_begin[p] = (int32_t)lams;
+        units += m;
+        tiles += ((m + 31) / 32) * (ldn / 32);
+        ztasks += nl * m;
+        lams += nl;
+        off += inst_layout(m, ldn, nl, sizeof(T)).total;
+    }
+    if (tiles > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
+    bd->unit_begin[batch] = units;
+    bd->tile_begin[batch] = (int32_t)tiles;
+    bd->ztask_begin[batch] = (int32_t)ztasks;
+    bd->lam_begin[batch] = (int32_t)lams;
+    bd->units = units;
+    bd->tiles = (int32_t)tiles;
+    bd->ztasks = (int32_t)ztasks;
+    bd->lams = (int32_t)lams;
+    int launches = 0;
+    if (launch_batch<T>(*bd, static_cast<unsigned char *>(ws), out_v, out_obj, out_jstar, plan,
+                        sh.multi, sms, static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t l1line_batched_workspace_bytes(int dtype, int64_t batch, const int64_t *ns,
+                                      const int64_t *ms, const int64_t *lambda_offsets) {
+    if (dtype != L1L_DTYPE_F32 && dtype != L1L_DTYPE_F64) return 0;
+    BatchShape sh;
+    if (batch_shape(dtype, batch, ns, ms, lambda_offsets, sh) != L1L_OK) return 0;
+    return sh.ws_total;
+}
+
+int l1line_fit_batched_f32(int64_t batch, const float *const *Xs, const int64_t *ns,
+                           const int64_t *ms, const double *lambdas,
+                           const int64_t *lambda_offsets, float *out_v, double *out_obj,
+                           int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                           void *stream) {
+    return fit_batched_impl<float>(batch, Xs, ns, ms, lambdas, lambda_offsets, out_v, out_obj,
+                                   out_jstar, workspace, workspace_bytes, stream, 0u);
+}
+
+int l1line_fit_batched_f64(int64_t batch, const double *const *Xs, const int64_t *ns,
+                           const int64_t *ms, const double *lambdas,
+                           const int64_t *lambda_offsets, double *out_v, double *out_obj,
+                           int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                           void *stream) {
+    return fit_batched_impl<double>(batch, Xs, ns, ms, lambdas, lambda_offsets, out_v, out_obj,
+                                    out_jstar, workspace, workspace_bytes, stream, 0u);
 }
 
 }  // extern "C"

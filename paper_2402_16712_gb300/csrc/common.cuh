@@ -226,9 +226,70 @@ template <typename T> struct ScanArgs {
     uint32_t *slow_count;
     SlowEntry *slow;   // capacity n_lambda * m * m
     int force_exact;
+    int inst;          // instance index recorded in slow-list entries (batched calls)
 };
 
 constexpr int MAX_LAMBDA_PER_LAUNCH = 256;
+
+// ---------------------------------------------------------------------------
+// A batch of independent instances, described entirely by value so that the
+// launches can be captured in a CUDA graph without host-memory copies.
+// Instances are listed in processing order (largest work first); each owns a
+// region of the workspace laid out by inst_layout().
+// ---------------------------------------------------------------------------
+constexpr int MAX_BATCH = 256;
+constexpr int MAX_BATCH_LAMBDAS = 512;
+
+template <typename T> struct BatchInst {
+    const T *X;         // caller's row-major n x m matrix
+    int64_t ws_off;     // this instance's workspace region
+    int64_t out_v_off;  // first element of its v* rows in out_v
+    int32_t n, m, ldn, nl;
+    int32_t out_t_off;  // first slot of its objectives / jhat* in out_obj / out_jstar
+    int16_t tl_min, tl_max;
+};
+
+template <typename T> struct BatchDesc {
+    int32_t count;       // instances
+    int32_t tiles;       // transpose tiles over all instances
+    int64_t units;       // (instance, jhat) work units
+    int32_t ztasks;      // (instance, lambda, jhat) objective sums
+    int32_t lams;        // lambdas over all instances
+    int32_t lay_npad;    // shared-memory layout rows (largest n rounded up to 32)
+    int32_t cap;         // candidate slots per warp
+    int32_t force_exact;
+    int32_t pad;
+    BatchInst<T> inst[MAX_BATCH];
+    int64_t unit_begin[MAX_BATCH + 1];  // prefix of m over instances
+    int32_t tile_begin[MAX_BATCH + 1];
+    int32_t ztask_begin[MAX_BATCH + 1];  // prefix of nl * m
+    int32_t lam_begin[MAX_BATCH + 1];    // prefix of nl (also the index into lam)
+    double lam[MAX_BATCH_LAMBDAS];
+};
+
+// Layout of one instance's workspace region (host and device agree on it).
+struct InstLayout {
+    size_t ci, Xt, v_all, s_all, z_all, total;
+};
+__host__ __device__ inline size_t al256b(size_t x) { return (x + 255) & ~size_t(255); }
+__host__ __device__ inline InstLayout inst_layout(int64_t m, int64_t ldn, int64_t nl, size_t es) {
+    InstLayout L;
+    size_t o = 0;
+    L.ci = o;
+    o = al256b(o + (size_t)m * sizeof(ColInfo));
+    L.Xt = o;
+    o = al256b(o + (size_t)m * (size_t)ldn * es);
+    L.v_all = o;
+    o = al256b(o + (size_t)nl * (size_t)m * (size_t)m * es);
+    L.s_all = o;
+    o = al256b(o + (size_t)nl * (size_t)m * (size_t)m * 8);
+    L.z_all = o;
+    o = al256b(o + (size_t)nl * (size_t)m * 8);
+    L.total = o;
+    return L;
+}
+// Batch-wide workspace head: status word, exact-path counter, unit counter.
+constexpr size_t BATCH_HEAD = 768;
 struct LambdaPack {
     double lam[MAX_LAMBDA_PER_LAUNCH];
     int tl_min, tl_max;  // positions of the smallest and largest lambda of the launch

@@ -8,6 +8,13 @@
 
 namespace l1l {
 
+// Raise a kernel's dynamic shared-memory limit on the current device once;
+// later calls asking for no more skip the runtime call, so that launches can
+// be captured in a CUDA graph after one warm-up call.
+cudaError_t ensure_smem(const void *fn, size_t bytes);
+// Resident blocks per SM for (kernel, threads, dynamic shared memory), cached.
+cudaError_t blocks_per_sm(const void *fn, int threads, size_t smem, int *out);
+
 template <typename T>
 cudaError_t launch_prep(const T *X, T *Xt, ColInfo *ci, int64_t n, int64_t m, int64_t ldn,
                         uint32_t *status, cudaStream_t st, int &launches);
@@ -41,5 +48,11 @@ template <typename T>
 cudaError_t launch_argmin(const double *z_all, const T *v_all, int64_t m, int64_t n_lambda,
                           T *out_v, double *out_obj, int32_t *out_jstar, cudaStream_t st,
                           int &launches);
+
+// The batched fit: staging, one persistent pair kernel, exact path, sums, argmin.
+template <typename T>
+cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, double *out_obj,
+                         int32_t *out_jstar, const PairPlan &plan, bool multi, int num_sms,
+                         cudaStream_t st, int &launches);
 
 }  // namespace l1l

@@ -1,0 +1,920 @@
+// pairs.cuh -- steps A2-A4 for every (lambda, jhat, k): ratios, exact
+// weighted median (Lemma 1) and per-pair residual (Algorithm 1).
+//
+// Layout: one CTA per (jhat, k-chunk).  Column jhat is staged once in shared
+// memory -- x_ijhat, its float reciprocal and its fixed-point weight q_i -- and
+// shared by the CTA's warps; each warp owns one k at a time and keeps a short
+// candidate list of its own.
+//
+// Per pair the warp never divides per row.  It orders rows by a COARSE key,
+// the 32-bit order-preserving image of the ratio rounded to float, and
+// approximates it by one multiply, fl(x_ik * fl(1/x_ijhat)) (both rounded to
+// float first for double input).  The approximation is within G keys of the
+// coarse key of the correctly rounded ratio (G = 8 float, 16 double; the bound
+// is derived in the design notes), so a row whose approximate key is more than
+// G away from a pivot is classified exactly without dividing; the few rows
+// inside a guard band, and the final <= 31 candidates, are divided exactly.
+//
+//   level 0  64 sampled rows are keyed and sorted across the warp; two pivots
+//            bracketing the estimated crossing of half the weight are taken;
+//            one pass over all rows sums the exact fixed-point weight below
+//            the lower pivot and compacts the rows between the pivots (guard
+//            bands included) into the candidate list;
+//   resolve  guard-band candidates are divided exactly; the exact weight below
+//            and between the pivots decides whether the median lies between
+//            them (else level 0 repeats on the indicated side);
+//   levels   on the candidate list: sample 32, sort, two pivots, count, decide,
+//            compact, until <= 31 candidates or one coarse key remains;
+//   final    exact keys (double: 64-bit) of the candidates plus the penalty
+//            point's key are sorted across the warp; a prefix scan of the
+//            weights finds the smallest key whose cumulative weight passes
+//            half the total (the test of Lemma 1, decided exactly);
+//   residual sum_i |x_ik - v x_ijhat| over all rows (Algorithm 1, objective).
+//
+// A decision the truncated fixed-point weights cannot settle, a column whose
+// magnitudes fall outside the approximation's range, or a candidate list that
+// cannot be narrowed sends the pair to the exact wide-accumulator kernel.
+#pragma once
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+
+namespace l1l {
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__device__ __forceinline__ uint32_t ckey(float r) { return Traits<float>::key(r); }
+// Key of an approximate ratio: -0 is not folded onto +0 (the two keys are
+// adjacent, well inside the guard band), which saves two instructions.
+__device__ __forceinline__ uint32_t akey(float r) {
+    const uint32_t u = __float_as_uint(r);
+    return u ^ ((uint32_t)((int32_t)u >> 31) | 0x80000000u);
+}
+
+template <typename T> struct Approx;
+template <> struct Approx<float> {
+    static constexpr uint32_t G = 8;
+    static __device__ __forceinline__ float inv_of(float b) { return __frcp_rn(b); }
+    static __device__ __forceinline__ float a32(float a) { return a; }
+    static __device__ __forceinline__ uint32_t exact_ck(float a, float b) {
+        return ckey(__fdiv_rn(a, b));
+    }
+};
+template <> struct Approx<double> {
+    static constexpr uint32_t G = 16;
+    static __device__ __forceinline__ float inv_of(double b) {
+        return __frcp_rn(__double2float_rn(b));
+    }
+    static __device__ __forceinline__ float a32(double a) { return __double2float_rn(a); }
+    static __device__ __forceinline__ uint32_t exact_ck(double a, double b) {
+        return ckey(__double2float_rn(__ddiv_rn(a, b)));
+    }
+};
+
+constexpr int NSAMP = 64;   // weight-proportional sample rows per column
+constexpr int HIST_WORDS = 4 * 64;  // per-warp exact histogram (4 chunks x 64 bins)
+
+template <typename T> struct PairSmem {
+    // per CTA: x_ijhat (T), 1/x_ijhat (float, 0 marks x_ijhat == 0), q_i (int64),
+    // the 64 sample rows (uint16)
+    __host__ __device__ static size_t col_bytes(int64_t npad) {
+        return al16(npad * sizeof(T)) + al16(npad * 4) + al16(npad * 8) + al16(NSAMP * 2);
+    }
+    // per warp: candidate keys (uint32), row indices (uint16; bit 15 = exact key)
+    // and the histogram (uint32)
+    __host__ __device__ static size_t warp_bytes(int64_t cap) {
+        return al16(cap * 4) + al16(cap * 2) + al16(HIST_WORDS * 4);
+    }
+};
+
+constexpr uint16_t EXACT_BIT = 0x8000u;
+constexpr uint32_t CK0 = 0x80000000u;      // coarse key of 0
+constexpr uint32_t CKMAX = 0xFFFFFFFEu;    // largest usable coarse key
+constexpr uint32_t CKNONE = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------------------
+// Warp sorts.
+// ---------------------------------------------------------------------------
+template <typename K, typename W>
+__device__ __forceinline__ void warp_sort32(K &key, W &w, int lane) {
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            K ok = __shfl_xor_sync(0xFFFFFFFFu, key, stride);
+            W ow = __shfl_xor_sync(0xFFFFFFFFu, w, stride);
+            bool up = (lane & size) == 0 || size == 32;
+            bool lower = (lane & stride) == 0;
+            bool take = lower == up ? (ok < key) : (ok > key);
+            if (take) {
+                key = ok;
+                w = ow;
+            }
+        }
+    }
+}
+
+// 64 keys, element g = e*32 + lane held in slot e; ascending in g.
+__device__ __forceinline__ void warp_sort64(uint32_t (&k)[2], int lane) {
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride == 32) {  // only in the final merge: ascending
+                const uint32_t lo = min(k[0], k[1]), hi = max(k[0], k[1]);
+                k[0] = lo;
+                k[1] = hi;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t ok = __shfl_xor_sync(0xFFFFFFFFu, k[e], stride);
+                    const int g = e * 32 + lane;
+                    const bool up = (g & size) == 0;
+                    const bool lower = (lane & stride) == 0;
+                    k[e] = (lower == up) ? min(ok, k[e]) : max(ok, k[e]);
+                }
+            }
+        }
+    }
+}
+
+template <typename V> __device__ __forceinline__ V warp_scan_add(V x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        V y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// Outcomes of select_v2.  Every code >= SEL_SLOW hands the pair to the exact
+// path; the code says why (kept in the slow list for diagnostics).
+enum {
+    SEL_OK = 0,
+    SEL_INTERNAL = 1,
+    SEL_SLOW = 2,        // column outside the approximate-key range / forced
+    SEL_SLOW_TRIES,      // level 0 kept missing the median
+    SEL_SLOW_CAP,        // too many rows between the closest pivots
+    SEL_SLOW_BAND,       // truncated weights cannot settle a decision
+    SEL_SLOW_LEVELS,     // candidate list did not shrink
+    SEL_SLOW_TIE         // double: one coarse key holds distinct exact keys
+};
+
+__device__ __forceinline__ uint32_t sat_sub(uint32_t a, uint32_t b) { return a > b ? a - b : 0u; }
+__device__ __forceinline__ uint32_t sat_add(uint32_t a, uint32_t b) {
+    return a < CKNONE - b ? a + b : CKNONE;
+}
+
+// Estimated index (0..ns-1) of the first sorted sample whose scaled cumulative
+// weight passes the crossing target; targets are relative to L.
+// Pivot estimates are float: they only steer the search (every decision that
+// matters is exact, in int64), and this GPU's double pipe is narrow.
+__device__ __forceinline__ float target_for(uint32_t key, float hneg, float hpos) {
+    return key >= CK0 ? hpos : hneg;
+}
+
+// ---------------------------------------------------------------------------
+// Exact weight histogram: XB bins, each an int64 sum kept as four 16-bit
+// chunks in 32-bit shared-memory counters (exact for up to 65,535 rows per
+// bin; 64-bit shared atomics are several times slower on this GPU).
+// ---------------------------------------------------------------------------
+constexpr int XB = 64;
+constexpr uint16_t ROW_MASK = 0x7FFFu;
+
+__device__ __forceinline__ void hist_zero(uint32_t *h, int lane) {
+#pragma unroll
+    for (int q = 0; q < (4 * XB) / 32; ++q) h[q * 32 + lane] = 0u;
+}
+__device__ __forceinline__ void hist_add(uint32_t *h, int bin, int64_t q) {
+    const uint64_t u = (uint64_t)q;
+    atomicAdd(&h[bin], (uint32_t)(u & 0xFFFFu));
+    atomicAdd(&h[XB + bin], (uint32_t)((u >> 16) & 0xFFFFu));
+    atomicAdd(&h[2 * XB + bin], (uint32_t)((u >> 32) & 0xFFFFu));
+    atomicAdd(&h[3 * XB + bin], (uint32_t)(u >> 48));
+}
+__device__ __forceinline__ int64_t hist_get(const uint32_t *h, int bin) {
+    return (int64_t)h[bin] + ((int64_t)h[XB + bin] << 16) + ((int64_t)h[2 * XB + bin] << 32) +
+           ((int64_t)h[3 * XB + bin] << 48);
+}
+
+// Among bins 0..nbins-1 of [base, top] (bin b = keys base + [b, b+1) << sh),
+// find the first whose upper key passes the exact test with S = Sbase + weight
+// of bins <= b.  Returns the bin (-1: none passes, -2: undecidable) and the
+// weight below it in *below.
+__device__ __forceinline__ int hist_cross(const uint32_t *h, int nbins, uint32_t base,
+                                          uint32_t top, int sh, int64_t Sbase,
+                                          const Decide &dc, int64_t *below, int lane) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int b0 = 2 * lane, b1 = 2 * lane + 1;
+    const int64_t s0 = b0 < nbins ? hist_get(h, b0) : 0;
+    const int64_t s1 = b1 < nbins ? hist_get(h, b1) : 0;
+    const int64_t incl = warp_scan_add(s0 + s1, lane);
+    const int64_t ex = incl - s0 - s1;
+    auto bhi = [&](int b) -> uint32_t {
+        const uint64_t v = (uint64_t)base + ((uint64_t)(b + 1) << sh) - 1;
+        return v > top ? top : (uint32_t)v;
+    };
+    const int c0 = b0 < nbins ? dc.cond(Sbase + ex + s0, bhi(b0) >= CK0) : 0;
+    const int c1 = b1 < nbins ? dc.cond(Sbase + ex + s0 + s1, bhi(b1) >= CK0) : 0;
+    const unsigned m0 = __ballot_sync(FULL, c0 != 0), m1 = __ballot_sync(FULL, c1 != 0);
+    const unsigned any = m0 | m1;
+    if (!any) return -1;
+    const int ln = __ffs(any) - 1;
+    const bool first_is_b0 = (m0 >> ln) & 1u;
+    const int bsel = 2 * ln + (first_is_b0 ? 0 : 1);
+    const int csel = __shfl_sync(FULL, first_is_b0 ? c0 : c1, ln);
+    const int64_t bel = __shfl_sync(FULL, first_is_b0 ? ex : ex + s0, ln);
+    if (csel < 0) return -2;
+    *below = Sbase + bel;
+    return bsel;
+}
+
+// ---------------------------------------------------------------------------
+// Weighted median of one pair.  Returns SEL_* and the exact key in tstar.
+//
+// The candidate list is kept as 32 interleaved per-lane segments: lane l's
+// j-th candidate sits at slot j*32 + l (bank l, so every access is free of bank
+// conflicts) and each lane counts its own candidates against a quota of
+// qt = cap/32 slots; only the final <= 31 candidates are gathered across the
+// warp.  Row indices carry a flag bit, EXACT: the stored key is exact.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *inv,
+                         const int64_t *colq, const uint16_t *samp, uint32_t *lk, uint16_t *li,
+                         uint32_t *hist, int qt, int n, const Decide &dc,
+                         typename Traits<T>::K &tstar, int lane) {
+    using Tr = Traits<T>;
+    using K = typename Tr::K;
+    using A = Approx<T>;
+    constexpr uint32_t G = A::G;
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int npad_m1 = ((n + 31) & ~31) - 1;
+    const float Qf = (float)dc.Q;
+    const float hneg0 = 0.5f * (Qf + (float)dc.Lf), hpos0 = 0.5f * (Qf - (float)dc.Lc);
+
+    // ---------------- level 0 -------------------------------------------
+    // 64 rows drawn in proportion to their weight (each stands for Q/64), so the
+    // sorted sample keys estimate the weighted quantiles directly.
+    uint32_t sk[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int i = samp[e * 32 + lane];
+        sk[e] = akey(__fmul_rn(A::a32(xk[i]), inv[i]));
+    }
+    warp_sort64(sk, lane);
+    int jx;
+    {
+        const float unit = Qf * (1.0f / 64.0f);
+        const bool c0 = (float)(lane + 1) * unit > target_for(sk[0], hneg0, hpos0);
+        const bool c1 = (float)(lane + 33) * unit > target_for(sk[1], hneg0, hpos0);
+        const unsigned m0 = __ballot_sync(FULL, c0), m1 = __ballot_sync(FULL, c1);
+        jx = m0 ? __ffs(m0) - 1 : (m1 ? 32 + __ffs(m1) - 1 : 63);
+    }
+    auto sample_key = [&](int g) -> uint32_t {
+        const uint32_t a0 = __shfl_sync(FULL, sk[0], g & 31);
+        const uint32_t a1 = __shfl_sync(FULL, sk[1], g & 31);
+        return g < 32 ? a0 : a1;
+    };
+    // the median's coarse key is known to lie in [lo0, hi0]; pivots stay inside
+    uint32_t lo0 = 0, hi0 = CKMAX;
+    auto pick = [&](int g, uint32_t dflt) -> uint32_t {
+        uint32_t kk = (g < 0 || g > 63) ? dflt : sample_key(g);
+        if (kk > CKMAX) kk = dflt;
+        return min(max(kk, lo0), hi0);
+    };
+    int d0 = 6;  // +-6 of 64 samples: ~15% of the rows in the bracket, ~1.5% misses
+    uint32_t P1 = pick(jx - d0, lo0);
+    uint32_t P2 = pick(jx + d0, hi0);
+    if (P1 > P2) P1 = P2;
+    bool sampled = true;     // the bracket still comes from the sample
+    bool count_pass = false;  // next attempt: narrow by a histogram over all rows
+
+    int64_t L = 0;   // exact weight of rows with coarse key < lo
+    uint32_t lo = 0, hi = CKMAX;
+    int cnt = 0;     // this lane's candidates
+    bool placed = false;
+    for (int attempt = 0; attempt < 12 && !placed; ++attempt) {
+        if (count_pass) {
+            // One pass over all rows straight into the exact histogram of
+            // [P1, P2] (rows near a bin edge are divided on the spot); nothing
+            // is stored, so it cannot overflow.  The median's bin becomes the
+            // next bracket, 1/64 of this one.
+            const uint32_t span = P2 - P1;
+            const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
+            const uint32_t bmask = (1u << sh) - 1u;
+            const int nbins = (int)(span >> sh) + 1;
+            const uint32_t bt = sat_sub(P1, G), at = sat_add(P2, G);
+            const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
+            hist_zero(hist, lane);
+            __syncwarp();
+            int64_t Sb = 0;
+            for (int i = lane; i < n; i += 32) {
+                const float iv = inv[i];
+                if (iv == 0.0f) continue;
+                uint32_t kk = akey(__fmul_rn(A::a32(xk[i]), iv));
+                if (kk < bt) {
+                    Sb += colq[i];
+                    continue;
+                }
+                if (kk > at) continue;
+                const uint32_t off = (kk - P1) & bmask;
+                if (!(kk >= g1 && kk <= g2 && off >= G && off + G <= bmask))
+                    kk = A::exact_ck(xk[i], colb[i]);
+                if (kk < P1)
+                    Sb += colq[i];
+                else if (kk <= P2)
+                    hist_add(hist, (int)((kk - P1) >> sh), colq[i]);
+            }
+            Sb = warp_sum_i64(Sb);
+            __syncwarp();
+            const int r1 = P1 == lo0 ? 0 : dc.cond(Sb, (P1 - 1) >= CK0);
+            if (r1 < 0) return SEL_SLOW_BAND;
+            if (r1 == 1) {
+                hi0 = P1 - 1;
+                P1 = lo0;
+                P2 = hi0;
+                continue;
+            }
+            int64_t below = 0;
+            const int bs = hist_cross(hist, nbins, P1, P2, sh, Sb, dc, &below, lane);
+            __syncwarp();
+            if (bs == -2) return SEL_SLOW_BAND;
+            if (bs < 0) {
+                if (P2 >= hi0) return SEL_INTERNAL;
+                lo0 = P2 + 1;
+                P1 = lo0;
+                P2 = hi0;
+                continue;
+            }
+            const uint32_t K1 = P1 + ((uint32_t)bs << sh);
+            const uint32_t K2 = min(P2, K1 + bmask);
+            lo0 = K1;
+            hi0 = K2;
+            P1 = K1;
+            P2 = K2;
+            sampled = false;
+            count_pass = false;
+            if (K1 == K2) {  // one coarse key holds the median
+                if (sizeof(T) == 4) {
+                    tstar = (K)K1;
+                    return SEL_OK;
+                }
+                return SEL_SLOW_CAP;  // double: its exact keys are not known here
+            }
+            continue;
+        }
+        // one pass over all rows: exact weight of rows certainly below P1; rows
+        // whose approximate key is within G of [P1, P2] become candidates
+        const uint32_t bt = sat_sub(P1, G);  // certain below: key' < bt
+        const uint32_t at = sat_add(P2, G);  // certain above: key' > at
+        int64_t Sb = 0;
+        cnt = 0;
+        // rows are visited in batches of 4 per lane; the global loads of the next
+        // batch are issued before the current one is classified, so the L2
+        // latency overlaps the work
+        constexpr int U = 4;
+        T an[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = u * 32 + lane;
+            an[u] = i < n ? xk[i] : T(0);
+        }
+        for (int i0 = 0; i0 < n; i0 += 32 * U) {
+            T ac[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) ac[u] = an[u];
+            if (i0 + 32 * U < n) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int i = i0 + 32 * U + u * 32 + lane;
+                    an[u] = i < n ? xk[i] : T(0);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                // branch-free; rows past n are clamped to a readable slot and masked
+                const int i = i0 + u * 32 + lane;
+                const int ic = min(i, npad_m1);
+                const float iv = inv[ic];
+                const uint32_t kk = akey(__fmul_rn(A::a32(ac[u]), iv));
+                const bool valid = i < n && iv != 0.0f;
+                const bool below = valid && kk < bt;
+                const bool cand = valid && !below && kk <= at;
+                const int64_t q = colq[ic];
+                Sb += below ? q : 0;
+                // speculative store: the slot is only kept when cnt advances
+                if (cnt < qt) {
+                    lk[cnt * 32 + lane] = kk;
+                    li[cnt * 32 + lane] = (uint16_t)ic;
+                }
+                cnt += cand ? 1 : 0;
+            }
+        }
+        Sb = warp_sum_i64(Sb);
+        __syncwarp();
+        if (__any_sync(FULL, cnt > qt)) {  // a lane overflowed: narrow by a count pass
+            if (P1 == P2) return SEL_SLOW_CAP;
+            count_pass = true;
+            continue;
+        }
+        // exact histogram of the candidates over [P1, P2]; rows near P1, P2 or a
+        // bin edge are divided exactly first; Sb2 = exact weight below P1
+        const uint32_t span = P2 - P1;
+        const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
+        const uint32_t bmask = (1u << sh) - 1u;
+        const int nbins = (int)(span >> sh) + 1;
+        const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
+        hist_zero(hist, lane);
+        __syncwarp();
+        int64_t Sb2 = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            uint32_t kk = lk[p];
+            const uint16_t id = li[p];
+            const uint32_t off = (kk - P1) & bmask;
+            const bool clear = kk >= g1 && kk <= g2 && off >= G && off + G <= bmask;
+            if (!clear) {
+                kk = A::exact_ck(xk[id], colb[id]);
+                lk[p] = kk;
+                li[p] = id | EXACT_BIT;
+            }
+            const int64_t q = colq[id];
+            if (kk < P1)
+                Sb2 += q;
+            else if (kk <= P2)
+                hist_add(hist, (int)((kk - P1) >> sh), q);
+        }
+        Sb += warp_sum_i64(Sb2);
+        __syncwarp();
+        const int r1 = P1 == lo0 ? 0 : dc.cond(Sb, (P1 - 1) >= CK0);
+        if (r1 < 0) return SEL_SLOW_BAND;
+        if (r1 == 1) {  // median below P1: retry under P1
+            hi0 = P1 - 1;
+            P2 = hi0;
+            P1 = sampled ? pick(jx - 3 * max(d0, 1) - 1, lo0) : lo0;
+            if (P1 > P2) P1 = lo0;
+            continue;
+        }
+        int64_t below = 0;
+        const int bs = hist_cross(hist, nbins, P1, P2, sh, Sb, dc, &below, lane);
+        __syncwarp();
+        if (bs == -2) return SEL_SLOW_BAND;
+        if (bs < 0) {  // median above P2: retry over P2
+            if (P2 >= hi0) return SEL_INTERNAL;
+            lo0 = P2 + 1;
+            P1 = lo0;
+            P2 = sampled ? pick(jx + 3 * max(d0, 1) + 1, hi0) : hi0;
+            if (P2 < P1) P2 = hi0;
+            continue;
+        }
+        // the median is in bin bs: keep its candidates (lane-local, in place)
+        const uint32_t K1 = P1 + ((uint32_t)bs << sh);
+        const uint32_t K2 = min(P2, K1 + bmask);
+        int w = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            const uint32_t kk = lk[p];
+            const uint16_t id = li[p];
+            lk[w * 32 + lane] = kk;  // w <= j: kept only if w advances
+            li[w * 32 + lane] = id;
+            w += (kk >= K1 && kk <= K2) ? 1 : 0;
+        }
+        __syncwarp();
+        cnt = w;
+        L = below;
+        lo = K1;
+        hi = K2;
+        placed = true;
+    }
+    if (!placed) return SEL_SLOW_TRIES;
+
+    // ---------------- levels on the candidate list: exact histograms ------
+    int c = __reduce_add_sync(FULL, cnt);
+    for (int level = 0; c > 31 && lo < hi; ++level) {
+        if (level >= 8) return SEL_SLOW_LEVELS;
+        const uint32_t span = hi - lo;
+        const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
+        const uint32_t bmask = (1u << sh) - 1u;
+        const int nbins = (int)(span >> sh) + 1;
+        hist_zero(hist, lane);
+        __syncwarp();
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            uint32_t kk = lk[p];
+            uint16_t id = li[p];
+            const uint32_t off = (kk - lo) & bmask;
+            if (!(id & EXACT_BIT) && (off < G || off + G > bmask)) {
+                const int row = id & ROW_MASK;
+                kk = A::exact_ck(xk[row], colb[row]);
+                lk[p] = kk;
+                id = (uint16_t)row | EXACT_BIT;
+                li[p] = id;
+            }
+            hist_add(hist, (int)((kk - lo) >> sh), colq[id & ROW_MASK]);
+        }
+        __syncwarp();
+        int64_t below = 0;
+        const int bs = hist_cross(hist, nbins, lo, hi, sh, L, dc, &below, lane);
+        __syncwarp();
+        if (bs == -2) return SEL_SLOW_BAND;
+        if (bs < 0) return SEL_INTERNAL;
+        const uint32_t K1 = lo + ((uint32_t)bs << sh);
+        const uint32_t K2 = min(hi, K1 + bmask);
+        int w = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int p = j * 32 + lane;
+            const uint32_t kk = lk[p];
+            const uint16_t id = li[p];
+            lk[w * 32 + lane] = kk;
+            li[w * 32 + lane] = id;
+            w += (kk >= K1 && kk <= K2) ? 1 : 0;
+        }
+        __syncwarp();
+        cnt = w;
+        L = below;
+        lo = K1;
+        hi = K2;
+        c = __reduce_add_sync(FULL, cnt);
+    }
+
+    // ---------------- final: exact keys of the candidates ------------------
+    if (sizeof(T) == 4 && lo == hi) {  // coarse keys are the exact keys for float
+        tstar = (K)lo;
+        return SEL_OK;
+    }
+    if (c > 31) {  // one coarse key left, many rows: all exact keys equal?
+        K kmin = Tr::NONE, kmax = 0;
+        for (int j = 0; j < cnt; ++j) {
+            const int row = li[j * 32 + lane] & ROW_MASK;
+            const K ke = Tr::key(Tr::div_rn(xk[row], colb[row]));
+            kmin = min(kmin, ke);
+            kmax = max(kmax, ke);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
+            kmax = max(kmax, __shfl_xor_sync(FULL, kmax, o));
+        }
+        const bool zero_in = lo <= CK0 && CK0 <= hi;
+        if (kmin == kmax && !(zero_in && kmin != Tr::KEY0)) {
+            tstar = kmin;
+            return SEL_OK;
+        }
+        return SEL_SLOW_TIE;
+    }
+    // gather the <= 31 candidate rows into lanes 0..c-1 (via the histogram buffer)
+    {
+        const int excl = warp_scan_add(cnt, lane) - cnt;
+        uint16_t *stage = reinterpret_cast<uint16_t *>(hist);
+        for (int j = 0; j < cnt; ++j) stage[excl + j] = li[j * 32 + lane] & ROW_MASK;
+    }
+    __syncwarp();
+    K fk = Tr::NONE;
+    int64_t fq = 0;
+    if (lane < c) {
+        const int row = reinterpret_cast<const uint16_t *>(hist)[lane];
+        fk = Tr::key(Tr::div_rn(xk[row], colb[row]));
+        fq = colq[row];
+    } else if (lane == c && lo <= CK0 && CK0 <= hi) {
+        fk = Tr::KEY0;
+        fq = 0;
+    }
+    __syncwarp();
+    warp_sort32(fk, fq, lane);
+    const int64_t P = warp_scan_add(fq, lane);
+    const K nxt = __shfl_down_sync(FULL, fk, 1);
+    const bool last = (lane == 31) || (nxt != fk);
+    int r = -2;
+    if (last && fk != Tr::NONE) r = dc.cond(L + P, fk >= Tr::KEY0);
+    const unsigned okm = __ballot_sync(FULL, r == 1);
+    const unsigned unm = __ballot_sync(FULL, r == -1);
+    const unsigned any = okm | unm;
+    if (!any) return SEL_INTERNAL;
+    const int first = __ffs(any) - 1;
+    if ((unm >> first) & 1u) return SEL_SLOW_BAND;
+    tstar = __shfl_sync(FULL, fk, first);
+    return SEL_OK;
+}
+
+// The lambdas of one launch (or of one instance of a batch).
+struct LamView {
+    const double *lam;
+    int tl_min, tl_max;  // positions of the smallest and largest lambda
+};
+
+// Everything one warp needs to solve the pairs of its CTA's column jhat.
+template <typename T> struct WarpCtx {
+    const T *colb;
+    const float *inv;
+    const int64_t *colq;
+    const uint16_t *samp;
+    uint32_t *lk;
+    uint16_t *li;
+    uint32_t *hist;
+    const Decide *s_dec;  // per-lambda thresholds for the first NDEC lambdas
+    int qt, n;
+    ColInfo cinfo;
+};
+constexpr int NDEC = 32;
+
+template <typename T>
+__device__ __forceinline__ Decide decide_for(const WarpCtx<T> &w, const LamView &lp, int tl) {
+    Decide dc;
+    if (tl < NDEC)
+        dc = w.s_dec[tl];
+    else
+        dc.init(w.cinfo, lp.lam[tl]);
+    return dc;
+}
+
+// Writes v and s of (lambda t0+tl, jhat, k), or lists the pair for the exact path.
+template <typename T>
+__device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int st,
+                          typename Traits<T>::K ts, const T *xk, const T *colb, int n,
+                          double lam, int lane) {
+    using Tr = Traits<T>;
+    const int64_t m = a.m;
+    const int64_t o = ((int64_t)t * m + j) * m + k;
+    if (st >= SEL_SLOW) {
+        if (lane == 0) {
+            uint32_t slot = atomicAdd(a.slow_count, 1u);
+            SlowEntry e;
+            e.t = t;
+            e.j = (int32_t)j;
+            e.k = (int32_t)k;
+            e.inst = (int16_t)a.inst;
+            e.reason = (int16_t)st;
+            a.slow[slot] = e;
+        }
+        return;
+    }
+    if (st == SEL_INTERNAL) {
+        if (lane == 0) {
+            atomicOr(a.status, ST_INTERNAL);
+            a.v_all[o] = T(NAN);
+            a.s_all[o] = NAN;
+        }
+        return;
+    }
+    const T v = Tr::value(ts);
+    const T res = warp_residual<T>(xk, colb, n, v, lane);
+    if (lane == 0) {
+        a.v_all[o] = v;
+        a.s_all[o] = (double)res + lam * (double)fabs(v);
+    }
+}
+
+// One lambda of one pair: the full selection.
+template <typename T>
+__device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int tl, int64_t j,
+                          int64_t k, const T *xk, const WarpCtx<T> &w, bool slow_pair,
+                          int lane) {
+    using Tr = Traits<T>;
+    typename Tr::K ts = Tr::KEY0;
+    int st = SEL_OK;
+    if (slow_pair) {
+        st = SEL_SLOW;
+    } else if (w.cinfo.n_valid > 0) {
+        const Decide dc = decide_for(w, lp, tl);
+        st = select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, dc,
+                          ts, lane);
+    }
+    emit_pair<T>(a, t0 + tl, j, k, st, ts, xk, w.colb, w.n, lp.lam[tl], lane);
+}
+
+// Lambda batch (step A7).  The weighted median moves monotonically toward 0
+// as lambda grows (the penalty point only gains weight), so every lambda's
+// median lies between those of the smallest and the largest lambda.  Solve
+// those two fully, collect the rows whose exact keys lie between them (one
+// pass, exact divisions only near the bounds) together with the exact weight
+// below, and decide every lambda from one sort and prefix scan of those rows.
+// Returns false (nothing written) when more than 31 rows lie between.
+template <typename T>
+__device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int nlc, int64_t j,
+                            int64_t k, const T *__restrict__ xk, const WarpCtx<T> &w, int lane) {
+    using Tr = Traits<T>;
+    using K = typename Tr::K;
+    using A = Approx<T>;
+    constexpr uint32_t G = A::G;
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int n = w.n;
+    K Ka = Tr::KEY0, Kb = Tr::KEY0;
+    {
+        const Decide da = decide_for(w, lp, lp.tl_min);
+        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, da, Ka,
+                         lane) != SEL_OK)
+            return false;
+        const Decide db = decide_for(w, lp, lp.tl_max);
+        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, db, Kb,
+                         lane) != SEL_OK)
+            return false;
+    }
+    const K Klo = min(Ka, Kb), Khi = max(Ka, Kb);
+    const uint32_t cl = ckey((float)Tr::value(Klo)), ch = ckey((float)Tr::value(Khi));
+    const uint32_t bt = sat_sub(cl, G), at = sat_add(ch, G);
+    int64_t Sb = 0;  // exact weight of rows with key < Klo
+    int cnt = 0;
+    uint16_t *stage = reinterpret_cast<uint16_t *>(w.hist);
+    int c = 0;
+    constexpr int U = 4;  // loads of the next batch in flight while this one is classified
+    T an[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int i = u * 32 + lane;
+        an[u] = i < n ? xk[i] : T(0);
+    }
+    for (int i0 = 0; i0 < n; i0 += 32 * U) {
+        T ac[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) ac[u] = an[u];
+        if (i0 + 32 * U < n) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + 32 * U + u * 32 + lane;
+                an[u] = i < n ? xk[i] : T(0);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = i0 + u * 32 + lane;
+            bool take = false;
+            if (i < n) {
+                const float iv = w.inv[i];
+                if (iv != 0.0f) {
+                    const uint32_t kk = akey(__fmul_rn(A::a32(ac[u]), iv));
+                    if (kk < bt) {
+                        Sb += w.colq[i];
+                    } else if (kk <= at) {
+                        const K ke = Tr::key(Tr::div_rn(ac[u], w.colb[i]));
+                        if (ke < Klo)
+                            Sb += w.colq[i];
+                        else if (ke <= Khi)
+                            take = true;
+                    }
+                }
+            }
+            const unsigned msk = __ballot_sync(FULL, take);
+            if (take) {
+                const int pos = c + __popc(msk & ((1u << lane) - 1u));
+                if (pos < 31) stage[pos] = (uint16_t)i;
+            }
+            c += __popc(msk);
+            cnt += take ? 1 : 0;
+        }
+    }
+    (void)cnt;
+    Sb = warp_sum_i64(Sb);
+    __syncwarp();
+    if (c > 31) return false;
+    K fk = Tr::NONE;
+    int64_t fq = 0;
+    if (lane < c) {
+        const int row = stage[lane];
+        fk = Tr::key(Tr::div_rn(xk[row], w.colb[row]));
+        fq = w.colq[row];
+    } else if (lane == c && Klo <= Tr::KEY0 && Tr::KEY0 <= Khi) {
+        fk = Tr::KEY0;
+    }
+    __syncwarp();
+    warp_sort32(fk, fq, lane);
+    const int64_t P = warp_scan_add(fq, lane);
+    const K nxt = __shfl_down_sync(FULL, fk, 1);
+    const bool last = (lane == 31) || (nxt != fk);
+    K prev = Tr::NONE;
+    T prev_res = T(0);
+    for (int tl = 0; tl < nlc; ++tl) {
+        const Decide dc = decide_for(w, lp, tl);
+        int r = -2;
+        if (last && fk != Tr::NONE) r = dc.cond(Sb + P, fk >= Tr::KEY0);
+        const unsigned okm = __ballot_sync(FULL, r == 1);
+        const unsigned unm = __ballot_sync(FULL, r == -1);
+        const unsigned any = okm | unm;
+        const int first = any ? __ffs(any) - 1 : 0;
+        if (!any || ((unm >> first) & 1u)) {  // undecided here: full selection
+            solve_one<T>(a, lp, t0, tl, j, k, xk, w, false, lane);
+            prev = Tr::NONE;
+            continue;
+        }
+        const K ts = __shfl_sync(FULL, fk, first);
+        const T v = Tr::value(ts);
+        if (ts != prev) {
+            prev_res = warp_residual<T>(xk, w.colb, n, v, lane);
+            prev = ts;
+        }
+        if (lane == 0) {
+            const int64_t o = ((int64_t)(t0 + tl) * a.m + j) * a.m + k;
+            a.v_all[o] = v;
+            a.s_all[o] = (double)prev_res + lp.lam[tl] * (double)fabs(v);
+        }
+    }
+    return true;
+}
+
+// One work unit: column jhat = j of an instance and the k in [k0, k1), all
+// lambdas of the launch.  Called by every thread of a CTA; `smem` is laid out
+// for lay_npad rows (column arrays, then one candidate list per warp).
+template <typename T, bool MULTI>
+__device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int nlc, int j,
+                           int64_t k0, int64_t k1, int cap, int lay_npad, unsigned char *smem,
+                           Decide *s_dec) {
+    using Tr = Traits<T>;
+    using K = typename Tr::K;
+    const int n = (int)a.n;
+    const int64_t m = a.m, ldn = a.ldn;
+    const int npad = lay_npad;  // shared-memory layout stride (>= n rounded up to 32)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+
+    T *colb = reinterpret_cast<T *>(smem);
+    size_t off = al16((size_t)npad * sizeof(T));
+    float *inv = reinterpret_cast<float *>(smem + off);
+    off += al16((size_t)npad * 4);
+    int64_t *colq = reinterpret_cast<int64_t *>(smem + off);
+    off += al16((size_t)npad * 8);
+    uint16_t *samp = reinterpret_cast<uint16_t *>(smem + off);
+    unsigned char *wbase =
+        smem + PairSmem<T>::col_bytes(npad) + (size_t)warp * PairSmem<T>::warp_bytes(cap);
+    uint32_t *lk = reinterpret_cast<uint32_t *>(wbase);
+    uint16_t *li = reinterpret_cast<uint16_t *>(wbase + al16((size_t)cap * 4));
+    uint32_t *hist = reinterpret_cast<uint32_t *>(wbase + al16((size_t)cap * 4) +
+                                                  al16((size_t)cap * 2));
+    // prologue scratch: the first 256 bytes of warp 0's candidate list
+    long long *s_wsum = reinterpret_cast<long long *>(smem + PairSmem<T>::col_bytes(npad));
+
+    const ColInfo cinfo = a.ci[j];
+    const T *xj = a.Xt + (int64_t)j * ldn;
+    for (int i = threadIdx.x; i < npad; i += blockDim.x) {
+        const T b = i < n ? xj[i] : T(0);
+        colb[i] = b;
+        inv[i] = b != T(0) ? Approx<T>::inv_of(b) : 0.0f;
+        int e = 0;
+        colq[i] = b != T(0) ? fixq(b < T(0) ? -b : b, cinfo.sigma, e) : 0;
+    }
+    for (int q = threadIdx.x; q < NSAMP; q += blockDim.x) samp[q] = 0;  // always a valid row
+    __syncthreads();
+    // Systematic weight-proportional sample of the rows of column jhat: sample
+    // s is the row whose cumulative weight interval contains (s + 1/2) Q / 64.
+    if (cinfo.n_valid > 0) {
+        const int nt = blockDim.x;
+        const int chunk = (n + nt - 1) / nt;
+        const int r0 = min(n, threadIdx.x * chunk), r1 = min(n, r0 + chunk);
+        long long mine = 0;
+        for (int r = r0; r < r1; ++r) mine += colq[r];
+        long long incl = warp_scan_add(mine, lane);
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        long long before = incl - mine;
+        for (int w = 0; w < warp; ++w) before += s_wsum[w];
+        const double per = (double)NSAMP / (double)cinfo.Q;
+        for (int r = r0; r < r1; ++r) {
+            const long long after = before + colq[r];
+            const double x0 = (double)before * per - 0.5, x1 = (double)after * per - 0.5;
+            int s0 = (int)floor(x0) + 1, s1 = (int)floor(x1);
+            s0 = max(s0, 0);
+            s1 = min(s1, NSAMP - 1);
+            for (int sidx = s0; sidx <= s1; ++sidx) samp[sidx] = (uint16_t)r;
+            before = after;
+        }
+        __syncthreads();
+    }
+    // per-lambda thresholds of the exact test depend on (jhat, lambda) only
+    for (int tl = threadIdx.x; tl < min(nlc, NDEC); tl += blockDim.x) s_dec[tl].init(cinfo, lp.lam[tl]);
+    __syncthreads();
+    WarpCtx<T> wc;
+    wc.colb = colb;
+    wc.inv = inv;
+    wc.colq = colq;
+    wc.samp = samp;
+    wc.lk = lk;
+    wc.li = li;
+    wc.hist = hist;
+    wc.s_dec = s_dec;
+    wc.qt = cap / 32;
+    wc.n = n;
+    wc.cinfo = cinfo;
+
+    const bool jwide = (cinfo.flags & COL_WIDE) != 0;
+    for (int64_t k = k0 + warp; k < k1; k += nw) {
+        if (k == j) {  // v_jhat = 1: zero residual, penalty lambda * 1
+            for (int tl = lane; tl < nlc; tl += 32) {
+                int64_t o = ((int64_t)(t0 + tl) * m + j) * m + k;
+                a.v_all[o] = T(1);
+                a.s_all[o] = lp.lam[tl];
+            }
+            continue;
+        }
+        const T *xk = a.Xt + k * ldn;
+        const bool slow_pair = a.force_exact || jwide ||
+                               (sizeof(T) == 8 && (a.ci[k].flags & COL_WIDE));
+        if (MULTI && nlc >= 3 && !slow_pair && cinfo.n_valid > 0 &&
+            lambda_path<T>(a, lp, t0, nlc, j, k, xk, wc, lane)) {
+            __syncwarp();
+            continue;
+        }
+        for (int tl = 0; tl < nlc; ++tl) solve_one<T>(a, lp, t0, tl, j, k, xk, wc, slow_pair, lane);
+        __syncwarp();
+    }
+    __syncthreads();  // the CTA may stage another column next
+}
+
+}  // namespace l1l

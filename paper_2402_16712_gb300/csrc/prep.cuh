@@ -1,0 +1,115 @@
+// prep.cuh -- step A1 (staging) bodies shared by the single-instance and
+// batched kernels: column-major copy of X with the non-finite check, and the
+// per-column fixed-point statistics of the exact weighted-median decisions.
+#pragma once
+#include "common.cuh"
+
+namespace l1l {
+
+// X (n x m, row-major, rows = points) -> Xt (m x ldn, column-major, rows
+// n..ldn-1 zero).  32x32 tiles through shared memory so both the read and the
+// write are coalesced.  Any NaN/inf sets ST_NONFINITE.
+template <typename T>
+__device__ __forceinline__ void transpose_tile(const T *__restrict__ X, T *__restrict__ Xt,
+                                               int64_t n, int64_t m, int64_t ldn,
+                                               uint32_t *status, int64_t tile_c, int64_t tile_r) {
+    __shared__ T tile[32][33];
+    const int64_t c0 = tile_c * 32;  // column of X
+    const int64_t r0 = tile_r * 32;  // row of X
+    const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int64_t r = r0 + ty + 8 * q, c = c0 + tx;
+        T v = 0;
+        if (r < n && c < m) {
+            v = X[r * m + c];
+            bad |= !isfinite(v);
+        }
+        tile[ty + 8 * q][tx] = v;
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && tx == 0) atomicOr(status, ST_NONFINITE);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int64_t c = c0 + ty + 8 * q, r = r0 + tx;
+        if (c < m && r < ldn) Xt[c * ldn + r] = tile[tx][ty + 8 * q];
+    }
+}
+
+template <typename T> __device__ __forceinline__ T absval(T x) { return x < T(0) ? -x : x; }
+
+// One block per column jhat: n_valid, sigma (from the largest |x_ijhat|), the
+// fixed-point total Q and the number of truncated weights.
+template <typename T>
+__device__ __forceinline__ void colprep_column(const T *__restrict__ col, ColInfo *out, int64_t n) {
+    __shared__ int s_max[8];
+    __shared__ int s_min[8];
+    __shared__ int s_cnt[8];
+    __shared__ long long s_q[8];
+    __shared__ int s_inx[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    int emax = -100000, emin = 100000, cnt = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        T b = col[i];
+        if (b != T(0)) {
+            cnt++;
+            const int e = ilog2_pos(b);
+            emax = max(emax, e);
+            emin = min(emin, e);
+        }
+    }
+    cnt = __reduce_add_sync(0xFFFFFFFFu, cnt);
+    emax = __reduce_max_sync(0xFFFFFFFFu, emax);
+    emin = __reduce_min_sync(0xFFFFFFFFu, emin);
+    if (lane == 0) {
+        s_max[warp] = emax;
+        s_min[warp] = emin;
+        s_cnt[warp] = cnt;
+    }
+    __syncthreads();
+    int nv = 0, E = -100000, Emin = 100000;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        nv += s_cnt[w];
+        E = max(E, s_max[w]);
+        Emin = min(Emin, s_min[w]);
+    }
+    const int Lbits = nv > 0 ? 32 - __clz(nv) : 0;
+    const int sigma = nv > 0 ? 60 - E - Lbits : 0;
+
+    long long q = 0;
+    int inx = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        T b = col[i];
+        if (b != T(0)) {
+            int e = 0;
+            q += fixq(absval(b), sigma, e);
+            inx += e;
+        }
+    }
+    q = warp_sum_i64(q);
+    inx = __reduce_add_sync(0xFFFFFFFFu, inx);
+    if (lane == 0) {
+        s_q[warp] = q;
+        s_inx[warp] = inx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long Q = 0;
+        int I = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            Q += s_q[w];
+            I += s_inx[w];
+        }
+        ColInfo c;
+        c.Q = Q;
+        c.sigma = sigma;
+        c.n_valid = nv;
+        c.n_inexact = I;
+        c.flags = (nv > 0 && (Emin < WideRange<T>::lo || E > WideRange<T>::hi)) ? COL_WIDE : 0;
+        *out = c;
+    }
+}
+
+}  // namespace l1l

@@ -37,6 +37,9 @@ SIGNATURES = {
     "l1line_last_launch_count": (_I, []),
     "l1line_profile_events": (_I, [_P, _P]),
     "l1line_fit_noalloc_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P]),
+    "l1line_batched_workspace_bytes": (_SZ, [_I, _I64, _P, _P, _P]),
+    "l1line_fit_batched_f32": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_fit_batched_f64": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
 }
 NOALLOC_SCRATCH_BYTES = 32 << 20  # L1L_NOALLOC_SCRATCH_BYTES in include/l1line.h
 
@@ -188,3 +191,64 @@ def profile_events(start=None, stop=None) -> None:
     else:
         load().l1line_profile_events(ctypes.c_void_p(start.cuda_event),
                                      ctypes.c_void_p(stop.cuda_event))
+
+
+class Batched:
+    """A batch of independent fits (`l1line_fit_batched_*`), set up once and run
+    any number of times (e.g. inside a torch.cuda.CUDAGraph capture after one
+    warm-up run).  Xs: list of contiguous CUDA tensors (same dtype), lambdas:
+    list of 1-D sequences, one per instance."""
+
+    def __init__(self, Xs, lambdas, device=None):
+        import torch
+        if len(Xs) != len(lambdas) or not Xs:
+            raise ValueError("one lambda list per instance")
+        for X in Xs:
+            _check_x(X)
+        self.dtype = Xs[0].dtype
+        if any(X.dtype != self.dtype for X in Xs):
+            raise TypeError("all instances must share a dtype")
+        device = device or Xs[0].device
+        self.Xs = list(Xs)
+        self.ns = np.array([X.shape[0] for X in Xs], dtype=np.int64)
+        self.ms = np.array([X.shape[1] for X in Xs], dtype=np.int64)
+        lams = [_lams(l) for l in lambdas]
+        self.nl = np.array([l.size for l in lams], dtype=np.int64)
+        self.loff = np.concatenate([[0], np.cumsum(self.nl)]).astype(np.int64)
+        self.lam = np.ascontiguousarray(np.concatenate(lams), dtype=np.float64)
+        self.xptr = np.array([X.data_ptr() for X in Xs], dtype=np.uint64)
+        nb = int(load().l1line_batched_workspace_bytes(
+            _dt(self.dtype), len(Xs), self.ns.ctypes.data_as(ctypes.c_void_p),
+            self.ms.ctypes.data_as(ctypes.c_void_p), self.loff.ctypes.data_as(ctypes.c_void_p)))
+        if nb == 0:
+            raise L1LineError(ERR_UNSUPPORTED, "l1line_batched_workspace_bytes")
+        self.ws = Workspace(nb, device)
+        vlen = int((self.nl * self.ms).sum())
+        self.out_v = torch.empty(vlen, dtype=self.dtype, device=device)
+        self.out_obj = torch.empty(int(self.nl.sum()), dtype=torch.float64, device=device)
+        self.out_jstar = torch.empty(int(self.nl.sum()), dtype=torch.int32, device=device)
+
+    def run(self, stream=None):
+        import torch
+        f = (load().l1line_fit_batched_f32 if self.dtype == torch.float32
+             else load().l1line_fit_batched_f64)
+        P = ctypes.c_void_p
+        rc = f(len(self.Xs), self.xptr.ctypes.data_as(P), self.ns.ctypes.data_as(P),
+               self.ms.ctypes.data_as(P), self.lam.ctypes.data_as(P), self.loff.ctypes.data_as(P),
+               self.out_v.data_ptr(), self.out_obj.data_ptr(), self.out_jstar.data_ptr(),
+               P(self.ws.ptr), self.ws.nbytes, _stream_ptr(stream))
+        if rc != OK:
+            raise L1LineError(rc, "l1line_fit_batched")
+
+    def results(self):
+        """Per instance: (v [nl, m], obj [nl], jstar [nl]) views of the outputs."""
+        out, vo = [], 0
+        for b in range(len(self.Xs)):
+            nl, m, t0 = int(self.nl[b]), int(self.ms[b]), int(self.loff[b])
+            out.append((self.out_v[vo:vo + nl * m].view(nl, m), self.out_obj[t0:t0 + nl],
+                        self.out_jstar[t0:t0 + nl]))
+            vo += nl * m
+        return out
+
+    def status(self, stream=None) -> int:
+        return status(self.ws, stream)

@@ -92,3 +92,27 @@ def test_binding_has_no_cpu_fallback(tmp_path):
             l1line.load(str(tmp_path / "missing.so"))
         finally:
             l1line._lib = saved
+
+
+def test_batched_argument_errors(lib):
+    I = np.array
+    P = ctypes.c_void_p
+    ns, ms = I([10, 20], dtype=np.int64), I([3, 4], dtype=np.int64)
+    loff = I([0, 1, 3], dtype=np.int64)
+    f = lib.l1line_batched_workspace_bytes
+    ok = f(0, 2, ns.ctypes.data_as(P), ms.ctypes.data_as(P), loff.ctypes.data_as(P))
+    assert ok > 0
+    bad = I([1, 1, 3], dtype=np.int64)  # must start at 0
+    assert f(0, 2, ns.ctypes.data_as(P), ms.ctypes.data_as(P), bad.ctypes.data_as(P)) == 0
+    empty = I([0, 0, 3], dtype=np.int64)  # an instance without lambdas
+    assert f(0, 2, ns.ctypes.data_as(P), ms.ctypes.data_as(P), empty.ctypes.data_as(P)) == 0
+    big = np.zeros(258, dtype=np.int64) + 4
+    offs = np.arange(258, dtype=np.int64)
+    assert f(0, 257, big.ctypes.data_as(P), big.ctypes.data_as(P), offs.ctypes.data_as(P)) == 0
+    lam = I([0.1, -1.0, 0.2])
+    xp = I([256, 512], dtype=np.uint64)
+    rc = lib.l1line_fit_batched_f32(2, xp.ctypes.data_as(P), ns.ctypes.data_as(P),
+                                    ms.ctypes.data_as(P), lam.ctypes.data_as(P),
+                                    loff.ctypes.data_as(P), P(256), P(256), P(256), P(1024),
+                                    1 << 30, None)
+    assert rc == l1line.ERR_ARG  # negative lambda
