@@ -52,7 +52,7 @@ def _env_rank():
 
 def _src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("k_pairs.cu", "common.cuh"):
+    for f in ("k_pairs.cu", "pairs.cuh", "common.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2402_16712_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -298,6 +298,8 @@ def run_gpu(args):
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     d2h = vh.numel() * 4 + 8 + 4
 
+    extras = {} if args.no_extras else measure_extras(dev, stream, flush)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
@@ -318,7 +320,7 @@ def run_gpu(args):
         "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": _profile_traffic(),
-                     "kernel": "k_pairs<float>", "kernel_ms": kms,
+                     "kernel": "k_pairs<float,false>", "kernel_ms": kms,
                      "basis": f"{ALG_INSTR_PER_ELEM} lane-instructions per (pair,row) element; "
                               f"peak = {SMS} SMs x {LANES_PER_SM_CLK} lanes x {SM_MAX_MHZ:.0f} MHz"},
         "e2e": {"value": pairs / (e2e_ms * 1e-3), "unit": UNIT,
@@ -326,6 +328,7 @@ def run_gpu(args):
         "gpu_launches": launches_per_fit * args.steps,
         "clocks": clocks,
     }
+    line.update(extras)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(X, float(lams[0])).items()
                                 if k in ("value", "unit", "cores", "kind", "sample")}
@@ -333,6 +336,81 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def _replay_ms(g, stream, steps, flush=None):
+    """Mean device time of `steps` replays of graph g on `stream` (events per
+    replay; L2 flushed before each when `flush` is given)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            g.replay()
+        for a, b in ev:
+            if flush is not None:
+                flush.fill_(1)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+    stream.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def measure_extras(dev, stream, flush):
+    """The lambda-path and uneven-batch workloads, each captured once into a
+    CUDA graph and replayed (reported beside the headline, not in `value`)."""
+    import numpy as np
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+    out = {}
+    # lambda path: n=1000, m=500 float32, 32 lambdas in one fit
+    X, lams, _ = datagen.lambda_path("float32")
+    n, m = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    ws = l1line.Workspace.for_shape(torch.float32, n, m, lams.size, dev)
+    res = (torch.empty((lams.size, m), dtype=torch.float32, device=dev),
+           torch.empty(lams.size, dtype=torch.float64, device=dev),
+           torch.empty(lams.size, dtype=torch.int32, device=dev))
+    with torch.cuda.stream(stream):
+        l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
+    stream.synchronize()
+    launches = l1line.last_launch_count()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
+    ms = _replay_ms(g, stream, 10, flush)
+    if l1line.status(ws, stream) != l1line.OK:
+        raise SystemExit("lambda-path fit failed on the device")
+    pl = m * (m - 1) * lams.size
+    out["lambda_path"] = {
+        "workload": f"n={n}, m={m} float32, {lams.size} lambdas logspace(-3,1), one fit "
+                    "(one pair launch for all lambdas), CUDA graph replay, L2 flushed",
+        "ms_per_step": ms, "pair_lambdas_per_s": pl / (ms * 1e-3),
+        "fits_per_s": lams.size / (ms * 1e-3), "gpu_launches_per_step": launches}
+    del Xd, ws, res, g
+    # uneven batch: 256 instances, n~U[100,5000], m~U[10,500], lambda=0.2
+    batch = datagen.uneven_batch(256)
+    Xs = [torch.from_numpy(Xb).to(dev) for Xb, _ in batch]
+    bat = l1line.Batched(Xs, [lb for _, lb in batch], device=dev)
+    with torch.cuda.stream(stream):
+        bat.run(stream)
+    stream.synchronize()
+    launches = l1line.last_launch_count()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        bat.run(stream)
+    ms = _replay_ms(g, stream, 5)
+    if bat.status(stream) != l1line.OK:
+        raise SystemExit("batched fit failed on the device")
+    pairs = int(sum(int(Xb.shape[1]) * (int(Xb.shape[1]) - 1) for Xb, _ in batch))
+    out["uneven_batch"] = {
+        "workload": "256 float32 instances, n~U[100,5000], m~U[10,500], lambda=0.2, one "
+                    "persistent pair launch, CUDA graph replay (inputs 658 MB > L2)",
+        "ms_per_step": ms, "fits_per_s": len(batch) / (ms * 1e-3),
+        "pairs_per_s": pairs / (ms * 1e-3), "gpu_launches_per_step": launches}
+    return out
 
 
 def run_profile_case(args):
@@ -360,6 +438,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the lambda-path and uneven-batch lines")
     ap.add_argument("--profile-case", action="store_true",
                     help="run --fits plain fits of an n x m instance (for ncu), no timing")
     ap.add_argument("--n", type=int, default=N_ROWS)
