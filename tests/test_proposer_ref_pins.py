@@ -1,0 +1,139 @@
+"""Pins of the CPU reference of the learned proposer (oracle/proposer_ref.py)
+against facts that do not come from that file: finite differences, hand
+computed values, invariances and known binary16 roundings."""
+import numpy as np
+import pytest
+
+from oracle import proposer_ref as P
+
+
+def _theta(seed, scale=0.3):
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, scale, P.N_PARAMS)
+
+
+def test_parameter_count_and_pack_roundtrip():
+    assert P.N_PARAMS == 128 * 3 + 128 + 128 * 128 + 128 + 128 + 1 == 17153
+    th = _theta(0)
+    assert np.array_equal(P.pack(*P.unpack(th)), th)
+
+
+def test_forward_hand_built_network():
+    # unit 0 = relu(f0), unit 1 = relu(-f0), unit 2 = relu(f1 - 1): layer 2 passes
+    # them through and the output is |f0| + 2 relu(f1 - 1) - 0.5
+    W1 = np.zeros((128, 3)); b1 = np.zeros(128)
+    W1[0, 0], W1[1, 0], W1[2, 1], b1[2] = 1.0, -1.0, 1.0, -1.0
+    W2 = np.zeros((128, 128)); W2[0, 0] = W2[1, 1] = W2[2, 2] = 1.0
+    b2 = np.zeros(128)
+    w3 = np.zeros(128); w3[0] = w3[1] = 1.0; w3[2] = 2.0
+    th = P.pack(W1, b1, W2, b2, w3, -0.5)
+    F = np.array([[0.7, 3.0, 9.0], [-2.5, 0.2, -1.0], [0.0, 1.0, 0.0]])
+    want = np.abs(F[:, 0]) + 2 * np.maximum(F[:, 1] - 1.0, 0.0) - 0.5
+    assert np.allclose(P.forward(th, F), want, rtol=0, atol=1e-15)
+
+
+def test_backward_matches_central_differences():
+    rng = np.random.default_rng(1)
+    th = _theta(2)
+    F = rng.normal(size=(9, 3))
+    ds = rng.normal(size=9)
+    g = P.backward(th, F, ds)
+    f = lambda t: float(ds @ P.forward(t, F))
+    # every bias, w3 and b3 entry plus samples of both matrices
+    idx = list(range(384, 512)) + list(range(16896, 17153))
+    idx += list(rng.choice(384, 40, replace=False)) + list(384 + 128 + rng.choice(16384, 200, replace=False))
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(th); e[i] = h
+        fd = (f(th + e) - f(th - e)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_rank_loss_gradient_and_invariances():
+    rng = np.random.default_rng(3)
+    offs = np.array([0, 5, 5, 12, 20])  # one empty instance
+    s = rng.normal(size=20)
+    u = rng.normal(size=20)
+    L, ds = P.rank_loss(s, u, offs)
+    h = 1e-6
+    for i in range(20):
+        e = np.zeros(20); e[i] = h
+        fd = (P.rank_loss(s + e, u, offs)[0] - P.rank_loss(s - e, u, offs)[0]) / (2 * h)
+        assert abs(fd - ds[i]) < 1e-8
+    # adding a constant to one instance's scores changes nothing
+    s2 = s.copy(); s2[5:12] += 3.7
+    L2, ds2 = P.rank_loss(s2, u, offs)
+    assert abs(L2 - L) < 1e-12 and np.allclose(ds2, ds, atol=1e-14)
+    # scores equal to the targets: zero gradient, loss = mean entropy of q
+    L3, ds3 = P.rank_loss(u, u, offs)
+    assert np.allclose(ds3, 0.0, atol=1e-15)
+    ent = 0.0
+    for b in range(4):
+        q = np.exp(u[offs[b]:offs[b + 1]]); q /= max(q.sum(), 1e-300)
+        ent += -(q * np.log(q)).sum() if q.size else 0.0
+    assert abs(L3 - ent / 4) < 1e-12
+    # each non-empty instance's gradient sums to zero (softmax minus softmax)
+    for b in range(4):
+        assert abs(ds[offs[b]:offs[b + 1]].sum()) < 1e-15
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    rng = np.random.default_rng(4)
+    th = rng.normal(size=50)
+    g = rng.normal(size=50)
+    t1, m1, m2 = P.adam(th, g, np.zeros(50), np.zeros(50), 1, 0.01, eps=0.0)
+    assert np.allclose(t1, th - 0.01 * np.sign(g), rtol=0, atol=1e-15)
+    assert np.allclose(m1, 0.1 * g) and np.allclose(m2, 0.001 * g * g)
+
+
+def test_raw_features_hand_values():
+    X = np.array([[3.0, 0.0, -1.0],
+                  [-4.0, 0.0, 2.0],
+                  [0.0, 0.0, -5.0],
+                  [1.0, 0.0, 2.0]])
+    F = P.raw_features(X)
+    assert np.allclose(F[:, 0], [8.0, 0.0, 10.0])
+    assert np.allclose(F[:, 1], [np.sqrt(26.0), 0.0, np.sqrt(34.0)])
+    # lower median of 4 values: rank 1 of the sorted |x|
+    assert np.array_equal(F[:, 2], [1.0, 0.0, 2.0])
+    F5 = P.raw_features(np.array([[5.0], [-1.0], [3.0], [-2.0], [4.0]]))
+    assert F5[0, 2] == 3.0
+
+
+def test_standardise():
+    rng = np.random.default_rng(5)
+    F = rng.gamma(2.0, size=(40, 3))
+    F[:, 1] = 7.0  # constant feature
+    Z = P.standardise(F)
+    assert np.allclose(Z[:, [0, 2]].mean(axis=0), 0.0, atol=1e-12)
+    assert np.allclose(Z[:, [0, 2]].std(axis=0), 1.0, atol=1e-12)
+    assert np.array_equal(Z[:, 1], np.zeros(40))
+
+
+def test_half_rounding_known_values():
+    th = np.zeros(P.N_PARAMS)
+    th[0] = 1.0 / 3.0            # nearest binary16: 0.333251953125
+    th[1] = 1.0 + 2.0 ** -11     # exactly halfway: ties to even -> 1.0
+    th[2] = 1.0 + 3 * 2.0 ** -11  # halfway, ties to even -> 1 + 2^-9
+    th[3] = 65504.0              # largest finite binary16
+    th[384] = 1.0 / 3.0          # a bias: not rounded
+    r = P.half_weights(th)
+    assert r[0] == 0.333251953125 and r[1] == 1.0 and r[2] == 1.0 + 2.0 ** -9
+    assert r[3] == 65504.0 and r[384] == 1.0 / 3.0
+
+
+def test_topk_ties_and_nan():
+    s = np.array([0.5, 2.0, np.nan, 2.0, -1.0, 0.5, -np.inf])
+    assert list(P.topk(s, 1)) == [1]
+    assert list(P.topk(s, 2)) == [1, 3]
+    assert list(P.topk(s, 3)) == [0, 1, 3]
+    assert list(P.topk(s, 6)) == [0, 1, 3, 4, 5, 6]
+    assert list(P.topk(s, 7)) == [0, 1, 2, 3, 4, 5, 6]
+
+
+def test_target_logits():
+    z = np.array([5.0, 3.0, 9.0, 4.0, 3.5])
+    u = P.target_logits(z, temperature=0.5, top=3)
+    # z_min = 3, third smallest = 4: span 1
+    assert np.allclose(u, -(z - 3.0) / 0.5)
+    assert u[1] == 0.0 and u.argmax() == 1
