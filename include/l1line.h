@@ -119,8 +119,8 @@ int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                    void *workspace, size_t workspace_bytes, void *stream);
 
 /*
- * Batched fit (step A7 over independent instances; BASELINE's uneven-batch
- * workload): `batch` (1..256) independent problems, instance b with its own
+ * Batched fit (step A7 over independent instances of uneven size): `batch`
+ * (1..256) independent problems, instance b with its own
  * X_b (DEVICE pointer, row-major ns[b] x ms[b]) and lambdas
  * lambdas[lambda_offsets[b] .. lambda_offsets[b+1]) (HOST arrays; at most 512
  * lambdas in total, lambda_offsets[0] = 0).  Each instance is fitted exactly
@@ -148,6 +148,118 @@ int l1line_fit_batched_f64(int64_t batch, const double *const *Xs, const int64_t
                            const int64_t *lambda_offsets, double *out_v, double *out_obj,
                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                            void *stream);
+
+/*
+ * Subset fit: Algorithm 1 restricted to the candidate jhat listed in
+ * jhat_list (DEVICE int32[K], entries in [0, m); duplicates are allowed and
+ * scored once each).  Every k is still scanned for each listed jhat, so the
+ * scores z_jhat of the listed jhat are exactly those of l1line_fit_*, and the
+ * result is the listed jhat of smallest z (smallest index on ties).  Outputs
+ * as for l1line_fit_*.  Workspace: l1line_workspace_bytes(dtype, n, m,
+ * n_lambda).  An entry outside [0, m) is reported by l1line_status as
+ * L1L_ERR_ARG (the list lives on the device, so it is checked there).
+ */
+int l1line_fit_subset_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                          int64_t n_lambda, const int32_t *jhat_list, int64_t K,
+                          float *out_v, double *out_obj, int32_t *out_jstar,
+                          void *workspace, size_t workspace_bytes, void *stream);
+int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                          int64_t n_lambda, const int32_t *jhat_list, int64_t K,
+                          double *out_v, double *out_obj, int32_t *out_jstar,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Learned jhat proposer (not in the paper; an extension of Algorithm 1's
+ * outer loop): a small network scores every candidate jhat from three column
+ * features, and only the K best-scored candidates are fitted exactly (the
+ * exact objective still decides among them; the full scan stays the reference
+ * for its regret).
+ *
+ * Features of column jhat: its l1 norm, l2 norm and the lower median of
+ * |x_i,jhat| (0-based rank floor((n-1)/2) of the ascending order), each
+ * standardised over the m columns of the instance (mean 0, population
+ * standard deviation 1; a feature constant over the columns becomes 0).
+ * Stored as float [m][3].
+ *
+ * Network: 3 -> 128 -> 128 -> 1, ReLU after both hidden layers; weight
+ * matrices in binary16, biases in float, float arithmetic.  l1line_mlp is its
+ * packed DEVICE image (34,832 bytes, 16-byte aligned); the flat float
+ * parameter vector used for training holds L1L_MLP_PARAMS values in the order
+ * W1 [128][3], b1 [128], W2 [128][128], b2 [128], w3 [128], b3.
+ */
+#define L1L_MLP_HIDDEN 128
+#define L1L_MLP_PARAMS 17153
+typedef struct l1line_mlp {
+    uint16_t w1[L1L_MLP_HIDDEN * 3];              /* binary16 bits, [o][c]  */
+    float b1[L1L_MLP_HIDDEN];
+    uint16_t w2[L1L_MLP_HIDDEN * L1L_MLP_HIDDEN]; /* binary16 bits, [o][i]  */
+    float b2[L1L_MLP_HIDDEN];
+    uint16_t w3[L1L_MLP_HIDDEN];                  /* binary16 bits          */
+    float b3;
+    float reserved[3];
+} l1line_mlp;
+
+/* Column features of X (raw and standardised, DEVICE float [m][3] each; raw
+ * may be NULL).  Workspace as for l1line_fit_* with n_lambda = 1. */
+int l1line_features_f32(const float *X, int64_t n, int64_t m, float *out_raw, float *out_std,
+                        void *workspace, size_t workspace_bytes, void *stream);
+int l1line_features_f64(const double *X, int64_t n, int64_t m, float *out_raw, float *out_std,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* Network forward pass: scores[r] = net(feat[rows[r]]) for r < N (rows NULL:
+ * row r).  feat DEVICE float [*][3], rows DEVICE int32 [N] or NULL, mlp
+ * DEVICE, scores DEVICE float [N]. */
+int l1line_mlp_forward(const float *feat, const int32_t *rows, int64_t N,
+                       const l1line_mlp *mlp, float *scores, void *stream);
+
+/* Bytes of DEVICE workspace l1line_mlp_backward needs for N samples. */
+size_t l1line_mlp_workspace_bytes(int64_t N);
+
+/* Gradient of sum_r dscores[r] * scores[r] with respect to the flat
+ * parameters (through the binary16 weights as used), written (not added) to
+ * grad (DEVICE float [L1L_MLP_PARAMS]).  Deterministic: per-CTA partial
+ * gradients in the workspace are summed in a fixed order. */
+int l1line_mlp_backward(const float *feat, const int32_t *rows, int64_t N,
+                        const l1line_mlp *mlp, const float *dscores, float *grad,
+                        void *workspace, size_t workspace_bytes, void *stream);
+
+/* Listwise training loss.  Instance b owns positions offsets[b] ..
+ * offsets[b+1]-1 (DEVICE int64 [n_inst + 1]) of scores; its loss is the cross
+ * entropy between softmax(targets) and softmax(scores) over those positions
+ * (targets[rows[r]], or targets[r] when rows is NULL).  Writes loss[b]
+ * (DEVICE float [n_inst]) and dscores[r] = d(mean_b loss_b)/d scores[r]. */
+int l1line_rank_loss(const float *scores, const float *targets, const int32_t *rows,
+                     const int64_t *offsets, int64_t n_inst, float *dscores, float *loss,
+                     void *stream);
+
+/* One Adam step (step >= 1, with bias correction) on the flat float
+ * parameters theta with moments m1, m2 (DEVICE float [L1L_MLP_PARAMS] each),
+ * then writes the updated network into mlp (DEVICE; may be NULL). */
+int l1line_adam_step(float *theta, const float *grad, float *m1, float *m2, int64_t step,
+                     float lr, float beta1, float beta2, float eps, l1line_mlp *mlp,
+                     void *stream);
+
+/* Packs flat float parameters into the network image (weights rounded to
+ * binary16, nearest even). */
+int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream);
+
+/* Indices of the K (1 <= K <= m) highest scores, ties to the smaller index,
+ * NaN lowest, written in ascending index order to out_idx (DEVICE int32 [K]). */
+int l1line_topk(const float *scores, int64_t m, int64_t K, int32_t *out_idx, void *stream);
+
+/* The whole learned path in one call: features, network, top-K, then the
+ * subset fit of those K candidates.  out_idx (DEVICE int32 [K]) receives the
+ * candidates (may be NULL).  Workspace as for l1line_fit_*. */
+int l1line_fit_proposed_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                            int64_t n_lambda, const l1line_mlp *mlp, int64_t K,
+                            int32_t *out_idx, float *out_v, double *out_obj,
+                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                            void *stream);
+int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                            int64_t n_lambda, const l1line_mlp *mlp, int64_t K,
+                            int32_t *out_idx, double *out_v, double *out_obj,
+                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                            void *stream);
 
 /*
  * No-allocation fit (the paper has no counterpart: this is an interface
@@ -183,7 +295,8 @@ int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m, const double *l
 
 /* Synchronise `stream` and return the device-side status recorded in the
  * workspace by the last call that used it (L1L_OK, L1L_ERR_NONFINITE,
- * L1L_ERR_TIMEOUT or L1L_ERR_INTERNAL), or L1L_ERR_CUDA. */
+ * L1L_ERR_TIMEOUT, L1L_ERR_INTERNAL, or L1L_ERR_ARG for a jhat list entry out
+ * of range), or L1L_ERR_CUDA. */
 int l1line_status(void *workspace, void *stream);
 
 /* Human-readable text of a status code (static storage). */

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libl1line.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_prep.cu", "k_pairs.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "abi.cu"]
+SOURCES = ["k_prep.cu", "k_pairs.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "k_propose.cu",
+           "abi.cu"]
 
 
 def nvcc() -> str:

@@ -32,7 +32,9 @@ bool mul_ok(int64_t a, int64_t b, int64_t &out) {
 }
 
 struct Layout {
-    size_t status, slow_count, colinfo, Xt, v_all, s_all, z_all, slow, total;
+    size_t status, slow_count, colinfo, Xt, v_all, s_all, z_all, slow;
+    size_t feat_raw, feat_std, score, idx;  // learned proposer: [m][3], [m][3], [m], [m]
+    size_t total;
     int64_t ldn;
 };
 
@@ -63,6 +65,14 @@ bool make_layout(int dtype, int64_t n, int64_t m, int64_t nl, Layout &L) {
     off = al256(off + (size_t)(m * nl) * 8);
     L.slow = off;
     off = al256(off + (size_t)chunk_pairs * sizeof(SlowEntry));
+    L.feat_raw = off;
+    off = al256(off + (size_t)m * 12);
+    L.feat_std = off;
+    off = al256(off + (size_t)m * 12);
+    L.score = off;
+    off = al256(off + (size_t)m * 4);
+    L.idx = off;
+    off = al256(off + (size_t)m * 4);
     L.total = off;
     L.ldn = ldn;
     return true;
@@ -79,10 +89,22 @@ template <typename T> int dtype_of();
 template <> int dtype_of<float>() { return L1L_DTYPE_F32; }
 template <> int dtype_of<double>() { return L1L_DTYPE_F64; }
 
+// One scan or fit in stages: setup (validation, workspace carving), prep
+// (transpose, column info), pairs (steps A2-A5 for the listed jhat), argmin.
+template <typename T> struct Scan {
+    ScanArgs<T> a;
+    Layout L;
+    int sms = 0;
+    double *z = nullptr;
+    unsigned char *base = nullptr;
+    cudaStream_t st = nullptr;
+    int launches = 0;
+};
+
 template <typename T>
-int scan_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl, T *v_all,
-              double *s_all, double *z_all, void *ws, size_t ws_bytes, void *stream,
-              uint32_t flags, Layout &L) {
+int scan_setup(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl, T *v_all,
+               double *s_all, double *z_all, void *ws, size_t ws_bytes, void *stream,
+               uint32_t flags, Scan<T> &c) {
     g_last_launches = 0;
     if (!X || !lambdas || n < 1 || m < 1 || nl < 1) return L1L_ERR_ARG;
     if (m > 0x7FFFFFFF || nl > 65535) return L1L_ERR_UNSUPPORTED;
@@ -90,70 +112,153 @@ int scan_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t n
         if (!(lambdas[t] >= 0.0) || std::isinf(lambdas[t])) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(X) % sizeof(T)) != 0) return L1L_ERR_ARG;
     if (n > max_rows_pairs<T>()) return L1L_ERR_UNSUPPORTED;
+    Layout &L = c.L;
     if (!make_layout(dtype_of<T>(), n, m, nl, L)) return L1L_ERR_UNSUPPORTED;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < L.total)
         return L1L_ERR_WORKSPACE;
-    const int sms = num_sms();
-    if (sms <= 0) return L1L_ERR_CUDA;
-    const PairPlan plan = plan_pairs<T>(n, m, sms);
-    if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
-
-    unsigned char *base = static_cast<unsigned char *>(ws);
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    ScanArgs<T> a;
-    a.Xt = reinterpret_cast<T *>(base + L.Xt);
-    a.ci = reinterpret_cast<ColInfo *>(base + L.colinfo);
+    c.sms = num_sms();
+    if (c.sms <= 0) return L1L_ERR_CUDA;
+    c.base = static_cast<unsigned char *>(ws);
+    c.st = static_cast<cudaStream_t>(stream);
+    ScanArgs<T> &a = c.a;
+    a.Xt = reinterpret_cast<T *>(c.base + L.Xt);
+    a.ci = reinterpret_cast<ColInfo *>(c.base + L.colinfo);
     a.n = n;
     a.m = m;
     a.ldn = L.ldn;
     a.n_lambda = (int32_t)nl;
-    a.v_all = v_all ? v_all : reinterpret_cast<T *>(base + L.v_all);
-    a.s_all = s_all ? s_all : reinterpret_cast<double *>(base + L.s_all);
-    a.status = reinterpret_cast<uint32_t *>(base + L.status);
-    a.slow_count = reinterpret_cast<uint32_t *>(base + L.slow_count);
-    a.slow = reinterpret_cast<SlowEntry *>(base + L.slow);
+    a.v_all = v_all ? v_all : reinterpret_cast<T *>(c.base + L.v_all);
+    a.s_all = s_all ? s_all : reinterpret_cast<double *>(c.base + L.s_all);
+    a.status = reinterpret_cast<uint32_t *>(c.base + L.status);
+    a.slow_count = reinterpret_cast<uint32_t *>(c.base + L.slow_count);
+    a.slow = reinterpret_cast<SlowEntry *>(c.base + L.slow);
     a.force_exact = (flags & L1L_FLAG_FORCE_EXACT) ? 1 : 0;
     a.inst = 0;
-    double *z = z_all ? z_all : reinterpret_cast<double *>(base + L.z_all);
+    a.jlist = nullptr;
+    a.nj = m;
+    c.z = z_all ? z_all : reinterpret_cast<double *>(c.base + L.z_all);
+    return L1L_OK;
+}
 
-    int launches = 0;
-    if (cudaMemsetAsync(a.status, 0, sizeof(uint32_t), st) != cudaSuccess) return L1L_ERR_CUDA;
-    if (launch_prep<T>(X, const_cast<T *>(a.Xt), const_cast<ColInfo *>(a.ci), n, m, L.ldn,
-                       a.status, st, launches) != cudaSuccess)
+template <typename T> int scan_prep(const T *X, Scan<T> &c) {
+    ScanArgs<T> &a = c.a;
+    if (cudaMemsetAsync(a.status, 0, sizeof(uint32_t), c.st) != cudaSuccess) return L1L_ERR_CUDA;
+    if (launch_prep<T>(X, const_cast<T *>(a.Xt), const_cast<ColInfo *>(a.ci), a.n, a.m, a.ldn,
+                       a.status, c.st, c.launches) != cudaSuccess)
         return L1L_ERR_CUDA;
+    return L1L_OK;
+}
+
+// Steps A2-A5 for the jhat in jlist[0..nj) (jlist == nullptr: all m).
+template <typename T>
+int scan_pairs(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jlist, int64_t nj) {
+    ScanArgs<T> &a = c.a;
+    a.jlist = jlist;
+    a.nj = nj;
+    const PairPlan plan = plan_pairs<T>(a.n, a.m, c.sms, nj);
+    if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
     const bool prof = g_ev_start && g_ev_stop;
     for (int64_t t0 = 0; t0 < nl; t0 += MAX_LAMBDA_PER_LAUNCH) {
         const int nlc = (int)((nl - t0) < MAX_LAMBDA_PER_LAUNCH ? (nl - t0) : MAX_LAMBDA_PER_LAUNCH);
         const bool last = t0 + MAX_LAMBDA_PER_LAUNCH >= nl;
-        if (cudaMemsetAsync(a.slow_count, 0, sizeof(uint32_t), st) != cudaSuccess)
+        if (cudaMemsetAsync(a.slow_count, 0, sizeof(uint32_t), c.st) != cudaSuccess)
             return L1L_ERR_CUDA;
-        if (prof && t0 == 0 && cudaEventRecord(g_ev_start, st) != cudaSuccess) return L1L_ERR_CUDA;
-        if (launch_pairs<T>(a, lambdas, (int)t0, nlc, plan, st, launches) != cudaSuccess)
+        if (prof && t0 == 0 && cudaEventRecord(g_ev_start, c.st) != cudaSuccess)
             return L1L_ERR_CUDA;
-        if (prof && last && cudaEventRecord(g_ev_stop, st) != cudaSuccess) return L1L_ERR_CUDA;
-        if (launch_exact<T>(a, lambdas, (int)t0, nlc, sms, st, launches) != cudaSuccess)
+        if (launch_pairs<T>(a, lambdas, (int)t0, nlc, plan, c.st, c.launches) != cudaSuccess)
+            return L1L_ERR_CUDA;
+        if (prof && last && cudaEventRecord(g_ev_stop, c.st) != cudaSuccess) return L1L_ERR_CUDA;
+        if (launch_exact<T>(a, lambdas, (int)t0, nlc, c.sms, c.st, c.launches) != cudaSuccess)
             return L1L_ERR_CUDA;
     }
-    if (launch_zreduce(a.s_all, z, m, nl, st, launches) != cudaSuccess) return L1L_ERR_CUDA;
-    g_last_launches = launches;
+    if (launch_zreduce(a.s_all, c.z, a.m, nl, jlist, nj, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
     return L1L_OK;
 }
 
 template <typename T>
-int fit_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl, T *out_v,
-             double *out_obj, int32_t *out_jstar, void *ws, size_t ws_bytes, void *stream) {
-    if (!out_v || !out_obj || !out_jstar) return L1L_ERR_ARG;
-    Layout L;
-    int rc = scan_impl<T>(X, n, m, lambdas, nl, nullptr, nullptr, nullptr, ws, ws_bytes, stream,
-                          0u, L);
-    if (rc != L1L_OK) return rc;
-    unsigned char *base = static_cast<unsigned char *>(ws);
-    int launches = g_last_launches;
-    if (launch_argmin<T>(reinterpret_cast<double *>(base + L.z_all),
-                         reinterpret_cast<T *>(base + L.v_all), m, nl, out_v, out_obj, out_jstar,
-                         static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+int scan_argmin(Scan<T> &c, int64_t nl, T *out_v, double *out_obj, int32_t *out_jstar) {
+    if (launch_argmin<T>(c.z, c.a.v_all, c.a.m, nl, c.a.jlist, c.a.nj, out_v, out_obj, out_jstar,
+                         c.st, c.launches) != cudaSuccess)
         return L1L_ERR_CUDA;
-    g_last_launches = launches;
+    return L1L_OK;
+}
+
+#define L1L_TRY(expr)                                                                             \
+    do {                                                                                          \
+        const int rc_ = (expr);                                                                   \
+        if (rc_ != L1L_OK) return rc_;                                                            \
+    } while (0)
+
+template <typename T>
+int scan_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl, T *v_all,
+              double *s_all, double *z_all, void *ws, size_t ws_bytes, void *stream,
+              uint32_t flags) {
+    Scan<T> c;
+    L1L_TRY(scan_setup<T>(X, n, m, lambdas, nl, v_all, s_all, z_all, ws, ws_bytes, stream, flags,
+                          c));
+    L1L_TRY(scan_prep<T>(X, c));
+    L1L_TRY(scan_pairs<T>(c, lambdas, nl, nullptr, m));
+    g_last_launches = c.launches;
+    return L1L_OK;
+}
+
+// Full fit (jlist == nullptr) or subset fit of jlist[0..nj).
+template <typename T>
+int fit_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl,
+             const int32_t *jlist, int64_t nj, T *out_v, double *out_obj, int32_t *out_jstar,
+             void *ws, size_t ws_bytes, void *stream) {
+    if (!out_v || !out_obj || !out_jstar) return L1L_ERR_ARG;
+    if (jlist && (nj < 1 || nj > 0x7FFFFFFF)) return L1L_ERR_ARG;
+    Scan<T> c;
+    L1L_TRY(scan_setup<T>(X, n, m, lambdas, nl, nullptr, nullptr, nullptr, ws, ws_bytes, stream,
+                          0u, c));
+    L1L_TRY(scan_prep<T>(X, c));
+    L1L_TRY(scan_pairs<T>(c, lambdas, nl, jlist, jlist ? nj : m));
+    L1L_TRY(scan_argmin<T>(c, nl, out_v, out_obj, out_jstar));
+    g_last_launches = c.launches;
+    return L1L_OK;
+}
+
+const double k_zero_lambda = 0.0;
+
+template <typename T>
+int features_impl(const T *X, int64_t n, int64_t m, float *out_raw, float *out_std, void *ws,
+                  size_t ws_bytes, void *stream) {
+    if (!out_std) return L1L_ERR_ARG;
+    Scan<T> c;
+    L1L_TRY(scan_setup<T>(X, n, m, &k_zero_lambda, 1, nullptr, nullptr, nullptr, ws, ws_bytes,
+                          stream, 0u, c));
+    L1L_TRY(scan_prep<T>(X, c));
+    float *raw = out_raw ? out_raw : reinterpret_cast<float *>(c.base + c.L.feat_raw);
+    if (launch_features<T>(c.a.Xt, c.a.ldn, n, m, raw, out_std, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = c.launches;
+    return L1L_OK;
+}
+
+template <typename T>
+int proposed_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl,
+                  const l1line_mlp *mlp, int64_t K, int32_t *out_idx, T *out_v, double *out_obj,
+                  int32_t *out_jstar, void *ws, size_t ws_bytes, void *stream) {
+    if (!mlp || !out_v || !out_obj || !out_jstar) return L1L_ERR_ARG;
+    if (K < 1 || K > m) return L1L_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
+    Scan<T> c;
+    L1L_TRY(scan_setup<T>(X, n, m, lambdas, nl, nullptr, nullptr, nullptr, ws, ws_bytes, stream,
+                          0u, c));
+    L1L_TRY(scan_prep<T>(X, c));
+    float *raw = reinterpret_cast<float *>(c.base + c.L.feat_raw);
+    float *stdz = reinterpret_cast<float *>(c.base + c.L.feat_std);
+    float *score = reinterpret_cast<float *>(c.base + c.L.score);
+    int32_t *idx = out_idx ? out_idx : reinterpret_cast<int32_t *>(c.base + c.L.idx);
+    if (launch_features<T>(c.a.Xt, c.a.ldn, n, m, raw, stdz, c.st, c.launches) != cudaSuccess ||
+        launch_mlp_forward(stdz, nullptr, m, mlp, score, c.st, c.launches) != cudaSuccess ||
+        launch_topk(score, m, (int)K, idx, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    L1L_TRY(scan_pairs<T>(c, lambdas, nl, idx, K));
+    L1L_TRY(scan_argmin<T>(c, nl, out_v, out_obj, out_jstar));
+    g_last_launches = c.launches;
     return L1L_OK;
 }
 
@@ -177,17 +282,15 @@ size_t l1line_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t n_lambda)
 int l1line_scan_ex_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                        int64_t n_lambda, float *v_all, double *s_all, double *z_all,
                        void *workspace, size_t workspace_bytes, void *stream, uint32_t flags) {
-    Layout L;
     return scan_impl<float>(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
-                            workspace_bytes, stream, flags, L);
+                            workspace_bytes, stream, flags);
 }
 
 int l1line_scan_ex_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                        int64_t n_lambda, double *v_all, double *s_all, double *z_all,
                        void *workspace, size_t workspace_bytes, void *stream, uint32_t flags) {
-    Layout L;
     return scan_impl<double>(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
-                             workspace_bytes, stream, flags, L);
+                             workspace_bytes, stream, flags);
 }
 
 int l1line_scan_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
@@ -207,15 +310,154 @@ int l1line_scan_f64(const double *X, int64_t n, int64_t m, const double *lambdas
 int l1line_fit_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, float *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream) {
-    return fit_impl<float>(X, n, m, lambdas, n_lambda, out_v, out_obj, out_jstar, workspace,
-                           workspace_bytes, stream);
+    return fit_impl<float>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar,
+                           workspace, workspace_bytes, stream);
 }
 
 int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, double *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream) {
-    return fit_impl<double>(X, n, m, lambdas, n_lambda, out_v, out_obj, out_jstar, workspace,
-                            workspace_bytes, stream);
+    return fit_impl<double>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar,
+                            workspace, workspace_bytes, stream);
+}
+
+int l1line_fit_subset_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                          int64_t n_lambda, const int32_t *jhat_list, int64_t K, float *out_v,
+                          double *out_obj, int32_t *out_jstar, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    if (!jhat_list) return L1L_ERR_ARG;
+    return fit_impl<float>(X, n, m, lambdas, n_lambda, jhat_list, K, out_v, out_obj, out_jstar,
+                           workspace, workspace_bytes, stream);
+}
+
+int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                          int64_t n_lambda, const int32_t *jhat_list, int64_t K, double *out_v,
+                          double *out_obj, int32_t *out_jstar, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    if (!jhat_list) return L1L_ERR_ARG;
+    return fit_impl<double>(X, n, m, lambdas, n_lambda, jhat_list, K, out_v, out_obj, out_jstar,
+                            workspace, workspace_bytes, stream);
+}
+
+int l1line_features_f32(const float *X, int64_t n, int64_t m, float *out_raw, float *out_std,
+                        void *workspace, size_t workspace_bytes, void *stream) {
+    return features_impl<float>(X, n, m, out_raw, out_std, workspace, workspace_bytes, stream);
+}
+
+int l1line_features_f64(const double *X, int64_t n, int64_t m, float *out_raw, float *out_std,
+                        void *workspace, size_t workspace_bytes, void *stream) {
+    return features_impl<double>(X, n, m, out_raw, out_std, workspace, workspace_bytes, stream);
+}
+
+int l1line_mlp_forward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
+                       float *scores, void *stream) {
+    g_last_launches = 0;
+    if (!feat || !mlp || !scores || N < 1) return L1L_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
+    if ((N + MLP_TILE - 1) / MLP_TILE > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
+    int launches = 0;
+    if (launch_mlp_forward(feat, rows, N, mlp, scores, static_cast<cudaStream_t>(stream),
+                           launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+size_t l1line_mlp_workspace_bytes(int64_t N) {
+    if (N < 1 || N > ((int64_t)1 << 34)) return 0;
+    return al256((size_t)((N + MLP_TILE - 1) / MLP_TILE) * L1L_MLP_PARAMS * sizeof(float));
+}
+
+int l1line_mlp_backward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
+                        const float *dscores, float *grad, void *workspace,
+                        size_t workspace_bytes, void *stream) {
+    g_last_launches = 0;
+    if (!feat || !mlp || !dscores || !grad || N < 1) return L1L_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
+    const size_t need = l1line_mlp_workspace_bytes(N);
+    if (need == 0) return L1L_ERR_UNSUPPORTED;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) != 0 ||
+        workspace_bytes < need)
+        return L1L_ERR_WORKSPACE;
+    int launches = 0;
+    if (launch_mlp_backward(feat, rows, N, mlp, dscores, static_cast<float *>(workspace), grad,
+                            static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+int l1line_rank_loss(const float *scores, const float *targets, const int32_t *rows,
+                     const int64_t *offsets, int64_t n_inst, float *dscores, float *loss,
+                     void *stream) {
+    g_last_launches = 0;
+    if (!scores || !targets || !offsets || !dscores || !loss || n_inst < 1) return L1L_ERR_ARG;
+    if (n_inst > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
+    int launches = 0;
+    if (launch_rank_loss(scores, targets, rows, offsets, n_inst, dscores, loss,
+                         static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+int l1line_adam_step(float *theta, const float *grad, float *m1, float *m2, int64_t step,
+                     float lr, float beta1, float beta2, float eps, l1line_mlp *mlp,
+                     void *stream) {
+    g_last_launches = 0;
+    if (!theta || !grad || !m1 || !m2 || step < 1) return L1L_ERR_ARG;
+    if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps >= 0.0f) || std::isinf(lr) || std::isinf(eps))
+        return L1L_ERR_ARG;
+    if (mlp && (reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
+    // bias corrections 1 / (1 - beta^step), formed in double on the host
+    const double c1 = 1.0 / (1.0 - std::pow((double)beta1, (double)step));
+    const double c2 = 1.0 / (1.0 - std::pow((double)beta2, (double)step));
+    int launches = 0;
+    if (launch_adam(theta, grad, m1, m2, lr, beta1, beta2, eps, (float)c1, (float)c2, mlp,
+                    static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream) {
+    g_last_launches = 0;
+    if (!theta || !mlp || (reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
+    int launches = 0;
+    if (launch_mlp_pack(theta, mlp, static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+int l1line_topk(const float *scores, int64_t m, int64_t K, int32_t *out_idx, void *stream) {
+    g_last_launches = 0;
+    if (!scores || !out_idx || m < 1 || K < 1 || K > m) return L1L_ERR_ARG;
+    if (m > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
+    int launches = 0;
+    if (launch_topk(scores, m, (int)K, out_idx, static_cast<cudaStream_t>(stream), launches) !=
+        cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
+int l1line_fit_proposed_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
+                            int64_t n_lambda, const l1line_mlp *mlp, int64_t K, int32_t *out_idx,
+                            float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
+                            size_t workspace_bytes, void *stream) {
+    return proposed_impl<float>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
+                                out_jstar, workspace, workspace_bytes, stream);
+}
+
+int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
+                            int64_t n_lambda, const l1line_mlp *mlp, int64_t K,
+                            int32_t *out_idx, double *out_v, double *out_obj,
+                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+    return proposed_impl<double>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
+                                 out_jstar, workspace, workspace_bytes, stream);
 }
 
 int l1line_status(void *workspace, void *stream) {
@@ -228,6 +470,7 @@ int l1line_status(void *workspace, void *stream) {
     if (w & ST_NONFINITE) return L1L_ERR_NONFINITE;
     if (w & ST_TIMEOUT) return L1L_ERR_TIMEOUT;
     if (w & ST_INTERNAL) return L1L_ERR_INTERNAL;
+    if (w & ST_BADINDEX) return L1L_ERR_ARG;
     return L1L_OK;
 }
 
@@ -324,7 +567,7 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
         return L1L_ERR_WORKSPACE;
     const int sms = num_sms();
     if (sms <= 0) return L1L_ERR_CUDA;
-    const PairPlan plan = plan_pairs<T>(sh.max_n, 1, sms);
+    const PairPlan plan = plan_pairs<T>(sh.max_n, 1, sms, 1);
     if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
 
     std::unique_ptr<BatchDesc<T>> bd(new BatchDesc<T>());
@@ -471,6 +714,6 @@ extern "C" int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m,
     if (rc != L1L_OK) return rc;
     // the status word and the exact-path counter are zeroed by the fit itself;
     // every other region of the workspace is fully overwritten before it is read
-    return fit_impl<float>(X, n, m, lambdas, n_lambda, out_v, out_obj, out_jstar, ws,
+    return fit_impl<float>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar, ws,
                            L1L_NOALLOC_SCRATCH_BYTES, stream);
 }

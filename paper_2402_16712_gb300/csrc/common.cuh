@@ -17,6 +17,7 @@ enum : uint32_t {
     ST_NONFINITE = 1u << 0,
     ST_INTERNAL = 1u << 1,
     ST_TIMEOUT = 1u << 2,
+    ST_BADINDEX = 1u << 3,  // a jhat list entry outside [0, m)
 };
 
 // ---------------------------------------------------------------------------
@@ -227,6 +228,8 @@ template <typename T> struct ScanArgs {
     SlowEntry *slow;   // capacity n_lambda * m * m
     int force_exact;
     int inst;          // instance index recorded in slow-list entries (batched calls)
+    const int32_t *jlist;  // device list of the jhat to score (nullptr: all m)
+    int64_t nj;            // entries of jlist (m when jlist is nullptr)
 };
 
 constexpr int MAX_LAMBDA_PER_LAUNCH = 256;

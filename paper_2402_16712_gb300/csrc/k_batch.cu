@@ -48,6 +48,8 @@ __device__ __forceinline__ ScanArgs<T> inst_args(const BatchDesc<T> &bd, int b,
     a.slow = reinterpret_cast<SlowEntry *>(ws + BATCH_HEAD);
     a.force_exact = bd.force_exact;
     a.inst = b;
+    a.jlist = nullptr;
+    a.nj = a.m;
     return a;
 }
 

@@ -67,8 +67,12 @@ __global__ void __launch_bounds__(256, 3)
     const int64_t k0 = (int64_t)blockIdx.y * kchunk;
     const int64_t k1 = min(a.m, k0 + kchunk);
     const LamView lv{lp.lam, lp.tl_min, lp.tl_max};
-    pairs_unit<T, MULTI>(a, lv, t0, nlc, (int)blockIdx.x, k0, k1, cap, ((int)a.n + 31) & ~31, smem,
-                         s_dec);
+    const int64_t j = a.jlist ? (int64_t)a.jlist[blockIdx.x] : (int64_t)blockIdx.x;
+    if (j < 0 || j >= a.m) {  // uniform over the CTA
+        if (threadIdx.x == 0) atomicOr(a.status, ST_BADINDEX);
+        return;
+    }
+    pairs_unit<T, MULTI>(a, lv, t0, nlc, (int)j, k0, k1, cap, ((int)a.n + 31) & ~31, smem, s_dec);
 }
 
 // Candidate slots per warp (a multiple of 32: 32 lanes x quota).  About 40% of
@@ -87,7 +91,7 @@ template <typename T> int64_t max_rows_pairs() {
     return n;
 }
 
-template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms) {
+template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj) {
     PairPlan p{0, 0, 0, 0, 0};
     const int64_t npad = (n + 31) & ~int64_t(31);
     if (n > max_rows_pairs<T>()) return p;
@@ -119,9 +123,10 @@ template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms) {
     p.warps = w;
     p.cap = cap;
     p.smem = cb + (size_t)w * PairSmem<T>::warp_bytes(cap);
+    // about four CTAs per SM over the nj x chunks grid
     int64_t want_ctas = (int64_t)num_sms * 4;
     int64_t chunks =
-        std::max<int64_t>(1, std::min<int64_t>((m + w - 1) / w, (want_ctas + m - 1) / m));
+        std::max<int64_t>(1, std::min<int64_t>((m + w - 1) / w, (want_ctas + nj - 1) / nj));
     p.kchunk = (int)((m + chunks - 1) / chunks);
     p.kchunks = (int)((m + p.kchunk - 1) / p.kchunk);
     return p;
@@ -134,7 +139,7 @@ cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, in
     auto kern = nlc >= 3 ? k_pairs<T, true> : k_pairs<T, false>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), plan.smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)a.m, (unsigned)plan.kchunks);
+    dim3 grid((unsigned)a.nj, (unsigned)plan.kchunks);
     LambdaPack lp;
     lp.tl_min = lp.tl_max = 0;
     for (int q = 0; q < nlc; ++q) {
@@ -147,8 +152,8 @@ cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, in
     return cudaGetLastError();
 }
 
-template PairPlan plan_pairs<float>(int64_t, int64_t, int);
-template PairPlan plan_pairs<double>(int64_t, int64_t, int);
+template PairPlan plan_pairs<float>(int64_t, int64_t, int, int64_t);
+template PairPlan plan_pairs<double>(int64_t, int64_t, int, int64_t);
 template int64_t max_rows_pairs<float>();
 template int64_t max_rows_pairs<double>();
 template cudaError_t launch_pairs<float>(const ScanArgs<float> &, const double *, int, int,

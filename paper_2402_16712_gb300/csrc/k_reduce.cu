@@ -5,10 +5,14 @@
 namespace l1l {
 
 // z[t][jhat] = sum_k s_all[t][jhat][k]  (the diagonal holds lambda * |v_jhat| =
-// lambda).  One warp per (t, jhat); fixed summation order, so deterministic.
+// lambda).  One warp per (t, listed jhat); fixed summation order, so
+// deterministic.  jlist == nullptr scores every jhat.
 __global__ void __launch_bounds__(32) k_zreduce(const double *__restrict__ s_all,
-                                                double *__restrict__ z_all, int64_t m) {
-    const int64_t t = blockIdx.y, j = blockIdx.x;
+                                                double *__restrict__ z_all, int64_t m,
+                                                const int32_t *__restrict__ jlist) {
+    const int64_t t = blockIdx.y;
+    const int64_t j = jlist ? (int64_t)jlist[blockIdx.x] : (int64_t)blockIdx.x;
+    if (j < 0 || j >= m) return;  // flagged by the pair kernel
     const double *s = s_all + (t * m + j) * m;
     double acc = 0.0;
     for (int64_t k = threadIdx.x; k < m; k += 32) acc += s[k];
@@ -21,12 +25,15 @@ __global__ void __launch_bounds__(32) k_zreduce(const double *__restrict__ s_all
 template <typename T>
 __global__ void __launch_bounds__(256) k_argmin(const double *__restrict__ z_all,
                                                 const T *__restrict__ v_all, int64_t m,
+                                                const int32_t *__restrict__ jlist, int64_t nj,
                                                 T *out_v, double *out_obj, int32_t *out_jstar) {
     const int64_t t = blockIdx.x;
     const double *z = z_all + t * m;
     double bz = 0.0;
     int64_t bj = -1;
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+    for (int64_t p = threadIdx.x; p < nj; p += blockDim.x) {
+        const int64_t j = jlist ? (int64_t)jlist[p] : p;
+        if (j < 0 || j >= m) continue;
         double zj = z[j];
         if (zj == zj && (bj < 0 || zj < bz)) {
             bz = zj;
@@ -62,25 +69,28 @@ __global__ void __launch_bounds__(256) k_argmin(const double *__restrict__ z_all
 }
 
 cudaError_t launch_zreduce(const double *s_all, double *z_all, int64_t m, int64_t n_lambda,
-                           cudaStream_t st, int &launches) {
-    dim3 grid((unsigned)m, (unsigned)n_lambda);
-    k_zreduce<<<grid, 32, 0, st>>>(s_all, z_all, m);
+                           const int32_t *jlist, int64_t nj, cudaStream_t st, int &launches) {
+    dim3 grid((unsigned)nj, (unsigned)n_lambda);
+    k_zreduce<<<grid, 32, 0, st>>>(s_all, z_all, m, jlist);
     launches++;
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_argmin(const double *z_all, const T *v_all, int64_t m, int64_t n_lambda,
-                          T *out_v, double *out_obj, int32_t *out_jstar, cudaStream_t st,
-                          int &launches) {
-    k_argmin<T><<<(unsigned)n_lambda, 256, 0, st>>>(z_all, v_all, m, out_v, out_obj, out_jstar);
+                          const int32_t *jlist, int64_t nj, T *out_v, double *out_obj,
+                          int32_t *out_jstar, cudaStream_t st, int &launches) {
+    k_argmin<T><<<(unsigned)n_lambda, 256, 0, st>>>(z_all, v_all, m, jlist, nj, out_v, out_obj,
+                                                    out_jstar);
     launches++;
     return cudaGetLastError();
 }
 
-template cudaError_t launch_argmin<float>(const double *, const float *, int64_t, int64_t, float *,
-                                          double *, int32_t *, cudaStream_t, int &);
+template cudaError_t launch_argmin<float>(const double *, const float *, int64_t, int64_t,
+                                          const int32_t *, int64_t, float *, double *, int32_t *,
+                                          cudaStream_t, int &);
 template cudaError_t launch_argmin<double>(const double *, const double *, int64_t, int64_t,
-                                           double *, double *, int32_t *, cudaStream_t, int &);
+                                           const int32_t *, int64_t, double *, double *,
+                                           int32_t *, cudaStream_t, int &);
 
 }  // namespace l1l

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "common.cuh"
+#include "l1line.h"
 
 namespace l1l {
 
@@ -28,7 +29,8 @@ struct PairPlan {
     int kchunks;
     int cap;  // per-warp candidate-list capacity
 };
-template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms);
+// nj: number of jhat scored (m for a full scan).
+template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj);
 template <typename T> int64_t max_rows_pairs();
 
 // One launch of the pair kernel for lambdas[t0 .. t0+nlc) (nlc <= MAX_LAMBDA_PER_LAUNCH).
@@ -41,13 +43,36 @@ template <typename T>
 cudaError_t launch_exact(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
                          int num_sms, cudaStream_t st, int &launches);
 
+// z of the listed jhat (jlist == nullptr: all m, nj == m).
 cudaError_t launch_zreduce(const double *s_all, double *z_all, int64_t m, int64_t n_lambda,
-                           cudaStream_t st, int &launches);
+                           const int32_t *jlist, int64_t nj, cudaStream_t st, int &launches);
 
+// Argmin over the listed jhat (smallest jhat on ties) and gather of v*.
 template <typename T>
 cudaError_t launch_argmin(const double *z_all, const T *v_all, int64_t m, int64_t n_lambda,
-                          T *out_v, double *out_obj, int32_t *out_jstar, cudaStream_t st,
-                          int &launches);
+                          const int32_t *jlist, int64_t nj, T *out_v, double *out_obj,
+                          int32_t *out_jstar, cudaStream_t st, int &launches);
+
+// ---- learned jhat proposer (k_propose.cu) ----
+constexpr int MLP_TILE = 64;  // samples per CTA of the network kernels
+size_t mlp_smem_bytes();
+template <typename T>
+cudaError_t launch_features(const T *Xt, int64_t ldn, int64_t n, int64_t m, float *raw,
+                            float *stdz, cudaStream_t st, int &launches);
+cudaError_t launch_mlp_forward(const float *feat, const int32_t *rows, int64_t N,
+                               const l1line_mlp *p, float *score, cudaStream_t st, int &launches);
+cudaError_t launch_mlp_backward(const float *feat, const int32_t *rows, int64_t N,
+                                const l1line_mlp *p, const float *dscore, float *part,
+                                float *grad, cudaStream_t st, int &launches);
+cudaError_t launch_rank_loss(const float *score, const float *target, const int32_t *rows,
+                             const int64_t *off, int64_t n_inst, float *ds, float *loss,
+                             cudaStream_t st, int &launches);
+cudaError_t launch_adam(float *theta, const float *grad, float *m1, float *m2, float lr,
+                        float beta1, float beta2, float eps, float c1, float c2, l1line_mlp *out,
+                        cudaStream_t st, int &launches);
+cudaError_t launch_mlp_pack(const float *theta, l1line_mlp *out, cudaStream_t st, int &launches);
+cudaError_t launch_topk(const float *score, int64_t m, int K, int32_t *out, cudaStream_t st,
+                        int &launches);
 
 // The batched fit: staging, one persistent pair kernel, exact path, sums, argmin.
 template <typename T>

@@ -95,18 +95,59 @@ def uneven_batch(count=256, seed=0, n_range=(100, 5000), m_range=(10, 500), lam=
     return out
 
 
-def proposer_instance(seed, n_range=(500, 5000), m_range=(100, 1000), dtype="float32",
-                      n=None, m=None):
-    """Training/held-out instance for the learned proposer: n ~ U[500,5000],
-    m ~ U[100,1000] unless given; nnz ~ U[1, m//10], outliers ~ U[0,0.2];
-    lambda = 0.2."""
+PROPOSER_LAMBDA = 0.2
+# Held-out instances of the learned proposer use seeds from here on; training
+# instances use seeds 1 .. 20000.
+PROPOSER_HELDOUT_SEED0 = 1_000_001
+
+
+def proposer_spec(seed, n_range=(500, 5000), m_range=(100, 1000), dtype="float32", n=None,
+                  m=None) -> Planted:
+    """Shape and model parameters of a training / held-out instance of the
+    learned proposer: n ~ U[500,5000], m ~ U[100,1000] unless given,
+    nnz ~ U[1, m//10], outlier fraction ~ U[0, 0.2], Laplace(0, 0.1) noise,
+    N(0, 100 I) outliers; lambda = 0.2."""
     rng = np.random.default_rng(10_000_019 + seed)
     n = int(rng.integers(n_range[0], n_range[1] + 1)) if n is None else n
     m = int(rng.integers(m_range[0], m_range[1] + 1)) if m is None else m
     nnz = int(rng.integers(1, max(1, m // 10) + 1))
     frac = float(rng.uniform(0.0, 0.2))
-    X, v, _ = planted(Planted(n, m, nnz, 0.1, frac, 10.0, seed, dtype))
-    return X, np.array([0.2]), v
+    return Planted(n, m, nnz, 0.1, frac, 10.0, seed, dtype)
+
+
+def proposer_instance(seed, n_range=(500, 5000), m_range=(100, 1000), dtype="float32",
+                      n=None, m=None):
+    """proposer_spec's instance drawn with numpy (host memory)."""
+    X, v, _ = planted(proposer_spec(seed, n_range, m_range, dtype, n, m))
+    return X, np.array([PROPOSER_LAMBDA]), v
+
+
+def planted_torch(spec: Planted, device):
+    """The planted model of `planted`, drawn on a CUDA device by torch's
+    seeded generator (a different random stream from `planted`, same
+    distribution), for the learned proposer's many training instances.
+    Laplace noise by inversion: -b sgn(u) log(1 - 2|u|), u ~ U[-1/2, 1/2).
+    Returns (X, v_star, outlier_rows) as device tensors."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(spec.seed))
+    f64 = torch.float64
+    n, m = spec.n, spec.m
+    nnz = max(1, min(spec.nnz, m))
+    pos = torch.randperm(m, generator=g, device=device)[:nnz]
+    v = torch.zeros(m, dtype=f64, device=device)
+    v[pos] = torch.randn(nnz, generator=g, device=device, dtype=f64)
+    v = v / v.abs().sum().clamp_min(1e-300)
+    t = torch.randn(n, generator=g, device=device, dtype=f64)
+    u = torch.rand((n, m), generator=g, device=device, dtype=f64) - 0.5
+    e = -spec.noise_b * torch.sign(u) * torch.log((1.0 - 2.0 * u.abs()).clamp_min(1e-300))
+    X = t[:, None] * v[None, :] + e
+    nout = int(round(spec.outlier_frac * n))
+    rows = torch.sort(torch.randperm(n, generator=g, device=device)[:nout]).values
+    if nout:
+        X[rows] = torch.randn((nout, m), generator=g, device=device, dtype=f64) * spec.outlier_std
+    dt = torch.float32 if spec.dtype == "float32" else torch.float64
+    return X.to(dt).contiguous(), v, rows
 
 
 # ---------------------------------------------------------------------------

@@ -40,7 +40,25 @@ SIGNATURES = {
     "l1line_batched_workspace_bytes": (_SZ, [_I, _I64, _P, _P, _P]),
     "l1line_fit_batched_f32": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "l1line_fit_batched_f64": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_fit_subset_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_fit_subset_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_features_f32": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "l1line_features_f64": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "l1line_mlp_forward": (_I, [_P, _P, _I64, _P, _P, _P]),
+    "l1line_mlp_workspace_bytes": (_SZ, [_I64]),
+    "l1line_mlp_backward": (_I, [_P, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_rank_loss": (_I, [_P, _P, _P, _P, _I64, _P, _P, _P]),
+    "l1line_adam_step": (_I, [_P, _P, _P, _P, _I64, ctypes.c_float, ctypes.c_float,
+                              ctypes.c_float, ctypes.c_float, _P, _P]),
+    "l1line_mlp_pack": (_I, [_P, _P, _P]),
+    "l1line_topk": (_I, [_P, _I64, _I64, _P, _P]),
+    "l1line_fit_proposed_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P,
+                                     _SZ, _P]),
+    "l1line_fit_proposed_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P,
+                                     _SZ, _P]),
 }
+MLP_PARAMS = 17153   # L1L_MLP_PARAMS
+MLP_BYTES = 34832    # sizeof(l1line_mlp)
 NOALLOC_SCRATCH_BYTES = 32 << 20  # L1L_NOALLOC_SCRATCH_BYTES in include/l1line.h
 
 _lib = None
@@ -132,14 +150,23 @@ class Workspace:
 
 
 def scan(X, lambdas, workspace: Optional[Workspace] = None, stream=None, flags: int = 0,
-         out=None):
-    """A1-A5: v_all [nl, m, m], s_all [nl, m, m] (double), z_all [nl, m] (double)."""
+         out=None, z_only=False):
+    """A1-A5: v_all [nl, m, m], s_all [nl, m, m] (double), z_all [nl, m] (double).
+    With z_only, v_all and s_all are not returned (None) and stay internal."""
     import torch
     _check_x(X)
     lam = _lams(lambdas)
     n, m = X.shape
     nl = lam.size
     ws = workspace or Workspace.for_shape(X.dtype, n, m, nl, X.device)
+    if z_only:
+        z_all = out if out is not None else torch.empty((nl, m), dtype=torch.float64,
+                                                        device=X.device)
+        f = load().l1line_scan_ex_f32 if X.dtype == torch.float32 else load().l1line_scan_ex_f64
+        _check(f(X.data_ptr(), n, m, lam.ctypes.data_as(ctypes.c_void_p), nl, None, None,
+                 z_all.data_ptr(), ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream), flags),
+               "l1line_scan")
+        return None, None, z_all, ws
     if out is None:
         v_all = torch.empty((nl, m, m), dtype=X.dtype, device=X.device)
         s_all = torch.empty((nl, m, m), dtype=torch.float64, device=X.device)
@@ -176,6 +203,140 @@ def fit(X, lambdas, workspace: Optional[Workspace] = None, stream=None, out=None
     if rc != OK:
         raise L1LineError(rc, "l1line_fit")
     return v, obj, js, ws
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _check(rc, where):
+    if rc != OK:
+        raise L1LineError(rc, where)
+
+
+def _fit_outputs(X, nl, out):
+    import torch
+    if out is not None:
+        return out
+    m = X.shape[1]
+    return (torch.empty((nl, m), dtype=X.dtype, device=X.device),
+            torch.empty(nl, dtype=torch.float64, device=X.device),
+            torch.empty(nl, dtype=torch.int32, device=X.device))
+
+
+def fit_subset(X, lambdas, jhat, workspace: Optional[Workspace] = None, stream=None, out=None):
+    """Algorithm 1 over the candidate jhat in `jhat` (int32 CUDA tensor) only:
+    v [nl, m], obj [nl], jstar [nl]."""
+    import torch
+    _check_x(X)
+    if jhat.dtype != torch.int32 or not jhat.is_cuda or jhat.dim() != 1:
+        raise TypeError("jhat must be a 1-D int32 CUDA tensor")
+    lam = _lams(lambdas)
+    n, m = X.shape
+    ws = workspace or Workspace.for_shape(X.dtype, n, m, lam.size, X.device)
+    v, obj, js = _fit_outputs(X, lam.size, out)
+    f = load().l1line_fit_subset_f32 if X.dtype == torch.float32 else load().l1line_fit_subset_f64
+    _check(f(X.data_ptr(), n, m, lam.ctypes.data_as(ctypes.c_void_p), lam.size, _ptr(jhat),
+             jhat.numel(), v.data_ptr(), obj.data_ptr(), js.data_ptr(), ctypes.c_void_p(ws.ptr),
+             ws.nbytes, _stream_ptr(stream)), "l1line_fit_subset")
+    return v, obj, js, ws
+
+
+def features(X, workspace: Optional[Workspace] = None, stream=None, raw=True):
+    """Column features of X: (raw [m, 3] or None, standardised [m, 3]) float32."""
+    import torch
+    _check_x(X)
+    n, m = X.shape
+    ws = workspace or Workspace.for_shape(X.dtype, n, m, 1, X.device)
+    r = torch.empty((m, 3), dtype=torch.float32, device=X.device) if raw else None
+    z = torch.empty((m, 3), dtype=torch.float32, device=X.device)
+    f = load().l1line_features_f32 if X.dtype == torch.float32 else load().l1line_features_f64
+    _check(f(X.data_ptr(), n, m, _ptr(r), _ptr(z), ctypes.c_void_p(ws.ptr), ws.nbytes,
+             _stream_ptr(stream)), "l1line_features")
+    return r, z
+
+
+def mlp_pack(theta, mlp=None, stream=None):
+    """Network image (uint8 CUDA tensor of MLP_BYTES) from flat float32 params."""
+    import torch
+    if mlp is None:
+        mlp = torch.empty(MLP_BYTES, dtype=torch.uint8, device=theta.device)
+    _check(load().l1line_mlp_pack(_ptr(theta), _ptr(mlp), _stream_ptr(stream)), "l1line_mlp_pack")
+    return mlp
+
+
+def mlp_forward(feat, mlp, rows=None, n=None, out=None, stream=None):
+    import torch
+    N = int(rows.numel() if rows is not None else (feat.shape[0] if n is None else n))
+    s = out if out is not None else torch.empty(N, dtype=torch.float32, device=feat.device)
+    _check(load().l1line_mlp_forward(_ptr(feat), _ptr(rows), N, _ptr(mlp), _ptr(s),
+                                     _stream_ptr(stream)), "l1line_mlp_forward")
+    return s
+
+
+class MlpWorkspace:
+    def __init__(self, N, device=None):
+        nb = int(load().l1line_mlp_workspace_bytes(int(N)))
+        if nb == 0:
+            raise ValueError("bad sample count")
+        self.ws = Workspace(nb, device)
+
+
+def mlp_backward(feat, mlp, dscores, rows=None, grad=None, workspace=None, stream=None):
+    import torch
+    N = int(dscores.numel())
+    g = grad if grad is not None else torch.empty(MLP_PARAMS, dtype=torch.float32,
+                                                  device=feat.device)
+    ws = (workspace or MlpWorkspace(N, feat.device)).ws
+    _check(load().l1line_mlp_backward(_ptr(feat), _ptr(rows), N, _ptr(mlp), _ptr(dscores),
+                                      _ptr(g), ctypes.c_void_p(ws.ptr), ws.nbytes,
+                                      _stream_ptr(stream)), "l1line_mlp_backward")
+    return g
+
+
+def rank_loss(scores, targets, offsets, rows=None, dscores=None, loss=None, stream=None):
+    import torch
+    nb = int(offsets.numel()) - 1
+    ds = dscores if dscores is not None else torch.empty_like(scores)
+    lo = loss if loss is not None else torch.empty(nb, dtype=torch.float32, device=scores.device)
+    _check(load().l1line_rank_loss(_ptr(scores), _ptr(targets), _ptr(rows), _ptr(offsets), nb,
+                                   _ptr(ds), _ptr(lo), _stream_ptr(stream)), "l1line_rank_loss")
+    return lo, ds
+
+
+def adam_step(theta, grad, m1, m2, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, mlp=None,
+              stream=None):
+    _check(load().l1line_adam_step(_ptr(theta), _ptr(grad), _ptr(m1), _ptr(m2), int(step),
+                                   float(lr), float(beta1), float(beta2), float(eps), _ptr(mlp),
+                                   _stream_ptr(stream)), "l1line_adam_step")
+
+
+def topk(scores, K, out=None, stream=None):
+    import torch
+    o = out if out is not None else torch.empty(int(K), dtype=torch.int32, device=scores.device)
+    _check(load().l1line_topk(_ptr(scores), scores.numel(), int(K), _ptr(o), _stream_ptr(stream)),
+           "l1line_topk")
+    return o
+
+
+def fit_proposed(X, lambdas, mlp, K, workspace: Optional[Workspace] = None, stream=None,
+                 out=None, idx=None):
+    """The learned path: features, network, top-K, exact fit of the K
+    candidates.  Returns v, obj, jstar, candidate indices, workspace."""
+    import torch
+    _check_x(X)
+    lam = _lams(lambdas)
+    n, m = X.shape
+    ws = workspace or Workspace.for_shape(X.dtype, n, m, lam.size, X.device)
+    v, obj, js = _fit_outputs(X, lam.size, out)
+    if idx is None:
+        idx = torch.empty(int(K), dtype=torch.int32, device=X.device)
+    f = (load().l1line_fit_proposed_f32 if X.dtype == torch.float32
+         else load().l1line_fit_proposed_f64)
+    _check(f(X.data_ptr(), n, m, lam.ctypes.data_as(ctypes.c_void_p), lam.size, _ptr(mlp), int(K),
+             _ptr(idx), v.data_ptr(), obj.data_ptr(), js.data_ptr(), ctypes.c_void_p(ws.ptr),
+             ws.nbytes, _stream_ptr(stream)), "l1line_fit_proposed")
+    return v, obj, js, idx, ws
 
 
 def status(ws: Workspace, stream=None) -> int:

@@ -1,0 +1,240 @@
+"""Learned jhat proposer on the GPU: every kernel against the float64 CPU
+reference in oracle/proposer_ref.py, and the subset / proposed fits against
+the oracle restricted to the same candidate list.
+
+Bars:
+  * features: l1 and l2 within 1e-6 relative of the float64 values (they are
+    float64 sums rounded once to float); the median exactly float(median);
+    the standardised features within 1e-5 of the reference standardisation of
+    the GPU's raw features.
+  * network forward, backward, loss and Adam: float arithmetic against float64
+    with the same binary16 weights; bounds are stated per test.
+  * top-K: exact indices.
+  * subset and proposed fits: the parity bar of tests/_parity.py against the
+    oracle run on the same candidate list.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import proposer_ref as P
+from paper_2402_16712_gb300 import datagen, l1line
+from tests._parity import assert_v_equal, tolerances
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _theta(seed, scale=0.25):
+    rng = np.random.default_rng(seed)
+    th = rng.normal(0.0, scale, P.N_PARAMS)
+    return th.astype(np.float32)
+
+
+def _dev(a, dtype=None):
+    return torch.from_numpy(np.ascontiguousarray(a if dtype is None else a.astype(dtype))).cuda()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("shape", [(1, 5), (2, 3), (7, 40), (300, 33), (1001, 70)])
+def test_features_match_reference(dtype, shape):
+    n, m = shape
+    rng = np.random.default_rng(n * 131 + m)
+    X = rng.laplace(0.0, 1.0, size=(n, m)).astype(dtype)
+    X[:, 0] = 0.0                      # zero column
+    if m > 2:
+        X[rng.random(n) < 0.3, 1] = 0.0  # many zeros
+        X[:, 2] = np.where(rng.random(n) < 0.5, -2.5, 2.5).astype(dtype)  # constant |x|
+    raw, z = l1line.features(_dev(X))
+    raw, z = raw.cpu().numpy(), z.cpu().numpy()
+    ref = P.raw_features(X)
+    assert np.allclose(raw[:, :2], ref[:, :2], rtol=1e-6, atol=0)
+    assert np.array_equal(raw[:, 2], ref[:, 2].astype(np.float32))
+    zr = P.standardise(raw.astype(np.float64))
+    assert np.allclose(z, zr, rtol=0, atol=1e-5)
+
+
+def test_network_forward_matches_reference():
+    th = _theta(1)
+    thd = _dev(th)
+    mlp = l1line.mlp_pack(thd)
+    rng = np.random.default_rng(2)
+    F = rng.normal(size=(200, 3)).astype(np.float32)
+    rows = rng.integers(0, 200, size=131).astype(np.int32)  # ragged tile, gathered
+    s = l1line.mlp_forward(_dev(F), mlp, rows=_dev(rows)).cpu().numpy()
+    thh = P.half_weights(th.astype(np.float64))
+    ref = P.forward(thh, F[rows].astype(np.float64))
+    # float sums of 128 products against float64: well inside 1e-4 of the scale
+    scale = 1.0 + np.abs(ref).max()
+    assert np.abs(s - ref).max() <= 1e-5 * scale
+    # the packed image holds the binary16 weights
+    img = mlp.cpu().numpy()
+    w1 = img[:768].view(np.float16).astype(np.float64)
+    assert np.array_equal(w1, thh[:384])
+
+
+def test_network_backward_matches_reference():
+    th = _theta(3)
+    thd = _dev(th)
+    mlp = l1line.mlp_pack(thd)
+    rng = np.random.default_rng(4)
+    F = rng.normal(size=(300, 3)).astype(np.float32)
+    rows = rng.permutation(300)[:197].astype(np.int32)
+    ds = rng.normal(size=197).astype(np.float32)
+    g = l1line.mlp_backward(_dev(F), mlp, _dev(ds), rows=_dev(rows)).cpu().numpy()
+    thh = P.half_weights(th.astype(np.float64))
+    ref = P.backward(thh, F[rows].astype(np.float64), ds.astype(np.float64))
+    err = np.abs(g - ref)
+    # float sums over <= 197 samples of products of O(1) terms
+    lim = 2e-5 * np.abs(ref) + 2e-5 * np.abs(ref).max()
+    assert (err <= lim).all(), (np.argmax(err - lim), err.max())
+    # deterministic: a second call gives the same bits
+    g2 = l1line.mlp_backward(_dev(F), mlp, _dev(ds), rows=_dev(rows)).cpu().numpy()
+    assert np.array_equal(g.view(np.uint32), g2.view(np.uint32))
+
+
+def test_rank_loss_matches_reference():
+    rng = np.random.default_rng(5)
+    offs = np.array([0, 40, 40, 41, 300, 1000], dtype=np.int64)  # empty and single-row instances
+    s = rng.normal(size=1000).astype(np.float32) * 3
+    u = rng.normal(size=1500).astype(np.float32) * 2
+    rows = rng.integers(0, 1500, size=1000).astype(np.int32)
+    loss, ds = l1line.rank_loss(_dev(s), _dev(u), _dev(offs), rows=_dev(rows))
+    loss, ds = loss.cpu().numpy(), ds.cpu().numpy()
+    L, dref = P.rank_loss(s.astype(np.float64), u[rows].astype(np.float64), offs)
+    assert abs(loss.mean() - L) <= 1e-6 * max(1.0, abs(L))
+    assert np.abs(ds - dref).max() <= 1e-7
+
+
+def test_adam_matches_reference():
+    rng = np.random.default_rng(6)
+    th = _theta(7)
+    thd = _dev(th)
+    m1 = torch.zeros_like(thd)
+    m2 = torch.zeros_like(thd)
+    mlp = torch.empty(l1line.MLP_BYTES, dtype=torch.uint8, device="cuda")
+    tr, a, b = th.astype(np.float64), np.zeros(th.size), np.zeros(th.size)
+    for step in range(1, 4):
+        g = rng.normal(size=th.size).astype(np.float32)
+        l1line.adam_step(thd, _dev(g), m1, m2, step, 1e-2, mlp=mlp)
+        tr, a, b = P.adam(tr, g.astype(np.float64), a, b, step, 1e-2)
+    got = thd.cpu().numpy()
+    assert np.abs(got - tr).max() <= 1e-6
+    # the image is the binary16 rounding of the float parameters
+    ref_img = l1line.mlp_pack(thd).cpu().numpy()
+    assert np.array_equal(mlp.cpu().numpy()[:34820], ref_img[:34820])  # all but the reserved words
+
+
+@pytest.mark.parametrize("m,K", [(1, 1), (10, 10), (33, 1), (1000, 32), (3000, 257), (5000, 5000)])
+def test_topk_exact(m, K):
+    rng = np.random.default_rng(m + K)
+    s = rng.integers(-20, 20, size=m).astype(np.float32) / 4  # many ties
+    s[rng.random(m) < 0.05] = np.nan
+    s[rng.random(m) < 0.02] = -0.0
+    got = l1line.topk(_dev(s), K).cpu().numpy()
+    assert np.array_equal(got, P.topk(s, K))
+
+
+def _oracle_subset(X, lams, cand):
+    # the oracle restricted to the candidate list (duplicates scored once)
+    jl = np.unique(cand)
+    return oracle.fit(X, lams, jlist=jl, want_all=True), jl
+
+
+def _check_subset(X, lams, cand, v, obj, js, where):
+    ref, jl = _oracle_subset(X, lams, cand)
+    rtol, atol = tolerances(X, ref["v_all"])
+    for t in range(len(lams)):
+        jg = int(js[t])
+        assert jg in set(jl.tolist()), (where, jg)
+        zr = ref["z_all"][t]
+        zbest = np.nanmin(zr[jl])
+        assert zr[jg] - zbest <= rtol * abs(zbest) + 2 * np.nanmax(atol[t][jl]), (where, t)
+        assert_v_equal(v[t], ref["v_all"][t, jg], f"{where} lambda {t}")
+        assert abs(obj[t] - zr[jg]) <= rtol * abs(zr[jg]) + atol[t, jg]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_subset_fit_matches_oracle(dtype):
+    X, _, _ = datagen.planted(datagen.Planted(400, 37, 5, 0.1, 0.1, 10.0, 9, np.dtype(dtype).name))
+    lams = np.array([0.0, 0.2, 1.5])
+    cand = np.array([30, 2, 2, 17, 36, 0], dtype=np.int32)  # unsorted, one duplicate
+    v, obj, js, ws = l1line.fit_subset(_dev(X), lams, _dev(cand))
+    assert l1line.status(ws) == l1line.OK
+    _check_subset(X, lams, cand, v.cpu().numpy(), obj.cpu().numpy(), js.cpu().numpy(), "subset")
+    # the listed jhat's objectives are those of the full fit
+    v_all, s_all, z_all, _ = l1line.scan(_dev(X), lams)
+    vf, objf, jsf, _ = l1line.fit(_dev(X), lams)
+    zf = z_all.cpu().numpy()
+    for t in range(3):
+        jg = int(js[t])
+        assert obj[t].item() == zf[t, jg]
+        assert zf[t, jg] == zf[t, np.unique(cand)].min()
+
+
+def test_subset_fit_bad_index_reports_arg_error():
+    X, _, _ = datagen.planted(datagen.Planted(50, 8, 2, 0.1, 0.1, 5.0, 3, "float32"))
+    cand = np.array([1, 8], dtype=np.int32)  # 8 is out of range: checked on the device
+    v, obj, js, ws = l1line.fit_subset(_dev(X), [0.1], _dev(cand))
+    assert l1line.status(ws) == l1line.ERR_ARG
+    X2 = _dev(X)
+    v, obj, js, ws = l1line.fit_subset(X2, [0.1], _dev(np.array([1, 3], dtype=np.int32)),
+                                       workspace=ws)
+    assert l1line.status(ws) == l1line.OK  # the workspace is usable again
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_proposed_fit_is_the_subset_fit_of_the_network_top_k(dtype):
+    X, _, _ = datagen.planted(datagen.Planted(700, 90, 6, 0.1, 0.15, 10.0, 11,
+                                              np.dtype(dtype).name))
+    lams = np.array([0.2])
+    mlp = l1line.mlp_pack(_dev(_theta(12)))
+    K = 9
+    v, obj, js, idx, ws = l1line.fit_proposed(_dev(X), lams, mlp, K)
+    assert l1line.status(ws) == l1line.OK
+    idx = idx.cpu().numpy()
+    # stepwise: features -> network -> top-K through the separate entry points
+    _, z = l1line.features(_dev(X))
+    s = l1line.mlp_forward(z, mlp)
+    assert np.array_equal(idx, l1line.topk(s, K).cpu().numpy())
+    # and the reference chain picks the same candidates (scores well separated
+    # compared with the float error of the network)
+    sr = P.forward(P.half_weights(_theta(12).astype(np.float64)),
+                   P.standardise(P.raw_features(X)))
+    gap = np.sort(sr)[::-1]
+    if gap[K - 1] - gap[K] > 1e-3:
+        assert np.array_equal(idx, P.topk(sr, K))
+    _check_subset(X, lams, idx, v.cpu().numpy(), obj.cpu().numpy(), js.cpu().numpy(), "proposed")
+
+
+def test_training_steps_reduce_the_loss():
+    # a few hundred Adam steps on a fixed toy ranking task: the score should
+    # learn to prefer a large first feature
+    rng = np.random.default_rng(13)
+    nb, per = 32, 50
+    F = rng.normal(size=(nb * per, 3)).astype(np.float32)
+    u = (3.0 * F[:, 0] - F[:, 2]).astype(np.float32)
+    offs = (np.arange(nb + 1) * per).astype(np.int64)
+    th = (np.random.default_rng(14).normal(size=P.N_PARAMS) * 0.1).astype(np.float32)
+    thd, Fd, ud, od = _dev(th), _dev(F), _dev(u), _dev(offs)
+    m1, m2 = torch.zeros_like(thd), torch.zeros_like(thd)
+    mlp = l1line.mlp_pack(thd)
+    ws = l1line.MlpWorkspace(nb * per)
+    first = None
+    for step in range(1, 301):
+        s = l1line.mlp_forward(Fd, mlp)
+        loss, ds = l1line.rank_loss(s, ud, od)
+        if first is None:
+            first = float(loss.mean())
+        g = l1line.mlp_backward(Fd, mlp, ds, workspace=ws)
+        l1line.adam_step(thd, g, m1, m2, step, 3e-3, mlp=mlp)
+    last = float(l1line.rank_loss(l1line.mlp_forward(Fd, mlp), ud, od)[0].mean())
+    # entropy floor of the targets
+    floor = P.rank_loss(u.astype(np.float64), u.astype(np.float64), offs)[0]
+    assert last < first and last - floor < 0.2 * (first - floor), (first, last, floor)
