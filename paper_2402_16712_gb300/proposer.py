@@ -35,6 +35,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 THETA_PATH = os.path.join(_HERE, "proposer_theta.f32")
 TRAIN_SEEDS = (1, 20000)        # inclusive
 VAL_SEEDS = (30001, 30400)      # validation during training (disjoint from both)
+VAL_EVAL_SEED0 = 40001           # calibration of K at the evaluation shape
 TEMPERATURE, TOP = 0.25, 16
 K_DEFAULT = 32
 
@@ -220,20 +221,81 @@ def train(out_dir, n_train=None, epochs=24, batch_instances=16, lr=2e-3, seed=0,
 # ---------------------------------------------------------------------------
 # evaluation
 # ---------------------------------------------------------------------------
-def evaluate(theta_path=THETA_PATH, count=200, Ks=(K_DEFAULT, 64, 128), n=5000, m=1000,
-             device=None, log=None, seed0=datagen.PROPOSER_HELDOUT_SEED0):
-    """Held-out float32 n x m instances: for each K, the learned top-K path, a
-    column-l1 top-K heuristic and a random top-K against the full scan.  Zero
-    regret means the same objective as the full scan (bit for bit: the
-    candidates' objectives are computed by the same kernels).  Times are
-    CUDA-event times of one call each, L2 flushed before it."""
+def _ranks_of_best(z, score):
+    """Smallest K whose top-K by `score` (ties to the smaller index) holds a
+    jhat of minimal z, and the relative regret min(z over top-K) / min z - 1
+    for every K (index K - 1)."""
+    order = np.lexsort((np.arange(score.size), -score))
+    pos = np.empty(score.size, dtype=np.int64)
+    pos[order] = np.arange(score.size)
+    zmin = z.min()
+    regret = (np.minimum.accumulate(z[order]) - zmin) / (abs(zmin) if zmin != 0 else 1.0)
+    return int(pos[z == zmin].min()) + 1, regret
+
+
+def rank_study(count, seed0, n=5000, m=1000, theta_path=THETA_PATH, device=None, log=None):
+    """Per instance (float32 n x m, proposer_spec seeds seed0 ...): the exact
+    objectives of every jhat (one scan) and, for the learned scores, the l1,
+    l2 and median features and a random order, the smallest K that keeps a
+    best jhat.  Zero regret at K <=> that rank <= K."""
     import torch
     device = device or "cuda"
+    mlp = network(device, theta_path)
+    ws = l1line.Workspace.for_shape("float32", n, m, 1, device)
+    rng = np.random.default_rng(seed0)
+    ranks = {"learned": [], "l1": [], "l2": [], "median": [], "random": []}
+    regrets = {k: [] for k in ranks}
+    for i in range(count):
+        spec = datagen.proposer_spec(seed0 + i, n=n, m=m)
+        X, _, _ = datagen.planted_torch(spec, device)
+        raw, fz = l1line.features(X, workspace=ws)
+        s = l1line.mlp_forward(fz, mlp)
+        _, _, z, _ = l1line.scan(X, [datagen.PROPOSER_LAMBDA], workspace=ws, z_only=True)
+        if l1line.status(ws) != l1line.OK:
+            raise RuntimeError(f"instance {spec.seed} failed on the device")
+        z = z[0].cpu().numpy()
+        raw = raw.cpu().numpy().astype(np.float64)
+        for key, sc in (("learned", s.cpu().numpy().astype(np.float64)), ("l1", raw[:, 0]),
+                        ("l2", raw[:, 1]), ("median", raw[:, 2]), ("random", rng.random(m))):
+            r, reg = _ranks_of_best(z, sc)
+            ranks[key].append(r)
+            regrets[key].append(reg)
+        if log and (i + 1) % 50 == 0:
+            log(f"  {i + 1} instances ranked")
+    out = {k: np.array(v) for k, v in ranks.items()}
+    out["regret"] = {k: np.array(v) for k, v in regrets.items()}  # [instance, K - 1]
+    return out
+
+
+def k_for(ranks, frac):
+    """Smallest K with zero regret on at least `frac` of the instances."""
+    r = np.sort(ranks)
+    return int(r[int(np.ceil(frac * r.size)) - 1])
+
+
+def evaluate(theta_path=THETA_PATH, count=200, Ks=(32, 64, 128, 256, 512), n=5000, m=1000,
+             device=None, log=None, seed0=datagen.PROPOSER_HELDOUT_SEED0, target=0.99,
+             calib_count=200):
+    """Held-out float32 n x m instances.
+
+    1. K_target: the smallest K with zero regret on `target` of a calibration
+       set of the same shape (seeds VAL_EVAL_SEED0 ...), chosen before the
+       held-out set is looked at.
+    2. Held-out zero-regret curves (learned, each single feature, random) from
+       one exact scan per instance, at the listed K and K_target.
+    3. Times (CUDA events, L2 flushed before each call) of the full fit and of
+       the learned path at each K; the learned path's objective is checked
+       against the scan (the same kernels give the same bits)."""
+    import torch
+    device = device or "cuda"
+    cal = rank_study(calib_count, VAL_EVAL_SEED0, n, m, theta_path, device, log)
+    k_target = k_for(cal["learned"], target)
+    Ks = tuple(sorted(set(Ks) | {k_target}))
+    held = rank_study(count, seed0, n, m, theta_path, device, log)
     mlp = network(device, theta_path)
     lam = [datagen.PROPOSER_LAMBDA]
     ws = l1line.Workspace.for_shape("float32", n, m, 1, device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    rng = np.random.default_rng(7)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 
     def timed(fn):
@@ -244,45 +306,37 @@ def evaluate(theta_path=THETA_PATH, count=200, Ks=(K_DEFAULT, 64, 128), n=5000, 
         torch.cuda.synchronize()
         return r, ev[0].elapsed_time(ev[1])
 
-    regret = {(key, K): [] for K in Ks for key in ("learned", "l1", "random")}
     t_full, t_prop = [], {K: [] for K in Ks}
-    for i in range(count):
+    n_time = min(count, 40)
+    for i in range(n_time):
         spec = datagen.proposer_spec(seed0 + i, n=n, m=m)
         X, _, _ = datagen.planted_torch(spec, device)
-        if i == 0:  # warm-up of both paths
+        if i == 0:
             l1line.fit(X, lam, workspace=ws)
             for K in Ks:
                 l1line.fit_proposed(X, lam, mlp, K, workspace=ws)
         (_, of, _, _), tf = timed(lambda: l1line.fit(X, lam, workspace=ws))
-        if l1line.status(ws) != l1line.OK:
-            raise RuntimeError(f"held-out instance {spec.seed} failed on the device")
-        zfull = float(of[0])
         t_full.append(tf)
-        raw, _ = l1line.features(X, workspace=ws)
-        l1col = raw[:, 0].contiguous()
         for K in Ks:
             (_, op, _, _, _), tp = timed(lambda: l1line.fit_proposed(X, lam, mlp, K, workspace=ws))
-            if l1line.status(ws) != l1line.OK:
-                raise RuntimeError(f"held-out instance {spec.seed} failed on the device")
             t_prop[K].append(tp)
-            _, ol, _, _ = l1line.fit_subset(X, lam, l1line.topk(l1col, K), workspace=ws)
-            cand = np.sort(rng.choice(m, K, replace=False)).astype(np.int32)
-            _, orr, _, _ = l1line.fit_subset(X, lam, torch.from_numpy(cand).to(device),
-                                             workspace=ws)
-            for key, o in (("learned", op), ("l1", ol), ("random", orr)):
-                z = float(o[0])
-                regret[(key, K)].append((z - zfull) / abs(zfull) if zfull != 0 else z - zfull)
-        if log and (i + 1) % 20 == 0:
-            log(f"  {i + 1} held-out instances")
-    out = {"instances": count, "n": n, "m": m, "lambda": lam[0],
-           "full_ms_median": float(np.median(t_full)), "per_K": {}}
+            zero = bool(float(op[0]) == float(of[0]))
+            if zero != bool(held["learned"][i] <= K):
+                raise RuntimeError(f"instance {spec.seed}: learned path and rank study disagree")
+        if l1line.status(ws) != l1line.OK:
+            raise RuntimeError(f"held-out instance {spec.seed} failed on the device")
+    out = {"instances": count, "timed_instances": n_time, "n": n, "m": m, "lambda": lam[0],
+           "target": target, "calibration_instances": calib_count, "K_target": k_target,
+           "full_ms_median": float(np.median(t_full)), "per_K": {},
+           "K_for_target_on_heldout": {k: k_for(v, target) for k, v in held.items()
+                                       if k != "regret"}}
     for K in Ks:
         d = {"learned_ms_median": float(np.median(t_prop[K])),
-             "speedup_median": float(np.median(t_full) / np.median(t_prop[K]))}
-        for key in ("learned", "l1", "random"):
-            r = np.array(regret[(key, K)])
-            d[key] = {"zero_regret_frac": float(np.mean(r == 0.0)),
-                      "mean_rel_regret": float(r.mean()), "max_rel_regret": float(r.max())}
+             "speedup_median": float(np.median(t_full) / np.median(t_prop[K])),
+             "zero_regret_frac": {k: float(np.mean(v <= K)) for k, v in held.items()
+                                  if k != "regret"},
+             "mean_rel_regret": {k: float(v[:, K - 1].mean()) for k, v in held["regret"].items()},
+             "max_rel_regret": {k: float(v[:, K - 1].max()) for k, v in held["regret"].items()}}
         out["per_K"][str(K)] = d
     return out
 
@@ -298,7 +352,7 @@ def main(argv=None):
     e = sub.add_parser("eval")
     e.add_argument("--theta", default=THETA_PATH)
     e.add_argument("--count", type=int, default=200)
-    e.add_argument("--K", type=int, nargs="+", default=[K_DEFAULT, 64, 128])
+    e.add_argument("--K", type=int, nargs="+", default=[32, 64, 128, 256, 512])
     e.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     from . import build

@@ -116,3 +116,46 @@ def test_batched_argument_errors(lib):
                                     loff.ctypes.data_as(P), P(256), P(256), P(256), P(1024),
                                     1 << 30, None)
     assert rc == l1line.ERR_ARG  # negative lambda
+
+
+def test_proposer_argument_errors(lib):
+    P = ctypes.c_void_p
+    p = P(256)
+    lam = np.array([0.2])
+    L = lam.ctypes.data_as(P)
+    # top-K: K outside 1..m, null pointers
+    assert lib.l1line_topk(p, 10, 0, p, None) == l1line.ERR_ARG
+    assert lib.l1line_topk(p, 10, 11, p, None) == l1line.ERR_ARG
+    assert lib.l1line_topk(None, 10, 3, p, None) == l1line.ERR_ARG
+    # network: null or misaligned image, empty batch
+    assert lib.l1line_mlp_forward(p, None, 0, p, p, None) == l1line.ERR_ARG
+    assert lib.l1line_mlp_forward(p, None, 10, P(264), p, None) == l1line.ERR_ARG
+    assert lib.l1line_mlp_forward(p, None, 10, None, p, None) == l1line.ERR_ARG
+    assert lib.l1line_mlp_workspace_bytes(0) == 0
+    assert lib.l1line_mlp_workspace_bytes(64) == 17153 * 4 + 252  # one CTA row, 256-aligned
+    assert lib.l1line_mlp_backward(p, None, 100, p, p, p, None, 1 << 20, None) == \
+        l1line.ERR_WORKSPACE
+    assert lib.l1line_mlp_backward(p, None, 100, p, p, p, P(1024), 16, None) == l1line.ERR_WORKSPACE
+    # Adam: step >= 1, betas in [0, 1), finite learning rate
+    assert lib.l1line_adam_step(p, p, p, p, 0, 1e-3, 0.9, 0.999, 1e-8, None, None) == l1line.ERR_ARG
+    assert lib.l1line_adam_step(p, p, p, p, 1, 1e-3, 1.0, 0.999, 1e-8, None, None) == l1line.ERR_ARG
+    assert lib.l1line_adam_step(p, p, p, p, 1, float("inf"), 0.9, 0.999, 1e-8, None, None) == \
+        l1line.ERR_ARG
+    assert lib.l1line_rank_loss(p, p, None, p, 0, p, p, None) == l1line.ERR_ARG
+    # subset / proposed fits
+    assert lib.l1line_fit_subset_f32(p, 10, 5, L, 1, None, 2, p, p, p, P(1024), 1 << 30,
+                                     None) == l1line.ERR_ARG
+    assert lib.l1line_fit_subset_f32(p, 10, 5, L, 1, p, 0, p, p, p, P(1024), 1 << 30,
+                                     None) == l1line.ERR_ARG
+    assert lib.l1line_fit_proposed_f32(p, 10, 5, L, 1, p, 6, None, p, p, p, P(1024), 1 << 30,
+                                       None) == l1line.ERR_ARG
+    assert lib.l1line_fit_proposed_f64(p, 10, 5, L, 1, None, 2, None, p, p, p, P(1024), 1 << 30,
+                                       None) == l1line.ERR_ARG
+    assert lib.l1line_features_f32(p, 10, 5, None, None, P(1024), 1 << 30, None) == l1line.ERR_ARG
+
+
+def test_committed_network_parameters():
+    from paper_2402_16712_gb300 import proposer
+    th = proposer.load_theta()
+    assert th.dtype == np.float32 and th.size == l1line.MLP_PARAMS
+    assert np.isfinite(th).all() and np.abs(th).max() < 65504  # binary16-representable range

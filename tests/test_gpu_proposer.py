@@ -238,3 +238,33 @@ def test_training_steps_reduce_the_loss():
     # entropy floor of the targets
     floor = P.rank_loss(u.astype(np.float64), u.astype(np.float64), offs)[0]
     assert last < first and last - floor < 0.2 * (first - floor), (first, last, floor)
+
+
+def test_trained_network_gain_over_the_method_without_it():
+    """The committed network on held-out instances of the evaluation shape
+    (float32 5000 x 1000, seeds never used in training): its top-32 holds the
+    exact best jhat far more often than a random top-32 and at least as often
+    as the column-l1 heuristic (one instance of slack), and the learned path
+    is much faster than the full scan, which it replaces."""
+    from paper_2402_16712_gb300 import proposer
+    count = 24
+    r = proposer.rank_study(count, datagen.PROPOSER_HELDOUT_SEED0)
+    assert (r["regret"]["learned"][np.arange(count), r["learned"] - 1] == 0).all()
+    learned = np.mean(r["learned"] <= 32)
+    assert learned >= np.mean(r["random"] <= 32) + 0.3
+    assert learned >= np.mean(r["l1"] <= 32) - 1.0 / count
+    X, _, _ = datagen.planted_torch(datagen.proposer_spec(datagen.PROPOSER_HELDOUT_SEED0, n=5000,
+                                                          m=1000), "cuda")
+    mlp = proposer.network()
+    ws = l1line.Workspace.for_shape("float32", 5000, 1000, 1)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    for _ in range(2):
+        ev[0].record()
+        l1line.fit(X, [0.2], workspace=ws)
+        ev[1].record()
+        l1line.fit_proposed(X, [0.2], mlp, 32, workspace=ws)
+        ev[2].record()
+    torch.cuda.synchronize()
+    assert l1line.status(ws) == l1line.OK
+    t_full, t_prop = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    assert t_prop * 5 < t_full, (t_full, t_prop)
