@@ -60,7 +60,7 @@ def _src_hash() -> str:
 def _profile_traffic():
     """DRAM bytes per pair-kernel launch from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "k_pairs_paper_size_f32.md")
+    p = os.path.join(ROOT, "profiles", "launches_paper_size_f32.md")
     if not os.path.exists(p):
         return None
     txt = open(p).read()
@@ -189,7 +189,7 @@ def run_gpu(args):
     import numpy as np
     import torch
 
-    from paper_2402_16712_gb300 import datagen, l1line
+    from paper_2402_16712_gb300 import autotune, datagen, l1line
 
     rank, world, local = _env_rank()
     dist = None
@@ -230,6 +230,15 @@ def run_gpu(args):
     rc = l1line.status(ws, stream)
     if rc != l1line.OK:
         raise SystemExit(f"fit failed on the device: {l1line.status_string(rc)}")
+    # the library's autotuner picks the pair kernel's launch for this shape
+    # (untimed; results do not depend on it)
+    with torch.cuda.stream(stream):
+        tuning = autotune.apply(torch.float32, n, m, 1, flush=flush,
+                                run=lambda: l1line.fit(Xd, lams, workspace=ws, stream=stream,
+                                                       out=out))
+        for _ in range(2):
+            l1line.fit(Xd, lams, workspace=ws, stream=stream, out=out)
+    stream.synchronize()
     launches_per_fit = l1line.last_launch_count()
 
     # ---- timed region: K fits, L2 flushed before each ----------------------
@@ -263,6 +272,7 @@ def run_gpu(args):
     value = world * args.steps * pairs / (tot_ms * 1e-3)
 
     # ---- float64 input, same workload (reported beside the headline) -------
+    l1line.set_tuning(None)
     X64 = X.astype(np.float64)
     Xd64 = torch.from_numpy(X64).to(dev)
     ws64 = l1line.Workspace.for_shape(torch.float64, n, m, 1, dev)
@@ -279,6 +289,7 @@ def run_gpu(args):
     ms64 = e0.elapsed_time(e1) / k64
 
     # ---- end to end through the ABI with host buffers ----------------------
+    autotune.apply(torch.float32, n, m, 1)  # the cached tuning of the headline shape
     Xh = torch.from_numpy(X).pin_memory()
     vh = torch.empty((1, m), dtype=torch.float32).pin_memory()
     oh = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -315,7 +326,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "m": m, "lambda": float(lams[0]),
                    "pairs_per_fit": pairs, "parallelism": f"replicas x{world} (one instance per GPU)",
-                   "l2": "flushed before every timed step (512 MiB write)"},
+                   "l2": "flushed before every timed step (512 MiB write)",
+                   "tuning": {"applied": tuning, "plan": l1line.plan(torch.float32, n, m)}},
         "fits_per_s": world * args.steps / (tot_ms * 1e-3),
         "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
@@ -363,7 +375,7 @@ def measure_extras(dev, stream, flush):
     import numpy as np
     import torch
 
-    from paper_2402_16712_gb300 import datagen, l1line
+    from paper_2402_16712_gb300 import autotune, datagen, l1line
     out = {}
     # lambda path: n=1000, m=500 float32, 32 lambdas in one fit
     X, lams, _ = datagen.lambda_path("float32")
@@ -375,12 +387,17 @@ def measure_extras(dev, stream, flush):
            torch.empty(lams.size, dtype=torch.int32, device=dev))
     with torch.cuda.stream(stream):
         l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
+        tuning = autotune.apply(torch.float32, n, m, lams.size, flush=flush,
+                                run=lambda: l1line.fit(Xd, lams, workspace=ws, stream=stream,
+                                                       out=res))
+        l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
     stream.synchronize()
     launches = l1line.last_launch_count()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
     ms = _replay_ms(g, stream, 10, flush)
+    l1line.set_tuning(None)
     if l1line.status(ws, stream) != l1line.OK:
         raise SystemExit("lambda-path fit failed on the device")
     pl = m * (m - 1) * lams.size
@@ -388,7 +405,8 @@ def measure_extras(dev, stream, flush):
         "workload": f"n={n}, m={m} float32, {lams.size} lambdas logspace(-3,1), one fit "
                     "(one pair launch for all lambdas), CUDA graph replay, L2 flushed",
         "ms_per_step": ms, "pair_lambdas_per_s": pl / (ms * 1e-3),
-        "fits_per_s": lams.size / (ms * 1e-3), "gpu_launches_per_step": launches}
+        "fits_per_s": lams.size / (ms * 1e-3), "gpu_launches_per_step": launches,
+        "tuning": tuning}
     del Xd, ws, res, g
     # uneven batch: 256 instances, n~U[100,5000], m~U[10,500], lambda=0.2
     batch = datagen.uneven_batch(256)
@@ -396,12 +414,18 @@ def measure_extras(dev, stream, flush):
     bat = l1line.Batched(Xs, [lb for _, lb in batch], device=dev)
     with torch.cuda.stream(stream):
         bat.run(stream)
+        nmax = max(int(Xb.shape[0]) for Xb, _ in batch)
+        mmax = max(int(Xb.shape[1]) for Xb, _ in batch)
+        btune = autotune.apply(torch.float32, nmax, mmax, len(batch), kind="batch",
+                               run=lambda: bat.run(stream))
+        bat.run(stream)
     stream.synchronize()
     launches = l1line.last_launch_count()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=stream):
         bat.run(stream)
     ms = _replay_ms(g, stream, 5)
+    l1line.set_tuning(None)
     if bat.status(stream) != l1line.OK:
         raise SystemExit("batched fit failed on the device")
     pairs = int(sum(int(Xb.shape[1]) * (int(Xb.shape[1]) - 1) for Xb, _ in batch))
@@ -409,7 +433,8 @@ def measure_extras(dev, stream, flush):
         "workload": "256 float32 instances, n~U[100,5000], m~U[10,500], lambda=0.2, one "
                     "persistent pair launch, CUDA graph replay (inputs 658 MB > L2)",
         "ms_per_step": ms, "fits_per_s": len(batch) / (ms * 1e-3),
-        "pairs_per_s": pairs / (ms * 1e-3), "gpu_launches_per_step": launches}
+        "pairs_per_s": pairs / (ms * 1e-3), "gpu_launches_per_step": launches,
+        "tuning": btune}
     return out
 
 

@@ -306,6 +306,32 @@ const char *l1line_status_string(int status);
  * accounting); host-side counter, per calling thread. */
 int l1line_last_launch_count(void);
 
+/*
+ * Tuning of the pair kernel's launch (for an autotuner).  Every field 0 means
+ * "the planner's choice".  Results do not depend on the tuning (every
+ * decision stays exact); only the speed does.
+ *   warps        warps per CTA, 1..8
+ *   ctas_per_sm  CTAs per SM that the shared-memory plan is sized for, 1..3
+ *   kchunk       k per CTA of single-instance calls (the batched call always
+ *                gives a CTA a whole column jhat)
+ *   d0           half-width, in positions of the 64 weight-proportional
+ *                samples of column jhat, of the first bracket around the
+ *                weighted median, 1..24 (planner: 6)
+ * l1line_set_tuning applies to the later calls of the calling thread (NULL
+ * restores the planner); a tuning whose candidate lists do not fit shared
+ * memory makes those calls return L1L_ERR_UNSUPPORTED.  l1line_plan reports
+ * the plan such a call would use for nj scored jhat (nj = m for a full scan)
+ * on the current device.
+ */
+typedef struct l1line_tuning {
+    int32_t warps;
+    int32_t ctas_per_sm;
+    int32_t kchunk;
+    int32_t d0;
+} l1line_tuning;
+int l1line_set_tuning(const l1line_tuning *t);
+int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out);
+
 /* Measurement hook: when both are non-NULL (cudaEvent_t), later scan and fit
  * calls from this thread record `start` on their stream just before the pair
  * kernel (steps A2-A4) is launched and `stop` just after it, so the caller can

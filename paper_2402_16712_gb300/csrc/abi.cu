@@ -20,6 +20,7 @@ using namespace l1l;
 namespace {
 
 thread_local int g_last_launches = 0;
+thread_local Tune g_tune;  // l1line_set_tuning
 thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -136,6 +137,7 @@ int scan_setup(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t 
     a.inst = 0;
     a.jlist = nullptr;
     a.nj = m;
+    a.d0 = D0_DEFAULT;
     c.z = z_all ? z_all : reinterpret_cast<double *>(c.base + L.z_all);
     return L1L_OK;
 }
@@ -155,8 +157,9 @@ int scan_pairs(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jli
     ScanArgs<T> &a = c.a;
     a.jlist = jlist;
     a.nj = nj;
-    const PairPlan plan = plan_pairs<T>(a.n, a.m, c.sms, nj);
+    const PairPlan plan = plan_pairs<T>(a.n, a.m, c.sms, nj, g_tune);
     if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
+    a.d0 = plan.d0;
     const bool prof = g_ev_start && g_ev_stop;
     for (int64_t t0 = 0; t0 < nl; t0 += MAX_LAMBDA_PER_LAUNCH) {
         const int nlc = (int)((nl - t0) < MAX_LAMBDA_PER_LAUNCH ? (nl - t0) : MAX_LAMBDA_PER_LAUNCH);
@@ -490,6 +493,36 @@ const char *l1line_status_string(int status) {
 
 int l1line_last_launch_count(void) { return g_last_launches; }
 
+int l1line_set_tuning(const l1line_tuning *t) {
+    if (!t) {
+        g_tune = Tune();
+        return L1L_OK;
+    }
+    if (t->warps < 0 || t->warps > 8 || t->ctas_per_sm < 0 || t->ctas_per_sm > 3 ||
+        t->kchunk < 0 || t->d0 < 0 || t->d0 > 24)
+        return L1L_ERR_ARG;
+    g_tune.warps = t->warps;
+    g_tune.ctas = t->ctas_per_sm;
+    g_tune.kchunk = t->kchunk;
+    g_tune.d0 = t->d0;
+    return L1L_OK;
+}
+
+int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out) {
+    if (!out || n < 1 || m < 1 || nj < 1) return L1L_ERR_ARG;
+    if (dtype != L1L_DTYPE_F32 && dtype != L1L_DTYPE_F64) return L1L_ERR_ARG;
+    const int sms = num_sms();
+    if (sms <= 0) return L1L_ERR_CUDA;
+    const PairPlan p = dtype == L1L_DTYPE_F32 ? plan_pairs<float>(n, m, sms, nj, g_tune)
+                                              : plan_pairs<double>(n, m, sms, nj, g_tune);
+    if (p.warps == 0) return L1L_ERR_UNSUPPORTED;
+    out->warps = p.warps;
+    out->ctas_per_sm = p.ctas;
+    out->kchunk = p.kchunk;
+    out->d0 = p.d0;
+    return L1L_OK;
+}
+
 int l1line_profile_events(void *start, void *stop) {
     if (start && stop) {
         g_ev_start = static_cast<cudaEvent_t>(start);
@@ -567,7 +600,9 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
         return L1L_ERR_WORKSPACE;
     const int sms = num_sms();
     if (sms <= 0) return L1L_ERR_CUDA;
-    const PairPlan plan = plan_pairs<T>(sh.max_n, 1, sms, 1);
+    Tune tb = g_tune;
+    tb.kchunk = 0;  // the persistent kernel's unit is a whole column jhat
+    const PairPlan plan = plan_pairs<T>(sh.max_n, 1, sms, 1, tb);
     if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
 
     std::unique_ptr<BatchDesc<T>> bd(new BatchDesc<T>());
@@ -590,6 +625,7 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
     bd->lay_npad = (int32_t)((sh.max_n + 31) & ~int64_t(31));
     bd->cap = plan.cap;
     bd->force_exact = (flags & L1L_FLAG_FORCE_EXACT) ? 1 : 0;
+    bd->d0 = plan.d0;
     int64_t units = 0, tiles = 0, ztasks = 0, lams = 0;
     for (int64_t p = 0; p < batch; ++p) {
         const int b = sh.order[(size_t)p];

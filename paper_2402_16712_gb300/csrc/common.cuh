@@ -230,7 +230,13 @@ template <typename T> struct ScanArgs {
     int inst;          // instance index recorded in slow-list entries (batched calls)
     const int32_t *jlist;  // device list of the jhat to score (nullptr: all m)
     int64_t nj;            // entries of jlist (m when jlist is nullptr)
+    int d0;                // first-bracket half-width of the selection, sample positions
 };
+
+// Default first-bracket half-width (of NSAMP = 64 weight-proportional samples):
+// +-4 samples keep ~12% of the rows as candidates and miss the median in ~5% of
+// the pairs (a miss costs one more pass); the autotuner may choose another.
+constexpr int D0_DEFAULT = 4;
 
 constexpr int MAX_LAMBDA_PER_LAUNCH = 256;
 
@@ -261,7 +267,7 @@ template <typename T> struct BatchDesc {
     int32_t lay_npad;    // shared-memory layout rows (largest n rounded up to 32)
     int32_t cap;         // candidate slots per warp
     int32_t force_exact;
-    int32_t pad;
+    int32_t d0;          // first-bracket half-width of the selection
     BatchInst<T> inst[MAX_BATCH];
     int64_t unit_begin[MAX_BATCH + 1];  // prefix of m over instances
     int32_t tile_begin[MAX_BATCH + 1];

@@ -50,6 +50,7 @@ __device__ __forceinline__ ScanArgs<T> inst_args(const BatchDesc<T> &bd, int b,
     a.inst = b;
     a.jlist = nullptr;
     a.nj = a.m;
+    a.d0 = bd.d0;
     return a;
 }
 

@@ -91,24 +91,30 @@ template <typename T> int64_t max_rows_pairs() {
     return n;
 }
 
-template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj) {
-    PairPlan p{0, 0, 0, 0, 0};
+template <typename T>
+PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune) {
+    PairPlan p{0, 0, 0, 0, 0, 0, 0};
     const int64_t npad = (n + 31) & ~int64_t(31);
     if (n > max_rows_pairs<T>()) return p;
     const size_t cb = PairSmem<T>::col_bytes(npad);
-    // Per-lane candidate quota wanted: the level-0 bracket holds ~15% of the
-    // rows, i.e. mu = 0.15 n/32 per lane; ask for mu + 3.5 sqrt(mu) + 1 so that
-    // the busiest of 32 lanes rarely overflows (an overflow costs one more pass).
-    const double mu = 0.15 * (double)npad / 32.0;
+    const int d0 = tune.d0 > 0 ? tune.d0 : D0_DEFAULT;
+    // Per-lane candidate quota wanted: the level-0 bracket (+-d0 of 64 weight
+    // samples) holds ~2.5% of the rows per sample position, i.e. mu = 0.025 d0
+    // n/32 per lane; ask for mu + 3.5 sqrt(mu) + 1 so that the busiest of 32
+    // lanes rarely overflows (an overflow costs one more pass).
+    const double mu = 0.025 * (double)d0 * (double)npad / 32.0;
     const int64_t qt_need = std::min<int64_t>(npad / 32, (int64_t)ceil(mu + 3.5 * sqrt(mu) + 1.0));
     // Up to three 8-warp CTAs per SM fit the register budget (80 registers x
-    // 256 threads).  Over 1-3 CTAs per SM and 1-8 warps per CTA, keep the plan
-    // with the most resident warps whose lists meet the quota in 228 KB of
-    // shared memory (1 KB reserved per CTA, static arrays included).
-    int w = 0, cap = 0, best = 0;
-    for (int ctas = 3; ctas >= 1; --ctas) {
+    // 256 threads).  Over 1-3 CTAs per SM and 1-8 warps per CTA (or the
+    // caller's choice), keep the plan with the most resident warps whose lists
+    // meet the quota in 228 KB of shared memory (1 KB reserved per CTA,
+    // static arrays included).
+    int w = 0, cap = 0, best = 0, nc = 0;
+    const int c_hi = tune.ctas > 0 ? tune.ctas : 3, c_lo = tune.ctas > 0 ? tune.ctas : 1;
+    const int w_hi = tune.warps > 0 ? tune.warps : 8, w_lo = tune.warps > 0 ? tune.warps : 1;
+    for (int ctas = c_hi; ctas >= c_lo; --ctas) {
         const int64_t per_cta = 233472 / ctas - 1024 - 1024;
-        for (int cand = 8; cand >= 1; --cand) {
+        for (int cand = w_hi; cand >= w_lo; --cand) {
             if (ctas * cand <= best || ctas * cand > 24) continue;
             const int64_t fit = ((per_cta - (int64_t)cb) / cand - HIST_WORDS * 4) / 6;
             const int64_t c32 = std::min<int64_t>(npad, fit) & ~int64_t(31);
@@ -116,17 +122,39 @@ template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int
                 w = cand;
                 cap = (int)c32;
                 best = ctas * cand;
+                nc = ctas;
             }
         }
     }
     if (w == 0) return p;
     p.warps = w;
     p.cap = cap;
+    p.ctas = nc;
+    p.d0 = d0;
     p.smem = cb + (size_t)w * PairSmem<T>::warp_bytes(cap);
-    // about four CTAs per SM over the nj x chunks grid
-    int64_t want_ctas = (int64_t)num_sms * 4;
-    int64_t chunks =
-        std::max<int64_t>(1, std::min<int64_t>((m + w - 1) / w, (want_ctas + nj - 1) / nj));
+    int64_t chunks;
+    if (tune.kchunk > 0) {
+        chunks = (m + std::min<int64_t>(m, tune.kchunk) - 1) / std::min<int64_t>(m, tune.kchunk);
+    } else {
+        // At least four CTAs per SM over the nj x chunks grid; then the fewest
+        // chunks (1-4) whose last wave of resident CTAs is nearly full, so that
+        // staging column jhat is amortised over many k without a long tail.
+        const int64_t slots = (int64_t)num_sms * nc;
+        const int64_t cmax = std::max<int64_t>(1, (m + w - 1) / w);
+        chunks = std::max<int64_t>(1, std::min<int64_t>(cmax, (num_sms * 4 + nj - 1) / nj));
+        if (chunks == 1) {
+            double best_loss = 1e30;
+            for (int64_t c = 1; c <= std::min<int64_t>(4, cmax); ++c) {
+                const double waves = (double)(nj * c) / (double)slots;
+                const double loss = std::ceil(waves) / waves;
+                if (loss < best_loss - 0.02) {
+                    best_loss = loss;
+                    chunks = c;
+                }
+                if (loss <= 1.05) break;
+            }
+        }
+    }
     p.kchunk = (int)((m + chunks - 1) / chunks);
     p.kchunks = (int)((m + p.kchunk - 1) / p.kchunk);
     return p;
@@ -152,8 +180,8 @@ cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, in
     return cudaGetLastError();
 }
 
-template PairPlan plan_pairs<float>(int64_t, int64_t, int, int64_t);
-template PairPlan plan_pairs<double>(int64_t, int64_t, int, int64_t);
+template PairPlan plan_pairs<float>(int64_t, int64_t, int, int64_t, const Tune &);
+template PairPlan plan_pairs<double>(int64_t, int64_t, int, int64_t, const Tune &);
 template int64_t max_rows_pairs<float>();
 template int64_t max_rows_pairs<double>();
 template cudaError_t launch_pairs<float>(const ScanArgs<float> &, const double *, int, int,

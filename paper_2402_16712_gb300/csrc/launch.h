@@ -27,10 +27,17 @@ struct PairPlan {
     size_t smem;
     int kchunk;
     int kchunks;
-    int cap;  // per-warp candidate-list capacity
+    int cap;   // per-warp candidate-list capacity
+    int ctas;  // CTAs per SM the shared memory is sized for
+    int d0;    // first-bracket half-width of the selection
+};
+// Caller overrides of the planner (0 = the planner's choice).
+struct Tune {
+    int warps = 0, ctas = 0, kchunk = 0, d0 = 0;
 };
 // nj: number of jhat scored (m for a full scan).
-template <typename T> PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj);
+template <typename T>
+PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune = Tune());
 template <typename T> int64_t max_rows_pairs();
 
 // One launch of the pair kernel for lambdas[t0 .. t0+nlc) (nlc <= MAX_LAMBDA_PER_LAUNCH).

@@ -242,7 +242,7 @@ __device__ __forceinline__ int hist_cross(const uint32_t *h, int nbins, uint32_t
 template <typename T>
 __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *inv,
                          const int64_t *colq, const uint16_t *samp, uint32_t *lk, uint16_t *li,
-                         uint32_t *hist, int qt, int n, const Decide &dc,
+                         uint32_t *hist, int qt, int n, int d0, const Decide &dc,
                          typename Traits<T>::K &tstar, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
@@ -283,7 +283,8 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
         if (kk > CKMAX) kk = dflt;
         return min(max(kk, lo0), hi0);
     };
-    int d0 = 6;  // +-6 of 64 samples: ~15% of the rows in the bracket, ~1.5% misses
+    // d0: half-width of the first bracket in sample positions (6 of 64: ~15%
+    // of the rows in the bracket, ~1.5% misses)
     uint32_t P1 = pick(jx - d0, lo0);
     uint32_t P2 = pick(jx + d0, hi0);
     if (P1 > P2) P1 = P2;
@@ -614,6 +615,7 @@ template <typename T> struct WarpCtx {
     uint32_t *hist;
     const Decide *s_dec;  // per-lambda thresholds for the first NDEC lambdas
     int qt, n;
+    int d0;               // first-bracket half-width in sample positions
     ColInfo cinfo;
 };
 constexpr int NDEC = 32;
@@ -677,7 +679,7 @@ __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int t
         st = SEL_SLOW;
     } else if (w.cinfo.n_valid > 0) {
         const Decide dc = decide_for(w, lp, tl);
-        st = select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, dc,
+        st = select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, w.d0, dc,
                           ts, lane);
     }
     emit_pair<T>(a, t0 + tl, j, k, st, ts, xk, w.colb, w.n, lp.lam[tl], lane);
@@ -702,11 +704,11 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     K Ka = Tr::KEY0, Kb = Tr::KEY0;
     {
         const Decide da = decide_for(w, lp, lp.tl_min);
-        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, da, Ka,
+        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, da, Ka,
                          lane) != SEL_OK)
             return false;
         const Decide db = decide_for(w, lp, lp.tl_max);
-        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, db, Kb,
+        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, db, Kb,
                          lane) != SEL_OK)
             return false;
     }
@@ -890,6 +892,7 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     wc.hist = hist;
     wc.s_dec = s_dec;
     wc.qt = cap / 32;
+    wc.d0 = a.d0;
     wc.n = n;
     wc.cinfo = cinfo;
 

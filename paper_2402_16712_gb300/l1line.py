@@ -56,6 +56,8 @@ SIGNATURES = {
                                      _SZ, _P]),
     "l1line_fit_proposed_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P,
                                      _SZ, _P]),
+    "l1line_set_tuning": (_I, [_P]),
+    "l1line_plan": (_I, [_I, _I64, _I64, _I64, _P]),
 }
 MLP_PARAMS = 17153   # L1L_MLP_PARAMS
 MLP_BYTES = 34832    # sizeof(l1line_mlp)
@@ -337,6 +339,33 @@ def fit_proposed(X, lambdas, mlp, K, workspace: Optional[Workspace] = None, stre
              _ptr(idx), v.data_ptr(), obj.data_ptr(), js.data_ptr(), ctypes.c_void_p(ws.ptr),
              ws.nbytes, _stream_ptr(stream)), "l1line_fit_proposed")
     return v, obj, js, idx, ws
+
+
+class Tuning(ctypes.Structure):
+    """l1line_tuning: pair-kernel launch overrides (0 = the planner's choice)."""
+    _fields_ = [("warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("kchunk", ctypes.c_int32), ("d0", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+def set_tuning(tuning=None) -> None:
+    """Apply a tuning (dict or Tuning) to this thread's later calls; None
+    restores the planner."""
+    if tuning is None:
+        _check(load().l1line_set_tuning(None), "l1line_set_tuning")
+        return
+    t = tuning if isinstance(tuning, Tuning) else Tuning(**tuning)
+    _check(load().l1line_set_tuning(ctypes.byref(t)), "l1line_set_tuning")
+
+
+def plan(dtype, n: int, m: int, nj: Optional[int] = None) -> dict:
+    """The pair-kernel plan the next call of this thread would use."""
+    t = Tuning()
+    _check(load().l1line_plan(_dt(dtype), n, m, m if nj is None else nj, ctypes.byref(t)),
+           "l1line_plan")
+    return t.as_dict()
 
 
 def status(ws: Workspace, stream=None) -> int:
