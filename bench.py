@@ -279,6 +279,10 @@ def run_gpu(args):
     with torch.cuda.stream(stream):
         for _ in range(2):
             l1line.fit(Xd64, lams, workspace=ws64, stream=stream)
+        tuning64 = autotune.apply(torch.float64, n, m, 1, flush=flush,
+                                  run=lambda: l1line.fit(Xd64, lams, workspace=ws64,
+                                                         stream=stream))
+        l1line.fit(Xd64, lams, workspace=ws64, stream=stream)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         k64 = max(2, args.steps // 4)
         e0.record(stream)
@@ -287,6 +291,7 @@ def run_gpu(args):
         e1.record(stream)
     stream.synchronize()
     ms64 = e0.elapsed_time(e1) / k64
+    l1line.set_tuning(None)
 
     # ---- end to end through the ABI with host buffers ----------------------
     autotune.apply(torch.float32, n, m, 1)  # the cached tuning of the headline shape
@@ -329,7 +334,8 @@ def run_gpu(args):
                    "l2": "flushed before every timed step (512 MiB write)",
                    "tuning": {"applied": tuning, "plan": l1line.plan(torch.float32, n, m)}},
         "fits_per_s": world * args.steps / (tot_ms * 1e-3),
-        "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT},
+        "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT,
+                "tuning": tuning64},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
                      "frac": achieved / peak, "traffic": _profile_traffic(),
                      "kernel": "k_pairs<float,false>", "kernel_ms": kms,

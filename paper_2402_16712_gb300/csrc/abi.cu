@@ -33,7 +33,7 @@ bool mul_ok(int64_t a, int64_t b, int64_t &out) {
 }
 
 struct Layout {
-    size_t status, slow_count, colinfo, Xt, v_all, s_all, z_all, slow;
+    size_t status, slow_count, colinfo, Xt, Xf, v_all, s_all, z_all, slow;
     size_t feat_raw, feat_std, score, idx;  // learned proposer: [m][3], [m][3], [m], [m]
     size_t total;
     int64_t ldn;
@@ -58,6 +58,11 @@ bool make_layout(int dtype, int64_t n, int64_t m, int64_t nl, Layout &L) {
     off = al256(off + (size_t)m * sizeof(ColInfo));
     L.Xt = off;
     off = al256(off + (size_t)xt * es);
+    L.Xf = L.Xt;  // double input: a float copy for the approximate keys
+    if (es == 8) {
+        L.Xf = off;
+        off = al256(off + (size_t)xt * 4);
+    }
     L.v_all = off;
     off = al256(off + (size_t)pairs * es);
     L.s_all = off;
@@ -123,6 +128,7 @@ int scan_setup(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t 
     c.st = static_cast<cudaStream_t>(stream);
     ScanArgs<T> &a = c.a;
     a.Xt = reinterpret_cast<T *>(c.base + L.Xt);
+    a.Xf = reinterpret_cast<float *>(c.base + L.Xf);
     a.ci = reinterpret_cast<ColInfo *>(c.base + L.colinfo);
     a.n = n;
     a.m = m;
@@ -145,7 +151,8 @@ int scan_setup(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t 
 template <typename T> int scan_prep(const T *X, Scan<T> &c) {
     ScanArgs<T> &a = c.a;
     if (cudaMemsetAsync(a.status, 0, sizeof(uint32_t), c.st) != cudaSuccess) return L1L_ERR_CUDA;
-    if (launch_prep<T>(X, const_cast<T *>(a.Xt), const_cast<ColInfo *>(a.ci), a.n, a.m, a.ldn,
+    if (launch_prep<T>(X, const_cast<T *>(a.Xt), const_cast<float *>(a.Xf),
+                       const_cast<ColInfo *>(a.ci), a.n, a.m, a.ldn,
                        a.status, c.st, c.launches) != cudaSuccess)
         return L1L_ERR_CUDA;
     return L1L_OK;

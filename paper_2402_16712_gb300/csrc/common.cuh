@@ -218,6 +218,7 @@ struct SlowEntry {
 // Shapes and device pointers of one scan, passed by value to every kernel.
 template <typename T> struct ScanArgs {
     const T *Xt;       // [m][ldn] column-major copy of X
+    const float *Xf;   // the same rounded to float (== Xt for float input)
     const ColInfo *ci;  // [m]
     int64_t n, m, ldn;
     int32_t n_lambda;
@@ -278,7 +279,7 @@ template <typename T> struct BatchDesc {
 
 // Layout of one instance's workspace region (host and device agree on it).
 struct InstLayout {
-    size_t ci, Xt, v_all, s_all, z_all, total;
+    size_t ci, Xt, Xf, v_all, s_all, z_all, total;
 };
 __host__ __device__ inline size_t al256b(size_t x) { return (x + 255) & ~size_t(255); }
 __host__ __device__ inline InstLayout inst_layout(int64_t m, int64_t ldn, int64_t nl, size_t es) {
@@ -288,6 +289,8 @@ __host__ __device__ inline InstLayout inst_layout(int64_t m, int64_t ldn, int64_
     o = al256b(o + (size_t)m * sizeof(ColInfo));
     L.Xt = o;
     o = al256b(o + (size_t)m * (size_t)ldn * es);
+    L.Xf = es == 8 ? o : L.Xt;  // float copy for double input
+    if (es == 8) o = al256b(o + (size_t)m * (size_t)ldn * 4);
     L.v_all = o;
     o = al256b(o + (size_t)nl * (size_t)m * (size_t)m * es);
     L.s_all = o;

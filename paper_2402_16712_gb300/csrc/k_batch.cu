@@ -36,6 +36,7 @@ __device__ __forceinline__ ScanArgs<T> inst_args(const BatchDesc<T> &bd, int b,
     unsigned char *base = ws + in.ws_off;
     ScanArgs<T> a;
     a.Xt = reinterpret_cast<const T *>(base + L.Xt);
+    a.Xf = reinterpret_cast<const float *>(base + L.Xf);
     a.ci = reinterpret_cast<const ColInfo *>(base + L.ci);
     a.n = in.n;
     a.m = in.m;
@@ -63,7 +64,8 @@ __global__ void __launch_bounds__(256) k_transpose_b(const __grid_constant__ Bat
     const int tiles_c = (in.m + 31) / 32;
     const InstLayout L = inst_layout(in.m, in.ldn, in.nl, sizeof(T));
     T *Xt = reinterpret_cast<T *>(ws + in.ws_off + L.Xt);
-    transpose_tile<T>(in.X, Xt, in.n, in.m, in.ldn, reinterpret_cast<uint32_t *>(ws), t % tiles_c,
+    float *Xf = reinterpret_cast<float *>(ws + in.ws_off + L.Xf);
+    transpose_tile<T>(in.X, Xt, Xf, in.n, in.m, in.ldn, reinterpret_cast<uint32_t *>(ws), t % tiles_c,
                       t / tiles_c);
 }
 

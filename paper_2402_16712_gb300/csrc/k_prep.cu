@@ -7,9 +7,10 @@ namespace l1l {
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose(const T *__restrict__ X, T *__restrict__ Xt,
+                                                   float *__restrict__ Xf,
                                                    int64_t n, int64_t m, int64_t ldn,
                                                    uint32_t *status) {
-    transpose_tile<T>(X, Xt, n, m, ldn, status, blockIdx.x, blockIdx.y);
+    transpose_tile<T>(X, Xt, Xf, n, m, ldn, status, blockIdx.x, blockIdx.y);
 }
 
 template <typename T>
@@ -19,11 +20,11 @@ __global__ void __launch_bounds__(256) k_colprep(const T *__restrict__ Xt, ColIn
 }
 
 template <typename T>
-cudaError_t launch_prep(const T *X, T *Xt, ColInfo *ci, int64_t n, int64_t m, int64_t ldn,
-                        uint32_t *status, cudaStream_t st, int &launches) {
+cudaError_t launch_prep(const T *X, T *Xt, float *Xf, ColInfo *ci, int64_t n, int64_t m,
+                        int64_t ldn, uint32_t *status, cudaStream_t st, int &launches) {
     dim3 tb(32, 8);
     dim3 tg((unsigned)((m + 31) / 32), (unsigned)((ldn + 31) / 32));
-    k_transpose<T><<<tg, tb, 0, st>>>(X, Xt, n, m, ldn, status);
+    k_transpose<T><<<tg, tb, 0, st>>>(X, Xt, Xf, n, m, ldn, status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_colprep<T><<<(unsigned)m, 256, 0, st>>>(Xt, ci, n, ldn);
@@ -31,9 +32,9 @@ cudaError_t launch_prep(const T *X, T *Xt, ColInfo *ci, int64_t n, int64_t m, in
     return cudaGetLastError();
 }
 
-template cudaError_t launch_prep<float>(const float *, float *, ColInfo *, int64_t, int64_t,
-                                        int64_t, uint32_t *, cudaStream_t, int &);
-template cudaError_t launch_prep<double>(const double *, double *, ColInfo *, int64_t, int64_t,
-                                         int64_t, uint32_t *, cudaStream_t, int &);
+template cudaError_t launch_prep<float>(const float *, float *, float *, ColInfo *, int64_t,
+                                        int64_t, int64_t, uint32_t *, cudaStream_t, int &);
+template cudaError_t launch_prep<double>(const double *, double *, float *, ColInfo *, int64_t,
+                                         int64_t, int64_t, uint32_t *, cudaStream_t, int &);
 
 }  // namespace l1l

@@ -56,7 +56,6 @@ template <typename T> struct Approx;
 template <> struct Approx<float> {
     static constexpr uint32_t G = 8;
     static __device__ __forceinline__ float inv_of(float b) { return __frcp_rn(b); }
-    static __device__ __forceinline__ float a32(float a) { return a; }
     static __device__ __forceinline__ uint32_t exact_ck(float a, float b) {
         return ckey(__fdiv_rn(a, b));
     }
@@ -66,7 +65,6 @@ template <> struct Approx<double> {
     static __device__ __forceinline__ float inv_of(double b) {
         return __frcp_rn(__double2float_rn(b));
     }
-    static __device__ __forceinline__ float a32(double a) { return __double2float_rn(a); }
     static __device__ __forceinline__ uint32_t exact_ck(double a, double b) {
         return ckey(__double2float_rn(__ddiv_rn(a, b)));
     }
@@ -240,7 +238,8 @@ __device__ __forceinline__ int hist_cross(const uint32_t *h, int nbins, uint32_t
 // warp.  Row indices carry a flag bit, EXACT: the stored key is exact.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *inv,
+__device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf, const T *colb,
+                         const float *inv,
                          const int64_t *colq, const uint16_t *samp, uint32_t *lk, uint16_t *li,
                          uint32_t *hist, int qt, int n, int d0, const Decide &dc,
                          typename Traits<T>::K &tstar, int lane) {
@@ -260,7 +259,7 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int i = samp[e * 32 + lane];
-        sk[e] = akey(__fmul_rn(A::a32(xk[i]), inv[i]));
+        sk[e] = akey(__fmul_rn(xf[i], inv[i]));
     }
     warp_sort64(sk, lane);
     int jx;
@@ -313,7 +312,7 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
             for (int i = lane; i < n; i += 32) {
                 const float iv = inv[i];
                 if (iv == 0.0f) continue;
-                uint32_t kk = akey(__fmul_rn(A::a32(xk[i]), iv));
+                uint32_t kk = akey(__fmul_rn(xf[i], iv));
                 if (kk < bt) {
                     Sb += colq[i];
                     continue;
@@ -375,21 +374,21 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
         // batch are issued before the current one is classified, so the L2
         // latency overlaps the work
         constexpr int U = 4;
-        T an[U];
+        float an[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int i = u * 32 + lane;
-            an[u] = i < n ? xk[i] : T(0);
+            an[u] = i < n ? xf[i] : 0.0f;
         }
         for (int i0 = 0; i0 < n; i0 += 32 * U) {
-            T ac[U];
+            float ac[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) ac[u] = an[u];
             if (i0 + 32 * U < n) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int i = i0 + 32 * U + u * 32 + lane;
-                    an[u] = i < n ? xk[i] : T(0);
+                    an[u] = i < n ? xf[i] : 0.0f;
                 }
             }
 #pragma unroll
@@ -398,7 +397,7 @@ __device__ int select_v2(const T *__restrict__ xk, const T *colb, const float *i
                 const int i = i0 + u * 32 + lane;
                 const int ic = min(i, npad_m1);
                 const float iv = inv[ic];
-                const uint32_t kk = akey(__fmul_rn(A::a32(ac[u]), iv));
+                const uint32_t kk = akey(__fmul_rn(ac[u], iv));
                 const bool valid = i < n && iv != 0.0f;
                 const bool below = valid && kk < bt;
                 const bool cand = valid && !below && kk <= at;
@@ -670,8 +669,8 @@ __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int
 // One lambda of one pair: the full selection.
 template <typename T>
 __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int tl, int64_t j,
-                          int64_t k, const T *xk, const WarpCtx<T> &w, bool slow_pair,
-                          int lane) {
+                          int64_t k, const T *xk, const float *xf, const WarpCtx<T> &w,
+                          bool slow_pair, int lane) {
     using Tr = Traits<T>;
     typename Tr::K ts = Tr::KEY0;
     int st = SEL_OK;
@@ -679,7 +678,7 @@ __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int t
         st = SEL_SLOW;
     } else if (w.cinfo.n_valid > 0) {
         const Decide dc = decide_for(w, lp, tl);
-        st = select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, w.d0, dc,
+        st = select_v2<T>(xk, xf, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, w.d0, dc,
                           ts, lane);
     }
     emit_pair<T>(a, t0 + tl, j, k, st, ts, xk, w.colb, w.n, lp.lam[tl], lane);
@@ -694,7 +693,8 @@ __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int t
 // Returns false (nothing written) when more than 31 rows lie between.
 template <typename T>
 __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int nlc, int64_t j,
-                            int64_t k, const T *__restrict__ xk, const WarpCtx<T> &w, int lane) {
+                            int64_t k, const T *__restrict__ xk, const float *__restrict__ xf,
+                            const WarpCtx<T> &w, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
     using A = Approx<T>;
@@ -704,11 +704,11 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     K Ka = Tr::KEY0, Kb = Tr::KEY0;
     {
         const Decide da = decide_for(w, lp, lp.tl_min);
-        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, da, Ka,
+        if (select_v2<T>(xk, xf, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, da, Ka,
                          lane) != SEL_OK)
             return false;
         const Decide db = decide_for(w, lp, lp.tl_max);
-        if (select_v2<T>(xk, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, db, Kb,
+        if (select_v2<T>(xk, xf, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, db, Kb,
                          lane) != SEL_OK)
             return false;
     }
@@ -720,21 +720,21 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     uint16_t *stage = reinterpret_cast<uint16_t *>(w.hist);
     int c = 0;
     constexpr int U = 4;  // loads of the next batch in flight while this one is classified
-    T an[U];
+    float an[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int i = u * 32 + lane;
-        an[u] = i < n ? xk[i] : T(0);
+        an[u] = i < n ? xf[i] : 0.0f;
     }
     for (int i0 = 0; i0 < n; i0 += 32 * U) {
-        T ac[U];
+        float ac[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) ac[u] = an[u];
         if (i0 + 32 * U < n) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int i = i0 + 32 * U + u * 32 + lane;
-                an[u] = i < n ? xk[i] : T(0);
+                an[u] = i < n ? xf[i] : 0.0f;
             }
         }
 #pragma unroll
@@ -744,11 +744,11 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
             if (i < n) {
                 const float iv = w.inv[i];
                 if (iv != 0.0f) {
-                    const uint32_t kk = akey(__fmul_rn(A::a32(ac[u]), iv));
+                    const uint32_t kk = akey(__fmul_rn(ac[u], iv));
                     if (kk < bt) {
                         Sb += w.colq[i];
                     } else if (kk <= at) {
-                        const K ke = Tr::key(Tr::div_rn(ac[u], w.colb[i]));
+                        const K ke = Tr::key(Tr::div_rn(xk[i], w.colb[i]));
                         if (ke < Klo)
                             Sb += w.colq[i];
                         else if (ke <= Khi)
@@ -794,7 +794,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
         const unsigned any = okm | unm;
         const int first = any ? __ffs(any) - 1 : 0;
         if (!any || ((unm >> first) & 1u)) {  // undecided here: full selection
-            solve_one<T>(a, lp, t0, tl, j, k, xk, w, false, lane);
+            solve_one<T>(a, lp, t0, tl, j, k, xk, xf, w, false, lane);
             prev = Tr::NONE;
             continue;
         }
@@ -907,14 +907,16 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
             continue;
         }
         const T *xk = a.Xt + k * ldn;
+        const float *xf = a.Xf + k * ldn;
         const bool slow_pair = a.force_exact || jwide ||
                                (sizeof(T) == 8 && (a.ci[k].flags & COL_WIDE));
         if (MULTI && nlc >= 3 && !slow_pair && cinfo.n_valid > 0 &&
-            lambda_path<T>(a, lp, t0, nlc, j, k, xk, wc, lane)) {
+            lambda_path<T>(a, lp, t0, nlc, j, k, xk, xf, wc, lane)) {
             __syncwarp();
             continue;
         }
-        for (int tl = 0; tl < nlc; ++tl) solve_one<T>(a, lp, t0, tl, j, k, xk, wc, slow_pair, lane);
+        for (int tl = 0; tl < nlc; ++tl)
+            solve_one<T>(a, lp, t0, tl, j, k, xk, xf, wc, slow_pair, lane);
         __syncwarp();
     }
     __syncthreads();  // the CTA may stage another column next

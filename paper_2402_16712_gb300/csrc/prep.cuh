@@ -7,12 +7,15 @@
 namespace l1l {
 
 // X (n x m, row-major, rows = points) -> Xt (m x ldn, column-major, rows
-// n..ldn-1 zero).  32x32 tiles through shared memory so both the read and the
-// write are coalesced.  Any NaN/inf sets ST_NONFINITE.
+// n..ldn-1 zero), and for double input also Xf, the same copy rounded to float
+// (the pair kernel's approximate keys read it, so they need no conversion on
+// the narrow double pipe).  32x32 tiles through shared memory so both the read
+// and the write are coalesced.  Any NaN/inf sets ST_NONFINITE.
 template <typename T>
 __device__ __forceinline__ void transpose_tile(const T *__restrict__ X, T *__restrict__ Xt,
-                                               int64_t n, int64_t m, int64_t ldn,
-                                               uint32_t *status, int64_t tile_c, int64_t tile_r) {
+                                               float *__restrict__ Xf, int64_t n, int64_t m,
+                                               int64_t ldn, uint32_t *status, int64_t tile_c,
+                                               int64_t tile_r) {
     __shared__ T tile[32][33];
     const int64_t c0 = tile_c * 32;  // column of X
     const int64_t r0 = tile_r * 32;  // row of X
@@ -33,7 +36,11 @@ __device__ __forceinline__ void transpose_tile(const T *__restrict__ X, T *__res
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         int64_t c = c0 + ty + 8 * q, r = r0 + tx;
-        if (c < m && r < ldn) Xt[c * ldn + r] = tile[tx][ty + 8 * q];
+        if (c < m && r < ldn) {
+            const T v = tile[tx][ty + 8 * q];
+            Xt[c * ldn + r] = v;
+            if (sizeof(T) == 8) Xf[c * ldn + r] = (float)v;
+        }
     }
 }
 
