@@ -54,6 +54,9 @@ def _load():
                 g = getattr(lib, f"oracle_pair_{sfx}")
                 g.restype = ctypes.c_int
                 g.argtypes = [P, P, I64, ctypes.c_double, P]
+                h = getattr(lib, f"oracle_path_{sfx}")
+                h.restype = I64
+                h.argtypes = [P, I64, I64, I64, I64, P, P, I64]
             lib.oracle_sign_of_sum.restype = ctypes.c_int
             lib.oracle_sign_of_sum.argtypes = [P, I64]
             lib.oracle_max_threads.restype = ctypes.c_int
@@ -128,3 +131,20 @@ def fit(X, lambdas, jlist=None, nthreads=None, want_all=True):
     if want_all:
         res.update(v_all=v_all, s_all=s_all, z_all=z_all)
     return res
+
+
+def path(X, jhat: int, k: int):
+    """The lambda path of v_k for preserved coordinate jhat (Algorithm 2):
+    (lam, v) with lam increasing from 0; v[g] is the value from lam[g] on
+    (see oracle_path_* for the conventions)."""
+    X = np.ascontiguousarray(X)
+    if X.dtype not in (np.float32, np.float64) or X.ndim != 2:
+        raise TypeError("X must be a 2-D float32/float64 array")
+    n, m = X.shape
+    lam = np.zeros(n + 1)
+    v = np.zeros(n + 1, dtype=X.dtype)
+    f = getattr(_load(), "oracle_path_f32" if X.dtype == np.float32 else "oracle_path_f64")
+    r = int(f(_ptr(X), n, m, int(jhat), int(k), _ptr(lam), _ptr(v), n + 1))
+    if r < 1:
+        raise OracleError(f"oracle_path failed: {r}")
+    return lam[:r].copy(), v[:r].copy()

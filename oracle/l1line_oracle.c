@@ -339,3 +339,207 @@ int oracle_max_threads(void) {
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Algorithm 2: the lambda path of one pair                            */
+/* ------------------------------------------------------------------ */
+/* Exact value of a rounded to the nearest double (ties to even). */
+static double kacc_to_double(const kacc *a) {
+    kacc m = *a;
+    const int neg = kacc_sign(a) < 0;
+    if (neg) { /* two's complement negation */
+        uint64_t c = 1;
+        for (int j = 0; j < KL_LIMBS; j++) {
+            uint64_t t = ~m.limb[j] + c;
+            c = (c && t == 0) ? 1 : 0;
+            m.limb[j] = t;
+        }
+    }
+    int top = -1;
+    for (int j = KL_LIMBS - 1; j >= 0 && top < 0; j--)
+        if (m.limb[j])
+            for (int b = 63; b >= 0; b--)
+                if ((m.limb[j] >> b) & 1) {
+                    top = j * 64 + b;
+                    break;
+                }
+    if (top < 0) return 0.0;
+    double v;
+    if (top <= 52) { /* fits 53 bits: exact (subnormal range included) */
+        v = ldexp((double)m.limb[0], -1074);
+    } else {
+        const int shift = top - 52;
+        /* the 53 bits [shift, top] */
+        const int li = shift / 64, lo = shift % 64;
+        uint64_t f = m.limb[li] >> lo;
+        if (lo && li + 1 < KL_LIMBS) f |= m.limb[li + 1] << (64 - lo);
+        uint64_t mant = f & ((UINT64_C(1) << 53) - 1);
+        const int rb = shift - 1;
+        const int round = (int)((m.limb[rb / 64] >> (rb % 64)) & 1);
+        int sticky = 0;
+        for (int b = 0; b < rb && !sticky; b++)
+            if ((m.limb[b / 64] >> (b % 64)) & 1) sticky = 1;
+        int e = shift;
+        if (round && (sticky || (mant & 1))) {
+            mant++;
+            if (mant == (UINT64_C(1) << 53)) {
+                mant >>= 1;
+                e++;
+            }
+        }
+        v = ldexp((double)mant, e - 1074);
+    }
+    return neg ? -v : v;
+}
+
+typedef struct {
+    double lam;
+    double v;
+} bp_t;
+
+static int cmp_bp(const void *pa, const void *pb) {
+    const bp_t *a = (const bp_t *)pa, *b = (const bp_t *)pb;
+    if (a->lam != b->lam) return (a->lam > b->lam) - (a->lam < b->lam);
+    const double x = fabs(a->v), y = fabs(b->v); /* then moving toward 0 */
+    return (x < y) - (x > y);
+}
+
+/* list[0..cnt): (ratio, weight) of the rows with x_ijhat != 0 (no penalty
+ * point).  Writes the path into out (capacity cnt + 1) and returns its
+ * length.  Steps of Algorithm 2 for one (jhat, j): sort the ratios; for each
+ * sorted position p, lambda_p = sgn(r_p) (S_after - S_before) - w_p (exact);
+ * a row with lambda_p + 2 w_p > 0 starts the value r_p at max(0, lambda_p);
+ * lambda_max = max(0, max_p lambda_p + 2 w_p) starts the value 0.  Readings
+ * (the paper is silent): a zero ratio is the penalty point itself, so such a
+ * row starts nothing (it still counts in the sums); the path starts with
+ * Algorithm 1's value at lambda = 0, v0; breakpoints are ordered by lambda
+ * and, at equal lambda, by decreasing |v|; consecutive equal values are
+ * merged, keeping the first lambda.  Meaning: v(0) = the first value; on the
+ * open interval between consecutive breakpoints, the later entry's value; at
+ * a breakpoint lambda > 0, the earlier value when it is positive (the test
+ * of Lemma 1 is strict there) and the later one when it is negative. */
+static void kacc_neg(kacc *a) { /* a = -a (two's complement) */
+    uint64_t c = 1;
+    for (int j = 0; j < KL_LIMBS; j++) {
+        const uint64_t t = ~a->limb[j] + c;
+        c = (c && t == 0) ? 1 : 0;
+        a->limb[j] = t;
+    }
+}
+
+static void kacc_addk(kacc *a, const kacc *b) { /* a += b */
+    uint64_t cy = 0;
+    for (int j = 0; j < KL_LIMBS; j++) {
+        const uint64_t s = a->limb[j] + b->limb[j];
+        const uint64_t c1 = s < b->limb[j];
+        const uint64_t s2 = s + cy;
+        const uint64_t c2 = s2 < cy;
+        a->limb[j] = s2;
+        cy = c1 | c2;
+    }
+}
+
+static int64_t path_pair(rw_t *list, int64_t cnt, double v0, bp_t *out) {
+    qsort(list, (size_t)cnt, sizeof(rw_t), cmp_rw);
+    kacc Q, before;
+    kacc_zero(&Q);
+    kacc_zero(&before);
+    for (int64_t p = 0; p < cnt; p++) kacc_add(&Q, list[p].w, 0);
+    int64_t e = 0;
+    double lmax = 0.0;
+    /* Algorithm 1's value at lambda = 0 (right end point of the minimiser
+     * interval); when that interval is not a point, Algorithm 2's strict test
+     * drops this value, which then holds at lambda = 0 only. */
+    out[e].lam = 0.0;
+    out[e].v = v0;
+    e++;
+    for (int64_t p = 0; p < cnt; p++) {
+        const double r = list[p].r, w = list[p].w;
+        if (r != 0.0) {
+            /* x = S_after - S_before = Q - 2 S_before - w */
+            kacc x = Q, nb = before;
+            kacc_neg(&nb);
+            kacc_addk(&x, &nb);
+            kacc_addk(&x, &nb);
+            kacc_add(&x, w, 1);
+            /* lam_p = sgn(r) x - w;  lam_p + 2 w = sgn(r) x + w */
+            if (r < 0.0) kacc_neg(&x);
+            kacc lam = x, top = x;
+            kacc_add(&lam, w, 1);
+            kacc_add(&top, w, 0);
+            if (kacc_sign(&top) > 0) {
+                out[e].lam = kacc_sign(&lam) > 0 ? kacc_to_double(&lam) : 0.0;
+                out[e].v = r;
+                e++;
+                const double tv = kacc_to_double(&top);
+                if (tv > lmax) lmax = tv;
+            }
+        }
+        kacc_add(&before, w, 0);
+    }
+    out[e].lam = lmax;
+    out[e].v = 0.0;
+    e++;
+    qsort(out, (size_t)e, sizeof(bp_t), cmp_bp);
+    int64_t k = 0;
+    for (int64_t p = 0; p < e; p++)
+        if (k == 0 || out[p].v != out[k - 1].v) out[k++] = out[p];
+    return k;
+}
+
+/* The lambda path of v_k for preserved coordinate jhat (Algorithm 2), X
+ * row-major n x m.  Writes up to cap entries: out_lam (double, increasing)
+ * and out_v (the value from that lambda on).  k == jhat gives (0, 1).
+ * Returns the path length, or -(length) when cap is too small, or an
+ * ORACLE_ERR_* code (all <= -1 ... callers check cap >= n + 1 first). */
+#define DEFINE_PATH(SUFFIX, T, ABS)                                                        \
+    int64_t oracle_path_##SUFFIX(const T *X, int64_t n, int64_t m, int64_t jh, int64_t k,   \
+                                 double *out_lam, T *out_v, int64_t cap) {                 \
+        if (!X || n < 1 || m < 1 || jh < 0 || jh >= m || k < 0 || k >= m || cap < n + 1)   \
+            return ORACLE_ERR_ARG;                                                         \
+        if (k == jh) {                                                                     \
+            out_lam[0] = 0.0;                                                              \
+            out_v[0] = (T)1;                                                               \
+            return 1;                                                                      \
+        }                                                                                  \
+        rw_t *list = (rw_t *)malloc(sizeof(rw_t) * (size_t)n);                             \
+        bp_t *bp = (bp_t *)malloc(sizeof(bp_t) * (size_t)(n + 1));                         \
+        if (!list || !bp) {                                                                \
+            free(list);                                                                    \
+            free(bp);                                                                      \
+            return ORACLE_ERR_ALLOC;                                                       \
+        }                                                                                  \
+        rw_t *med = (rw_t *)malloc(sizeof(rw_t) * (size_t)(n + 1));                        \
+        if (!med) {                                                                        \
+            free(list);                                                                    \
+            free(bp);                                                                      \
+            return ORACLE_ERR_ALLOC;                                                       \
+        }                                                                                  \
+        int64_t cnt = 0;                                                                   \
+        for (int64_t i = 0; i < n; i++) {                                                  \
+            T b = X[i * m + jh];                                                           \
+            if (b != (T)0) {                                                               \
+                volatile T r = X[i * m + k] / b;                                           \
+                T rr = r;                                                                  \
+                list[cnt].r = (rr == (T)0) ? 0.0 : (double)rr;                             \
+                list[cnt].w = (double)ABS(b);                                              \
+                med[cnt] = list[cnt];                                                      \
+                cnt++;                                                                     \
+            }                                                                              \
+        }                                                                                  \
+        med[cnt].r = 0.0; /* the penalty point, weight lambda = 0 */                       \
+        med[cnt].w = 0.0;                                                                  \
+        const double v0 = weighted_median_exact(med, cnt + 1);                             \
+        free(med);                                                                         \
+        const int64_t len = path_pair(list, cnt, v0, bp);                                  \
+        for (int64_t p = 0; p < len; p++) {                                                \
+            out_lam[p] = bp[p].lam;                                                        \
+            out_v[p] = (T)bp[p].v;                                                         \
+        }                                                                                  \
+        free(list);                                                                        \
+        free(bp);                                                                          \
+        return len;                                                                        \
+    }
+
+DEFINE_PATH(f64, double, fabs)
+DEFINE_PATH(f32, float, fabsf)
