@@ -169,6 +169,45 @@ int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *l
                           void *workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Algorithm 2: the lambda path of every (jhat, k) pair.  As lambda grows from
+ * 0 the penalty point gains weight and v_k moves monotonically from its
+ * lambda = 0 value to 0 through the distinct ratios in between.  Pair
+ * p = jhat * m + k owns entries offsets[p] .. offsets[p] + out_len[p] - 1:
+ * (out_lambda, out_v) with out_lambda increasing from 0 and out_v moving
+ * toward 0 (the last entry is 0, except for k == jhat: one entry (0, 1)).
+ * Meaning: v_k(0) = the first value; on the open interval between two
+ * consecutive lambdas, the later entry's value; at an entry's lambda > 0, the
+ * earlier value when that is positive and the later one when it is negative
+ * (Lemma 1's test is strict).  Two entries share lambda = 0 when the lambda = 0
+ * minimiser is an interval: the first (its right end point, Algorithm 1's
+ * choice) holds at lambda = 0 only.  v is exact (bit-identical to
+ * Algorithm 1 at every lambda); a lambda is the exact weight difference of
+ * Algorithm 2, computed in fixed point (exactly, then rounded once to double,
+ * when every |x_ijhat| of the column is a multiple of the column's
+ * fixed-point unit; otherwise within 2^-40 of the column's l1 norm).
+ *
+ * Two calls with one workspace (l1line_path_workspace_bytes, 256-byte
+ * aligned): l1line_path_count_* stages X, solves lambda = 0 exactly and writes
+ * offsets (DEVICE int64 [m*m + 1]: an exclusive scan of per-pair upper
+ * bounds; offsets[m*m] = entries to allocate); read offsets[m*m], then
+ * l1line_path_write_* (same X, n, m and workspace, nothing else using the
+ * workspace in between) fills out_lambda (DEVICE double), out_v (DEVICE, the
+ * input dtype), both of at least offsets[m*m] entries, and out_len (DEVICE
+ * int32 [m*m], the number of entries each pair used).
+ */
+size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m);
+int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets,
+                          void *workspace, size_t workspace_bytes, void *stream);
+int l1line_path_count_f64(const double *X, int64_t n, int64_t m, int64_t *offsets,
+                          void *workspace, size_t workspace_bytes, void *stream);
+int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *offsets,
+                          double *out_lambda, float *out_v, int32_t *out_len, void *workspace,
+                          size_t workspace_bytes, void *stream);
+int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *offsets,
+                          double *out_lambda, double *out_v, int32_t *out_len, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+/*
  * Learned jhat proposer (not in the paper; an extension of Algorithm 1's
  * outer loop): a small network scores every candidate jhat from three column
  * features, and only the K best-scored candidates are fitted exactly (the

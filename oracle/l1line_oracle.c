@@ -405,8 +405,8 @@ static int cmp_bp(const void *pa, const void *pb) {
 }
 
 /* list[0..cnt): (ratio, weight) of the rows with x_ijhat != 0 (no penalty
- * point).  Writes the path into out (capacity cnt + 1) and returns its
- * length.  Steps of Algorithm 2 for one (jhat, j): sort the ratios; for each
+ * point).  Writes the path into out (capacity cnt + 2; the merged result
+ * has at most cnt + 1 entries) and returns its length.  Steps of Algorithm 2 for one (jhat, j): sort the ratios; for each
  * sorted position p, lambda_p = sgn(r_p) (S_after - S_before) - w_p (exact);
  * a row with lambda_p + 2 w_p > 0 starts the value r_p at max(0, lambda_p);
  * lambda_max = max(0, max_p lambda_p + 2 w_p) starts the value 0.  Readings
@@ -503,7 +503,8 @@ static int64_t path_pair(rw_t *list, int64_t cnt, double v0, bp_t *out) {
             return 1;                                                                      \
         }                                                                                  \
         rw_t *list = (rw_t *)malloc(sizeof(rw_t) * (size_t)n);                             \
-        bp_t *bp = (bp_t *)malloc(sizeof(bp_t) * (size_t)(n + 1));                         \
+        /* before merging: v0, one entry per row, and the final 0 */                      \
+        bp_t *bp = (bp_t *)malloc(sizeof(bp_t) * (size_t)(n + 2));                         \
         if (!list || !bp) {                                                                \
             free(list);                                                                    \
             free(bp);                                                                      \

@@ -232,6 +232,82 @@ int fit_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl
 
 const double k_zero_lambda = 0.0;
 
+// Workspace of the lambda-path calls: the fit layout for one lambda, then the
+// scan scratch, the big-pair list and counters, and the big-pair slices.
+struct PathLayout {
+    Layout L;
+    size_t scan_tmp, big, big_count, scratch, total;
+};
+
+bool make_path_layout(int dtype, int64_t n, int64_t m, PathLayout &P) {
+    if (!make_layout(dtype, n, m, 1, P.L)) return false;
+    int64_t mm;
+    if (!mul_ok(m, m, mm) || mm > ((int64_t)1 << 40)) return false;
+    size_t off = P.L.total;
+    P.scan_tmp = off;
+    off = al256(off + path_scan_scratch(mm));
+    P.big = off;
+    off = al256(off + (size_t)mm * 4);
+    P.big_count = off;
+    off += 256;
+    P.scratch = off;
+    const size_t sl = dtype == L1L_DTYPE_F32 ? path_slice_bytes<float>(n) : path_slice_bytes<double>(n);
+    off = al256(off + (size_t)path_big_workers() * sl);
+    P.total = off;
+    return true;
+}
+
+template <typename T>
+int path_count_impl(const T *X, int64_t n, int64_t m, int64_t *offsets, void *ws, size_t ws_bytes,
+                    void *stream) {
+    g_last_launches = 0;
+    if (!offsets) return L1L_ERR_ARG;
+    PathLayout P;
+    if (X && n >= 1 && m >= 1 && !make_path_layout(dtype_of<T>(), n, m, P))
+        return L1L_ERR_UNSUPPORTED;
+    if (X && n >= 1 && m >= 1 && (!ws || ws_bytes < P.total)) return L1L_ERR_WORKSPACE;
+    Scan<T> c;
+    L1L_TRY(scan_setup<T>(X, n, m, &k_zero_lambda, 1, nullptr, nullptr, nullptr, ws, ws_bytes,
+                          stream, 0u, c));
+    L1L_TRY(scan_prep<T>(X, c));
+    L1L_TRY(scan_pairs<T>(c, &k_zero_lambda, 1, nullptr, m));  // lambda = 0 medians
+    if (launch_path<T>(true, c.a.Xt, c.a.Xf, c.a.ci, n, m, c.a.ldn, c.a.v_all, offsets,
+                       reinterpret_cast<int64_t *>(c.base + P.scan_tmp), nullptr, nullptr, nullptr,
+                       nullptr, nullptr, nullptr, c.a.status, c.sms, c.st, c.launches) !=
+        cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = c.launches;
+    return L1L_OK;
+}
+
+template <typename T>
+int path_write_impl(const T *X, int64_t n, int64_t m, const int64_t *offsets, double *out_lam,
+                    T *out_v, int32_t *out_len, void *ws, size_t ws_bytes, void *stream) {
+    g_last_launches = 0;
+    if (!X || !offsets || !out_lam || !out_v || !out_len || n < 1 || m < 1) return L1L_ERR_ARG;
+    if (n > max_rows_pairs<T>() || m > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
+    PathLayout P;
+    if (!make_path_layout(dtype_of<T>(), n, m, P)) return L1L_ERR_UNSUPPORTED;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < P.total)
+        return L1L_ERR_WORKSPACE;
+    const int sms = num_sms();
+    if (sms <= 0) return L1L_ERR_CUDA;
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    int launches = 0;
+    if (launch_path<T>(false, reinterpret_cast<const T *>(base + P.L.Xt),
+                       reinterpret_cast<const float *>(base + P.L.Xf),
+                       reinterpret_cast<const ColInfo *>(base + P.L.colinfo), n, m, P.L.ldn,
+                       reinterpret_cast<const T *>(base + P.L.v_all),
+                       const_cast<int64_t *>(offsets), nullptr, out_lam, out_v, out_len,
+                       reinterpret_cast<int32_t *>(base + P.big),
+                       reinterpret_cast<uint32_t *>(base + P.big_count), base + P.scratch,
+                       reinterpret_cast<uint32_t *>(base + P.L.status), sms,
+                       static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
 template <typename T>
 int features_impl(const T *X, int64_t n, int64_t m, float *out_raw, float *out_std, void *ws,
                   size_t ws_bytes, void *stream) {
@@ -468,6 +544,37 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
                             void *stream) {
     return proposed_impl<double>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
                                  out_jstar, workspace, workspace_bytes, stream);
+}
+
+size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m) {
+    if (dtype != L1L_DTYPE_F32 && dtype != L1L_DTYPE_F64) return 0;
+    PathLayout P;
+    if (!make_path_layout(dtype, n, m, P)) return 0;
+    return P.total;
+}
+
+int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    return path_count_impl<float>(X, n, m, offsets, workspace, workspace_bytes, stream);
+}
+
+int l1line_path_count_f64(const double *X, int64_t n, int64_t m, int64_t *offsets,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    return path_count_impl<double>(X, n, m, offsets, workspace, workspace_bytes, stream);
+}
+
+int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *offsets,
+                          double *out_lambda, float *out_v, int32_t *out_len, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    return path_write_impl<float>(X, n, m, offsets, out_lambda, out_v, out_len, workspace,
+                                  workspace_bytes, stream);
+}
+
+int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *offsets,
+                          double *out_lambda, double *out_v, int32_t *out_len, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    return path_write_impl<double>(X, n, m, offsets, out_lambda, out_v, out_len, workspace,
+                                   workspace_bytes, stream);
 }
 
 int l1line_status(void *workspace, void *stream) {

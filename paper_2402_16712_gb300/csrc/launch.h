@@ -82,6 +82,19 @@ cudaError_t launch_mlp_pack(const float *theta, l1line_mlp *out, cudaStream_t st
 cudaError_t launch_topk(const float *score, int64_t m, int K, int32_t *out, cudaStream_t st,
                         int &launches);
 
+// ---- Algorithm 2: lambda paths of every pair (k_path.cu) ----
+size_t path_scan_scratch(int64_t N);
+int path_big_workers();
+template <typename T> size_t path_slice_bytes(int64_t n);
+// count: bound_or_off = [m*m + 1] offsets out (exclusive scan of the bounds);
+// write: bound_or_off = those offsets in, lam / val / len out.
+template <typename T>
+cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo *ci, int64_t n,
+                        int64_t m, int64_t ldn, const T *v0, int64_t *bound_or_off,
+                        int64_t *scan_tmp, double *lam, T *val, int32_t *len, int32_t *big,
+                        uint32_t *big_count, unsigned char *scratch, uint32_t *status,
+                        int num_sms, cudaStream_t st, int &launches);
+
 // The batched fit: staging, one persistent pair kernel, exact path, sums, argmin.
 template <typename T>
 cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, double *out_obj,

@@ -56,6 +56,11 @@ SIGNATURES = {
                                      _SZ, _P]),
     "l1line_fit_proposed_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _P,
                                      _SZ, _P]),
+    "l1line_path_workspace_bytes": (_SZ, [_I, _I64, _I64]),
+    "l1line_path_count_f32": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
+    "l1line_path_count_f64": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
+    "l1line_path_write_f32": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_path_write_f64": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
     "l1line_set_tuning": (_I, [_P]),
     "l1line_plan": (_I, [_I, _I64, _I64, _I64, _P]),
 }
@@ -339,6 +344,37 @@ def fit_proposed(X, lambdas, mlp, K, workspace: Optional[Workspace] = None, stre
              _ptr(idx), v.data_ptr(), obj.data_ptr(), js.data_ptr(), ctypes.c_void_p(ws.ptr),
              ws.nbytes, _stream_ptr(stream)), "l1line_fit_proposed")
     return v, obj, js, idx, ws
+
+
+def path_workspace(dtype, n: int, m: int, device=None) -> "Workspace":
+    nb = int(load().l1line_path_workspace_bytes(_dt(dtype), n, m))
+    if nb == 0:
+        raise ValueError("bad shape for the path workspace")
+    return Workspace(nb, device)
+
+
+def paths(X, workspace: Optional[Workspace] = None, stream=None):
+    """Algorithm 2 for every (jhat, k): returns (offsets [m*m + 1] int64 CUDA,
+    lam double CUDA, v CUDA (X's dtype), length [m*m] int32 CUDA, workspace).
+    Pair p = jhat * m + k owns entries offsets[p] .. offsets[p] + length[p].
+    Reads the entry count back to the host between the two library calls."""
+    import torch
+    _check_x(X)
+    n, m = X.shape
+    ws = workspace or path_workspace(X.dtype, n, m, X.device)
+    off = torch.empty(m * m + 1, dtype=torch.int64, device=X.device)
+    f32 = X.dtype == torch.float32
+    cnt = load().l1line_path_count_f32 if f32 else load().l1line_path_count_f64
+    _check(cnt(X.data_ptr(), n, m, off.data_ptr(), ctypes.c_void_p(ws.ptr), ws.nbytes,
+               _stream_ptr(stream)), "l1line_path_count")
+    total = int(off[m * m].item())  # synchronises the stream
+    lam = torch.empty(max(total, 1), dtype=torch.float64, device=X.device)
+    v = torch.empty(max(total, 1), dtype=X.dtype, device=X.device)
+    ln = torch.empty(m * m, dtype=torch.int32, device=X.device)
+    wr = load().l1line_path_write_f32 if f32 else load().l1line_path_write_f64
+    _check(wr(X.data_ptr(), n, m, off.data_ptr(), lam.data_ptr(), v.data_ptr(), ln.data_ptr(),
+              ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream)), "l1line_path_write")
+    return off, lam, v, ln, ws
 
 
 class Tuning(ctypes.Structure):
