@@ -414,6 +414,33 @@ def measure_extras(dev, stream, flush):
         "fits_per_s": lams.size / (ms * 1e-3), "gpu_launches_per_step": launches,
         "tuning": tuning}
     del Xd, ws, res, g
+    # Algorithm 2: the lambda path of every (jhat, k) pair, 2000 x 2000 float32
+    X, _, _ = datagen.paper_size("float32")
+    Xd = torch.from_numpy(X).to(dev)
+    pws = l1line.path_workspace(torch.float32, 2000, 2000, dev)
+    with torch.cuda.stream(stream):
+        off, lam_o, v_o, ln, _ = l1line.paths(Xd, workspace=pws, stream=stream)
+    stream.synchronize()
+    tms = []
+    for _ in range(3):
+        flush.fill_(2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            off, lam_o, v_o, ln, _ = l1line.paths(Xd, workspace=pws, stream=stream)
+            e1.record(stream)
+        stream.synchronize()
+        tms.append(e0.elapsed_time(e1))
+    if l1line.status(pws, stream) != l1line.OK:
+        raise SystemExit("path enumeration failed on the device")
+    entries = int(ln.sum().item())
+    ms = statistics.median(tms)
+    out["lambda_paths"] = {
+        "workload": "Algorithm 2 for every (jhat, k) pair of the 2000 x 2000 float32 matrix: "
+                    "exact lambda = 0 scan, count pass, offsets scan, write pass (L2 flushed)",
+        "ms_per_step": ms, "breakpoints": entries,
+        "breakpoints_per_s": entries / (ms * 1e-3), "pairs_per_s": 2000 * 1999 / (ms * 1e-3)}
+    del Xd, pws, off, lam_o, v_o, ln
     # uneven batch: 256 instances, n~U[100,5000], m~U[10,500], lambda=0.2
     batch = datagen.uneven_batch(256)
     Xs = [torch.from_numpy(Xb).to(dev) for Xb, _ in batch]
