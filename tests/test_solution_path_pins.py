@@ -1,0 +1,74 @@
+"""Pins of the Algorithm 3 oracle (oracle/solution_path.py) against facts
+that do not come from it: the paper's toy solution path (Table 1 and the
+Figure 1 lines), and Algorithm 1 (the pinned fit oracle) at lambdas inside
+and beyond every interval of the computed path."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import solution_path as SP
+from paper_2402_16712_gb300 import datagen
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "toy_example.json")
+
+
+def test_toy_solution_path_table1_and_figure1():
+    d = json.load(open(GOLDEN))
+    X = np.array(d["points"], dtype=np.float64)
+    ent, lams = SP.solution_path(X)
+    starts = [float(e[0]) for e in ent]
+    # Table 1: breakpoints 0, 3, 3.5 (the crossing of two Figure 1 lines), 11
+    assert np.allclose(starts, [0.0, 3.0, d["crossing_lambda"], d["lambda_max"]], rtol=1e-12,
+                       atol=0)
+    assert [e[1] + 1 for e in ent] == [4, 4, 1, 1]
+    for e, row in zip(ent, d["table1"]):
+        want = []
+        for s in row["v"]:
+            if "/" in s:
+                a, b = s.split("/")
+                want.append(float(a) / float(b))
+            else:
+                want.append(float(s))
+        tol = 0.05 if row is d["table1"][0] else 1e-12  # the first row prints 1 decimal
+        assert np.allclose(e[2], want, rtol=0, atol=tol), (e, row)
+    # the winning lines are Figure 1's: intercept + slope * lambda
+    lines = {(s["jhat"], float(s["from"])): (float(s["intercept"]), float(s["slope"]))
+             for s in d["figure1_lines"]}
+    for e, key in zip(ent, [(4, 0.0), (4, 3.0), (1, 3.0), (1, 11.0)]):
+        I, S = lines[key]
+        assert abs(float(e[3]) - I) < 1e-9 and abs(float(e[4]) - S) < 1e-9, (e, key)
+
+
+def _check_against_alg1(X, extra):
+    ent, lams = SP.solution_path(X)
+    starts = [float(e[0]) for e in ent]
+    assert starts[0] == 0.0 and all(b > a for a, b in zip(starts, starts[1:]))
+    # v at an exact breakpoint follows Lemma 1's strict test (see oracle.path);
+    # compare inside intervals, where the solution is one value
+    bps = {float(l) for l in lams} | set(starts)
+    qs = [0.5 * (a + b) for a, b in zip(starts, starts[1:])] + \
+         [starts[-1] + 1.0, 3.0 * starts[-1] + 2.0] + [q for q in extra if q not in bps]
+    for q in qs:
+        g = int(np.searchsorted(starts, q, side="right")) - 1
+        s0, j, v, zi, sl = ent[g]
+        ref = oracle.fit(X, [q], want_all=True)
+        zq = float(zi) + float(sl) * q
+        assert abs(zq - ref["obj"][0]) <= 1e-12 * max(1.0, abs(ref["obj"][0])), (q, zq, ref["obj"])
+        jr = int(ref["jstar"][0])
+        if j != jr:  # only on an exact tie of objectives
+            assert abs(ref["z_all"][0][j] - ref["z_all"][0][jr]) <= 1e-12 * abs(ref["obj"][0])
+        assert np.array_equal(np.array(v), ref["v_all"][0][j].astype(np.float64)), (q, j)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_solution_path_equals_algorithm1_on_integers(seed):
+    X = datagen.small_integers(9, 5, seed, lo=-5, hi=5, zero_frac=0.2, dtype="float64")
+    _check_against_alg1(X, np.linspace(0.0, 30.0, 13))
+
+
+def test_solution_path_equals_algorithm1_on_planted_floats():
+    X, _, _ = datagen.planted(datagen.Planted(25, 5, 2, 0.1, 0.1, 5.0, 8, "float64"))
+    _check_against_alg1(X, np.linspace(0.0, 10.0, 11))
