@@ -193,7 +193,10 @@ int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *l
  * l1line_path_write_* (same X, n, m and workspace, nothing else using the
  * workspace in between) fills out_lambda (DEVICE double), out_v (DEVICE, the
  * input dtype), both of at least offsets[m*m] entries, and out_len (DEVICE
- * int32 [m*m], the number of entries each pair used).
+ * int32 [m*m], the number of entries each pair used).  out_resid (DEVICE
+ * double, same size, or NULL) receives each entry's residual
+ * sum_i |x_ik - v x_ijhat| (double sums), so that on the entry's lambda
+ * interval the pair's term of z_jhat is out_resid + lambda |out_v|.
  */
 size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m);
 int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets,
@@ -201,11 +204,39 @@ int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets
 int l1line_path_count_f64(const double *X, int64_t n, int64_t m, int64_t *offsets,
                           void *workspace, size_t workspace_bytes, void *stream);
 int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *offsets,
-                          double *out_lambda, float *out_v, int32_t *out_len, void *workspace,
-                          size_t workspace_bytes, void *stream);
+                          double *out_lambda, float *out_v, double *out_resid, int32_t *out_len,
+                          void *workspace, size_t workspace_bytes, void *stream);
 int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *offsets,
-                          double *out_lambda, double *out_v, int32_t *out_len, void *workspace,
-                          size_t workspace_bytes, void *stream);
+                          double *out_lambda, double *out_v, double *out_resid, int32_t *out_len,
+                          void *workspace, size_t workspace_bytes, void *stream);
+
+/*
+ * Algorithm 3: the solution path over all lambda >= 0, from the pair paths
+ * of the two calls above (with out_resid).  z_jhat(lambda) = sum_k (resid +
+ * lambda |v|) over the entries holding at lambda is piecewise linear and
+ * concave; the path is the lower envelope min_jhat z_jhat, as Algorithm 3's
+ * per-interval line crossings (beta_L, beta_U) give it.  Outputs (DEVICE,
+ * capacity cap entries): piece e holds from out_start[e] (increasing from 0)
+ * to the next start: jhat* = out_jhat[e] and z* = out_intercept[e] +
+ * out_slope[e] lambda; out_v (cap x m, may be NULL) receives v* on the open
+ * interval after the start.  *out_count (DEVICE int64) = the number of
+ * pieces (only the first cap are written).  entries = offsets[m*m].  Among
+ * identical lines the smallest jhat is named.  z and crossing lambdas are
+ * double sums of the residuals (relative error ~ entries x 2^-53).
+ */
+size_t l1line_solution_path_workspace_bytes(int64_t m, int64_t entries);
+int l1line_solution_path_f32(int64_t m, const int64_t *offsets, const double *lambda,
+                             const float *v, const double *resid, const int32_t *len,
+                             int64_t entries, double *out_start, int32_t *out_jhat,
+                             double *out_intercept, double *out_slope, float *out_v,
+                             int64_t *out_count, int64_t cap, void *workspace,
+                             size_t workspace_bytes, void *stream);
+int l1line_solution_path_f64(int64_t m, const int64_t *offsets, const double *lambda,
+                             const double *v, const double *resid, const int32_t *len,
+                             int64_t entries, double *out_start, int32_t *out_jhat,
+                             double *out_intercept, double *out_slope, double *out_v,
+                             int64_t *out_count, int64_t cap, void *workspace,
+                             size_t workspace_bytes, void *stream);
 
 /*
  * Learned jhat proposer (not in the paper; an extension of Algorithm 1's

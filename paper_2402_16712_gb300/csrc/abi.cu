@@ -273,7 +273,8 @@ int path_count_impl(const T *X, int64_t n, int64_t m, int64_t *offsets, void *ws
     L1L_TRY(scan_pairs<T>(c, &k_zero_lambda, 1, nullptr, m));  // lambda = 0 medians
     if (launch_path<T>(true, c.a.Xt, c.a.Xf, c.a.ci, n, m, c.a.ldn, c.a.v_all, offsets,
                        reinterpret_cast<int64_t *>(c.base + P.scan_tmp), nullptr, nullptr, nullptr,
-                       nullptr, nullptr, nullptr, c.a.status, c.sms, c.st, c.launches) !=
+                       nullptr, nullptr, nullptr, nullptr, c.a.status, c.sms, c.st,
+                       c.launches) !=
         cudaSuccess)
         return L1L_ERR_CUDA;
     g_last_launches = c.launches;
@@ -282,7 +283,8 @@ int path_count_impl(const T *X, int64_t n, int64_t m, int64_t *offsets, void *ws
 
 template <typename T>
 int path_write_impl(const T *X, int64_t n, int64_t m, const int64_t *offsets, double *out_lam,
-                    T *out_v, int32_t *out_len, void *ws, size_t ws_bytes, void *stream) {
+                    T *out_v, double *out_res, int32_t *out_len, void *ws, size_t ws_bytes,
+                    void *stream) {
     g_last_launches = 0;
     if (!X || !offsets || !out_lam || !out_v || !out_len || n < 1 || m < 1) return L1L_ERR_ARG;
     if (n > max_rows_pairs<T>() || m > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
@@ -298,7 +300,7 @@ int path_write_impl(const T *X, int64_t n, int64_t m, const int64_t *offsets, do
                        reinterpret_cast<const float *>(base + P.L.Xf),
                        reinterpret_cast<const ColInfo *>(base + P.L.colinfo), n, m, P.L.ldn,
                        reinterpret_cast<const T *>(base + P.L.v_all),
-                       const_cast<int64_t *>(offsets), nullptr, out_lam, out_v, out_len,
+                       const_cast<int64_t *>(offsets), nullptr, out_lam, out_v, out_res, out_len,
                        reinterpret_cast<int32_t *>(base + P.big),
                        reinterpret_cast<uint32_t *>(base + P.big_count), base + P.scratch,
                        reinterpret_cast<uint32_t *>(base + P.L.status), sms,
@@ -564,17 +566,75 @@ int l1line_path_count_f64(const double *X, int64_t n, int64_t m, int64_t *offset
 }
 
 int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *offsets,
-                          double *out_lambda, float *out_v, int32_t *out_len, void *workspace,
-                          size_t workspace_bytes, void *stream) {
-    return path_write_impl<float>(X, n, m, offsets, out_lambda, out_v, out_len, workspace,
-                                  workspace_bytes, stream);
+                          double *out_lambda, float *out_v, double *out_resid, int32_t *out_len,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    return path_write_impl<float>(X, n, m, offsets, out_lambda, out_v, out_resid, out_len,
+                                  workspace, workspace_bytes, stream);
 }
 
 int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *offsets,
-                          double *out_lambda, double *out_v, int32_t *out_len, void *workspace,
-                          size_t workspace_bytes, void *stream) {
-    return path_write_impl<double>(X, n, m, offsets, out_lambda, out_v, out_len, workspace,
-                                   workspace_bytes, stream);
+                          double *out_lambda, double *out_v, double *out_resid, int32_t *out_len,
+                          void *workspace, size_t workspace_bytes, void *stream) {
+    return path_write_impl<double>(X, n, m, offsets, out_lambda, out_v, out_resid, out_len,
+                                   workspace, workspace_bytes, stream);
+}
+
+size_t l1line_solution_path_workspace_bytes(int64_t m, int64_t entries) {
+    if (m < 1 || entries < 1 || m > 0x7FFFFFFF || entries > ((int64_t)1 << 40)) return 0;
+    if ((double)m * (double)(m + 2) > 1e12) return 0;
+    return solpath_bytes(m, entries);
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+int solution_path_impl(int64_t m, const int64_t *offsets, const double *lam, const T *v,
+                       const double *resid, const int32_t *len, int64_t entries,
+                       double *out_start, int32_t *out_jhat, double *out_intercept,
+                       double *out_slope, T *out_v, int64_t *out_count, int64_t cap, void *ws,
+                       size_t ws_bytes, void *stream) {
+    g_last_launches = 0;
+    if (!offsets || !lam || !v || !resid || !len || !out_start || !out_jhat || !out_intercept ||
+        !out_slope || !out_count || m < 1 || entries < 1 || cap < 1)
+        return L1L_ERR_ARG;
+    const size_t need = l1line_solution_path_workspace_bytes(m, entries);
+    if (need == 0) return L1L_ERR_UNSUPPORTED;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < need)
+        return L1L_ERR_WORKSPACE;
+    int launches = 0;
+    if (launch_solpath<T>(m, offsets, len, lam, v, resid, static_cast<unsigned char *>(ws),
+                          entries, out_start, out_jhat, out_intercept, out_slope, out_v,
+                          out_count, cap, static_cast<cudaStream_t>(stream), launches) !=
+        cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int l1line_solution_path_f32(int64_t m, const int64_t *offsets, const double *lambda,
+                             const float *v, const double *resid, const int32_t *len,
+                             int64_t entries, double *out_start, int32_t *out_jhat,
+                             double *out_intercept, double *out_slope, float *out_v,
+                             int64_t *out_count, int64_t cap, void *workspace,
+                             size_t workspace_bytes, void *stream) {
+    return solution_path_impl<float>(m, offsets, lambda, v, resid, len, entries, out_start,
+                                     out_jhat, out_intercept, out_slope, out_v, out_count, cap,
+                                     workspace, workspace_bytes, stream);
+}
+
+int l1line_solution_path_f64(int64_t m, const int64_t *offsets, const double *lambda,
+                             const double *v, const double *resid, const int32_t *len,
+                             int64_t entries, double *out_start, int32_t *out_jhat,
+                             double *out_intercept, double *out_slope, double *out_v,
+                             int64_t *out_count, int64_t cap, void *workspace,
+                             size_t workspace_bytes, void *stream) {
+    return solution_path_impl<double>(m, offsets, lambda, v, resid, len, entries, out_start,
+                                      out_jhat, out_intercept, out_slope, out_v, out_count, cap,
+                                      workspace, workspace_bytes, stream);
 }
 
 int l1line_status(void *workspace, void *stream) {

@@ -39,6 +39,7 @@ template <typename T> struct PathArgs {
     const int64_t *off;    // write pass: [m*m + 1]
     double *lam;           // write pass outputs
     T *val;
+    double *res;           // optional: residual sum_i |x_ik - v x_ijhat| of each entry
     int32_t *len;          // [m*m]
     int32_t *big;          // pairs whose rows exceed the warp list
     uint32_t *big_count;
@@ -46,6 +47,15 @@ template <typename T> struct PathArgs {
     unsigned char *scratch;  // big-pair lists, one slice per worker warp
     int64_t slice;         // entries per slice (power of two >= n)
     uint32_t *status;
+};
+
+// Double sums of one pass for the residual R(t) = sum_i |x_ik - t x_ijhat|,
+// which for t a ratio value is  Btot - 2 B(t) + t (2 A(t) - Wv) + C0  with
+// A(t), B(t) the sums of |x_ijhat| and sgn(x_ijhat) x_ik over valid rows whose
+// ratio is <= t, Btot, Wv their totals and C0 the sum of |x_ik| over rows with
+// x_ijhat = 0 (|x_ijhat| (r_i - t) = sgn(x_ijhat) x_ik - t |x_ijhat|).
+struct RowSums {
+    double Btot, Wv, C0, Ab, Bb;  // Ab, Bb: over the rows below the range
 };
 
 // Classification of one row against the range between 0 and v0 (exclusive
@@ -147,7 +157,8 @@ __device__ __forceinline__ double fix_to_double(int64_t D, int sigma) {
 template <typename T>
 __device__ void emit_path(const PathArgs<T> &a, int64_t p, T v0, bool pos,
                           const typename Traits<T>::K *keys, const uint32_t *rows, int c,
-                          const int64_t *colq, int64_t Q, int64_t Sbelow, int sigma, int lane) {
+                          const int64_t *colq, int64_t Q, int64_t Sbelow, int sigma,
+                          const T *colb, const T *xk, const RowSums &rs, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
     const unsigned FULL = 0xFFFFFFFFu;
@@ -160,6 +171,8 @@ __device__ void emit_path(const PathArgs<T> &a, int64_t p, T v0, bool pos,
         groups += __popc(__ballot_sync(FULL, end));
     }
     int64_t carry = Sbelow;  // S at the end of the previous chunk
+    double cA = rs.Ab, cB = rs.Bb;  // residual sums at the end of the previous chunk
+    double cQrun = 0.0;             // corrections of the run open at the chunk's end
     int gbase = 0;           // runs ended before this chunk
     for (int i0 = 0; i0 < c; i0 += 32) {
         const int i = i0 + lane;
@@ -168,6 +181,41 @@ __device__ void emit_path(const PathArgs<T> &a, int64_t p, T v0, bool pos,
         const bool end = i < c && (i == c - 1 || keys[i] != keys[i + 1]);
         const unsigned em = __ballot_sync(FULL, end);
         const int g = gbase + __popc(em & ((1u << lane) - 1u));  // run index (ascending)
+        if (a.res) {
+            // A, B: prefix sums through this row.  The formula counts the
+            // rows of t's own run as "ratio <= t"; a row whose exact ratio
+            // lies above its rounded value t then enters with the wrong sign,
+            // so each row of the run adds the correction
+            // qc = |x - t b| - (t |b| - sgn(b) x), summed over the run.
+            double w = 0.0, sx = 0.0, qc = 0.0, t = 0.0;
+            if (i < c) {
+                const double b = (double)colb[rows[i]], x = (double)xk[rows[i]];
+                t = (double)Tr::value(keys[i]);
+                w = fabs(b);
+                sx = b < 0.0 ? -x : x;
+                qc = fabs(x - t * b) - (t * w - sx);
+            }
+            const double A = cA + warp_scan_add(w, lane), B = cB + warp_scan_add(sx, lane);
+            const double Qi = warp_scan_add(qc, lane);  // inclusive, this chunk only
+            // run sums of qc: the run's start holds the prefix before it
+            const bool start = i < c && (i == 0 || keys[i - 1] != keys[i]);
+            const unsigned smk = __ballot_sync(FULL, start);
+            const double Qs = Qi - qc;  // chunk prefix before this row
+            const unsigned upto = smk & (lane == 31 ? FULL : ((2u << lane) - 1u));
+            const int hs = upto ? 31 - __clz(upto) : -1;
+            const double Qstart = __shfl_sync(FULL, Qs, hs < 0 ? 0 : hs);
+            // the run began in an earlier chunk: its prefix is cQ - cQrun
+            const double run_q = hs >= 0 ? Qi - Qstart : cQrun + Qi;
+            if (end) {  // each run writes the residual of its own entry
+                const int slot = pos ? groups - 1 - g : g;
+                a.res[o + slot] = rs.Btot - 2.0 * B + t * (2.0 * A - rs.Wv) + rs.C0 + run_q;
+            }
+            // the run still open at the end of this chunk carries its partial sum
+            const double last = __shfl_sync(FULL, run_q, 31);
+            cQrun = last;
+            cA = __shfl_sync(FULL, A, 31);
+            cB = __shfl_sync(FULL, B, 31);
+        }
         if (end) {
             if (pos) {
                 // run g (not the top one) starts at Q - 2 S(t_g), slot groups-1-g
@@ -194,6 +242,8 @@ __device__ void emit_path(const PathArgs<T> &a, int64_t p, T v0, bool pos,
             a.lam[o + groups] = D > 0 ? fix_to_double(D, sigma) : 0.0;
             a.val[o + groups] = T(0);
         }
+        // v = 0: R = Btot - 2 B(0) + C0 with B(0) the signed sum over ratios <= 0
+        if (a.res) a.res[o + groups] = rs.Btot - 2.0 * (pos ? rs.Bb : cB) + rs.C0;
         a.len[p] = groups + 1;
     }
 }
@@ -206,23 +256,40 @@ __device__ int scan_rows(const PathArgs<T> &a, int64_t j, int64_t k, const T *co
                          const float *inv, const int64_t *colq, bool wide, bool pos,
                          uint32_t ck_lo, uint32_t ck_hi, typename Traits<T>::K kv,
                          typename Traits<T>::K *keys, uint32_t *rows, int cap, int64_t &Sbelow,
-                         int lane) {
+                         RowSums &rs, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
     const unsigned FULL = 0xFFFFFFFFu;
     const T *xk = a.Xt + k * a.ldn;
     const float *xf = a.Xf + k * a.ldn;
+    const bool want_r = !COUNT && a.res != nullptr;
     int c = 0;
     int64_t sb = 0;
+    double bt = 0.0, wv = 0.0, c0 = 0.0, ab = 0.0, bb = 0.0;
     for (int i0 = 0; i0 < (int)a.n; i0 += 32) {
         const int i = i0 + lane;
         int cls = 1;
         K ke = Tr::NONE;
-        if (i < a.n && colb[i] != T(0))
+        const bool valid = i < a.n && colb[i] != T(0);
+        if (valid)
             cls = classify<T>(xf[i], inv[i], xk[i], colb[i], wide, pos, ck_lo, ck_hi, kv, ke);
         if (!COUNT) {
             if (cls < 0) sb += colq[i];
             if (cls == 0 && ke == Tr::NONE) ke = Tr::key(Tr::div_rn(xk[i], colb[i]));
+        }
+        if (want_r && i < a.n) {
+            const double x = (double)xk[i], b = (double)colb[i];
+            if (valid) {
+                const double sx = b < 0.0 ? -x : x;
+                bt += sx;
+                wv += fabs(b);
+                if (cls < 0) {
+                    ab += fabs(b);
+                    bb += sx;
+                }
+            } else {
+                c0 += fabs(x);
+            }
         }
         const unsigned im = __ballot_sync(FULL, cls == 0);
         if (!COUNT && cls == 0) {
@@ -235,6 +302,13 @@ __device__ int scan_rows(const PathArgs<T> &a, int64_t j, int64_t k, const T *co
         c += __popc(im);
     }
     if (!COUNT) Sbelow = warp_sum_i64(sb);
+    if (want_r) {
+        rs.Btot = warp_sum_f64(bt);
+        rs.Wv = warp_sum_f64(wv);
+        rs.C0 = warp_sum_f64(c0);
+        rs.Ab = warp_sum_f64(ab);
+        rs.Bb = warp_sum_f64(bb);
+    }
     __syncwarp();
     return c;
 }
@@ -268,6 +342,12 @@ __global__ void __launch_bounds__(PW * 32) k_path_pass(PathArgs<T> a, int kchunk
         const int64_t p = j * a.m + k;
         const T v0 = a.v0[p];
         if (k == j || v0 == T(0) || cj.n_valid == 0) {  // constant path
+            double r = 0.0;  // v = 1 for k == jhat: zero residual; v = 0: sum |x_ik|
+            if (!COUNT && a.res && k != j) {
+                const T *xk = a.Xt + k * a.ldn;
+                for (int i = lane; i < (int)a.n; i += 32) r += fabs((double)xk[i]);
+                r = warp_sum_f64(r);
+            }
             if (lane == 0) {
                 if (COUNT) {
                     a.bound[p] = 1;
@@ -275,6 +355,7 @@ __global__ void __launch_bounds__(PW * 32) k_path_pass(PathArgs<T> a, int kchunk
                     const int64_t off = a.off[p];
                     a.lam[off] = 0.0;
                     a.val[off] = k == j ? T(1) : T(0);
+                    if (a.res) a.res[off] = r;
                     a.len[p] = 1;
                 }
             }
@@ -286,8 +367,9 @@ __global__ void __launch_bounds__(PW * 32) k_path_pass(PathArgs<T> a, int kchunk
         range_of<T>(v0, pos, ck_lo, ck_hi, kv);
         const bool wide = pair_is_wide<T>(a, cj, k);
         int64_t Sbelow = 0;
+        RowSums rs{};
         const int c = scan_rows<T, COUNT>(a, j, k, colb, inv, colq, wide, pos, ck_lo, ck_hi, kv,
-                                          keys, rows, PATH_CAP, Sbelow, lane);
+                                          keys, rows, PATH_CAP, Sbelow, rs, lane);
         if (COUNT) {
             if (lane == 0) a.bound[p] = (int64_t)c + 1;
             continue;
@@ -299,7 +381,8 @@ __global__ void __launch_bounds__(PW * 32) k_path_pass(PathArgs<T> a, int kchunk
         int P = 32;
         while (P < c) P <<= 1;
         warp_list_sort<K>(keys, rows, c, P, lane);
-        emit_path<T>(a, p, v0, pos, keys, rows, c, colq, cj.Q, Sbelow, cj.sigma, lane);
+        emit_path<T>(a, p, v0, pos, keys, rows, c, colq, cj.Q, Sbelow, cj.sigma, colb,
+                     a.Xt + k * a.ldn, rs, lane);
         __syncwarp();
     }
 }
@@ -344,13 +427,15 @@ __global__ void __launch_bounds__(128) k_path_big(PathArgs<T> a) {
         K kv;
         range_of<T>(v0, pos, ck_lo, ck_hi, kv);
         int64_t Sbelow = 0;
+        RowSums rs{};
         const int c = scan_rows<T, false>(a, j, k, cb, ci_inv, cq, pair_is_wide<T>(a, cj, k), pos,
                                           ck_lo, ck_hi, kv, keys, rows, (int)a.slice, Sbelow,
-                                          lane);
+                                          rs, lane);
         int P = 32;
         while (P < c) P <<= 1;
         warp_list_sort<K>(keys, rows, c, P, lane);
-        emit_path<T>(a, p, v0, pos, keys, rows, c, cq, cj.Q, Sbelow, cj.sigma, lane);
+        emit_path<T>(a, p, v0, pos, keys, rows, c, cq, cj.Q, Sbelow, cj.sigma, cb,
+                     a.Xt + k * a.ldn, rs, lane);
         __syncwarp();
     }
 }
@@ -410,6 +495,15 @@ __global__ void k_scan_add(int64_t *out, const int64_t *bsum, int64_t N) {
 }  // namespace
 
 size_t path_scan_scratch(int64_t N) { return (size_t)((N + SCAN_B - 1) / SCAN_B) * 8; }
+
+cudaError_t launch_scan_i64(int64_t *a, int64_t N, int64_t *tmp, cudaStream_t st, int &launches) {
+    const int64_t nb = (N + SCAN_B - 1) / SCAN_B;
+    k_scan_blocks<<<(unsigned)nb, SCAN_B, 0, st>>>(a, a, tmp, N);
+    k_scan_tops<<<1, SCAN_B, 0, st>>>(tmp, nb, a + N);
+    k_scan_add<<<(unsigned)nb, SCAN_B, 0, st>>>(a, tmp, N);
+    launches += 3;
+    return cudaGetLastError();
+}
 int path_big_workers() { return 64; }
 
 template <typename T> size_t path_slice_bytes(int64_t n) {
@@ -427,9 +521,9 @@ template <typename T> size_t path_smem_bytes(int64_t n) {
 template <typename T>
 cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo *ci, int64_t n,
                         int64_t m, int64_t ldn, const T *v0, int64_t *bound_or_off,
-                        int64_t *scan_tmp, double *lam, T *val, int32_t *len, int32_t *big,
-                        uint32_t *big_count, unsigned char *scratch, uint32_t *status,
-                        int num_sms, cudaStream_t st, int &launches) {
+                        int64_t *scan_tmp, double *lam, T *val, double *res, int32_t *len,
+                        int32_t *big, uint32_t *big_count, unsigned char *scratch,
+                        uint32_t *status, int num_sms, cudaStream_t st, int &launches) {
     PathArgs<T> a{};
     a.Xt = Xt;
     a.Xf = Xf;
@@ -453,17 +547,12 @@ cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo 
         launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         // exclusive scan of the m*m bounds, in place, total at [m*m]
-        const int64_t N = m * m;
-        const int64_t nb = (N + SCAN_B - 1) / SCAN_B;
-        k_scan_blocks<<<(unsigned)nb, SCAN_B, 0, st>>>(bound_or_off, bound_or_off, scan_tmp, N);
-        k_scan_tops<<<1, SCAN_B, 0, st>>>(scan_tmp, nb, bound_or_off + N);
-        k_scan_add<<<(unsigned)nb, SCAN_B, 0, st>>>(bound_or_off, scan_tmp, N);
-        launches += 3;
-        return cudaGetLastError();
+        return launch_scan_i64(bound_or_off, m * m, scan_tmp, st, launches);
     }
     a.off = bound_or_off;
     a.lam = lam;
     a.val = val;
+    a.res = res;
     a.len = len;
     a.big = big;
     a.big_count = big_count;
@@ -487,13 +576,13 @@ template size_t path_slice_bytes<float>(int64_t);
 template size_t path_slice_bytes<double>(int64_t);
 template cudaError_t launch_path<float>(bool, const float *, const float *, const ColInfo *,
                                         int64_t, int64_t, int64_t, const float *, int64_t *,
-                                        int64_t *, double *, float *, int32_t *, int32_t *,
-                                        uint32_t *, unsigned char *, uint32_t *, int,
+                                        int64_t *, double *, float *, double *, int32_t *,
+                                        int32_t *, uint32_t *, unsigned char *, uint32_t *, int,
                                         cudaStream_t, int &);
 template cudaError_t launch_path<double>(bool, const double *, const float *, const ColInfo *,
                                          int64_t, int64_t, int64_t, const double *, int64_t *,
-                                         int64_t *, double *, double *, int32_t *, int32_t *,
-                                         uint32_t *, unsigned char *, uint32_t *, int,
+                                         int64_t *, double *, double *, double *, int32_t *,
+                                         int32_t *, uint32_t *, unsigned char *, uint32_t *, int,
                                          cudaStream_t, int &);
 
 }  // namespace l1l

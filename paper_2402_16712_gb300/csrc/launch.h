@@ -82,8 +82,19 @@ cudaError_t launch_mlp_pack(const float *theta, l1line_mlp *out, cudaStream_t st
 cudaError_t launch_topk(const float *score, int64_t m, int K, int32_t *out, cudaStream_t st,
                         int &launches);
 
+// ---- Algorithm 3: the solution path (k_solpath.cu) ----
+size_t solpath_bytes(int64_t m, int64_t entries);
+template <typename T>
+cudaError_t launch_solpath(int64_t m, const int64_t *off, const int32_t *len, const double *lam,
+                           const T *val, const double *res, unsigned char *ws, int64_t entries,
+                           double *out_start, int32_t *out_jhat, double *out_I, double *out_s,
+                           T *out_v, int64_t *out_count, int64_t cap, cudaStream_t st,
+                           int &launches);
+
 // ---- Algorithm 2: lambda paths of every pair (k_path.cu) ----
 size_t path_scan_scratch(int64_t N);
+// In place: a[0..N) -> its exclusive prefix sums, a[N] = total (tmp: path_scan_scratch(N)).
+cudaError_t launch_scan_i64(int64_t *a, int64_t N, int64_t *tmp, cudaStream_t st, int &launches);
 int path_big_workers();
 template <typename T> size_t path_slice_bytes(int64_t n);
 // count: bound_or_off = [m*m + 1] offsets out (exclusive scan of the bounds);
@@ -91,9 +102,9 @@ template <typename T> size_t path_slice_bytes(int64_t n);
 template <typename T>
 cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo *ci, int64_t n,
                         int64_t m, int64_t ldn, const T *v0, int64_t *bound_or_off,
-                        int64_t *scan_tmp, double *lam, T *val, int32_t *len, int32_t *big,
-                        uint32_t *big_count, unsigned char *scratch, uint32_t *status,
-                        int num_sms, cudaStream_t st, int &launches);
+                        int64_t *scan_tmp, double *lam, T *val, double *res, int32_t *len,
+                        int32_t *big, uint32_t *big_count, unsigned char *scratch,
+                        uint32_t *status, int num_sms, cudaStream_t st, int &launches);
 
 // The batched fit: staging, one persistent pair kernel, exact path, sums, argmin.
 template <typename T>

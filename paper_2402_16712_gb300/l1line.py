@@ -59,8 +59,13 @@ SIGNATURES = {
     "l1line_path_workspace_bytes": (_SZ, [_I, _I64, _I64]),
     "l1line_path_count_f32": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
     "l1line_path_count_f64": (_I, [_P, _I64, _I64, _P, _P, _SZ, _P]),
-    "l1line_path_write_f32": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
-    "l1line_path_write_f64": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_path_write_f32": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_path_write_f64": (_I, [_P, _I64, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    "l1line_solution_path_workspace_bytes": (_SZ, [_I64, _I64]),
+    "l1line_solution_path_f32": (_I, [_I64, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P,
+                                      _I64, _P, _SZ, _P]),
+    "l1line_solution_path_f64": (_I, [_I64, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P,
+                                      _I64, _P, _SZ, _P]),
     "l1line_set_tuning": (_I, [_P]),
     "l1line_plan": (_I, [_I, _I64, _I64, _I64, _P]),
 }
@@ -353,11 +358,13 @@ def path_workspace(dtype, n: int, m: int, device=None) -> "Workspace":
     return Workspace(nb, device)
 
 
-def paths(X, workspace: Optional[Workspace] = None, stream=None):
+def paths(X, workspace: Optional[Workspace] = None, stream=None, residuals=False):
     """Algorithm 2 for every (jhat, k): returns (offsets [m*m + 1] int64 CUDA,
-    lam double CUDA, v CUDA (X's dtype), length [m*m] int32 CUDA, workspace).
-    Pair p = jhat * m + k owns entries offsets[p] .. offsets[p] + length[p].
-    Reads the entry count back to the host between the two library calls."""
+    lam double CUDA, v CUDA (X's dtype), length [m*m] int32 CUDA, workspace),
+    and with residuals=True also the residual of every entry (double CUDA) as
+    a sixth item.  Pair p = jhat * m + k owns entries offsets[p] ..
+    offsets[p] + length[p].  Reads the entry count back to the host between
+    the two library calls."""
     import torch
     _check_x(X)
     n, m = X.shape
@@ -371,10 +378,47 @@ def paths(X, workspace: Optional[Workspace] = None, stream=None):
     lam = torch.empty(max(total, 1), dtype=torch.float64, device=X.device)
     v = torch.empty(max(total, 1), dtype=X.dtype, device=X.device)
     ln = torch.empty(m * m, dtype=torch.int32, device=X.device)
+    res = torch.empty(max(total, 1), dtype=torch.float64, device=X.device) if residuals else None
     wr = load().l1line_path_write_f32 if f32 else load().l1line_path_write_f64
-    _check(wr(X.data_ptr(), n, m, off.data_ptr(), lam.data_ptr(), v.data_ptr(), ln.data_ptr(),
-              ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream)), "l1line_path_write")
+    _check(wr(X.data_ptr(), n, m, off.data_ptr(), lam.data_ptr(), v.data_ptr(), _ptr(res),
+              ln.data_ptr(), ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream)),
+           "l1line_path_write")
+    if residuals:
+        return off, lam, v, ln, ws, res
     return off, lam, v, ln, ws
+
+
+def solution_path(X, cap: int = 4096, stream=None):
+    """Algorithms 2 and 3: the solution path of X over all lambda >= 0.
+    Returns (start, jhat, intercept, slope, v) CPU tensors of the pieces:
+    from start[e] on, jhat* = jhat[e], z* = intercept[e] + slope[e] lambda and
+    v* = v[e] (on the open interval after the start)."""
+    import torch
+    _check_x(X)
+    n, m = X.shape
+    off, lam, v, ln, pws, res = paths(X, stream=stream, residuals=True)
+    entries = int(off[m * m].item())
+    nb = int(load().l1line_solution_path_workspace_bytes(m, entries))
+    if nb == 0:
+        raise L1LineError(ERR_UNSUPPORTED, "l1line_solution_path_workspace_bytes")
+    ws = Workspace(nb, X.device)
+    dev = X.device
+    start = torch.empty(cap, dtype=torch.float64, device=dev)
+    jh = torch.empty(cap, dtype=torch.int32, device=dev)
+    I = torch.empty(cap, dtype=torch.float64, device=dev)
+    S = torch.empty(cap, dtype=torch.float64, device=dev)
+    vs = torch.empty((cap, m), dtype=X.dtype, device=dev)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    f = (load().l1line_solution_path_f32 if X.dtype == torch.float32
+         else load().l1line_solution_path_f64)
+    _check(f(m, off.data_ptr(), lam.data_ptr(), v.data_ptr(), res.data_ptr(), ln.data_ptr(),
+             entries, start.data_ptr(), jh.data_ptr(), I.data_ptr(), S.data_ptr(), vs.data_ptr(),
+             count.data_ptr(), cap, ctypes.c_void_p(ws.ptr), ws.nbytes, _stream_ptr(stream)),
+           "l1line_solution_path")
+    c = int(count.item())
+    if c > cap:
+        return solution_path(X, cap=c, stream=stream)
+    return start[:c].cpu(), jh[:c].cpu(), I[:c].cpu(), S[:c].cpu(), vs[:c].cpu()
 
 
 class Tuning(ctypes.Structure):
