@@ -222,7 +222,10 @@ int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *
  * interval after the start.  *out_count (DEVICE int64) = the number of
  * pieces (only the first cap are written).  entries = offsets[m*m].  Among
  * identical lines the smallest jhat is named.  z and crossing lambdas are
- * double sums of the residuals (relative error ~ entries x 2^-53).
+ * double sums of the residuals (relative error ~ entries x 2^-53); values and
+ * slopes agreeing to a relative 1e-12 are taken as equal.  The workspace
+ * (l1line_solution_path_workspace_bytes, 256-byte aligned) starts with a
+ * status word that l1line_status reads.
  */
 size_t l1line_solution_path_workspace_bytes(int64_t m, int64_t entries);
 int l1line_solution_path_f32(int64_t m, const int64_t *offsets, const double *lambda,

@@ -253,59 +253,153 @@ __global__ void __launch_bounds__(ZB) k_zbuild(int64_t m, const int64_t *off, co
 // breakpoint every slope is exactly 1 and rounding would otherwise invent a
 // crossing).
 constexpr double SOL_RTOL = 1e-12;
-__device__ int64_t min_merge(const Piece *F, int64_t a, const Piece *G, int64_t b, Piece *out) {
-    int64_t pf = 0, pg = 0, w = 0;
-    double cur = 0.0;
-    auto emit = [&](const Piece &p, double start) {
-        if (w > 0 && out[w - 1].owner == p.owner && out[w - 1].I == p.I && out[w - 1].s == p.s)
-            return;
-        Piece q = p;
-        q.lam = start;
-        out[w++] = q;
-    };
-    for (;;) {
-        const double nf = pf + 1 < a ? F[pf + 1].lam : INFINITY;
-        const double ng = pg + 1 < b ? G[pg + 1].lam : INFINITY;
-        const double end = fmin(nf, ng);
-        const Piece &f = F[pf], &g = G[pg];
-        double dI = f.I - g.I, ds = f.s - g.s;  // (f - g)(lambda) = dI + ds lambda
-        if (fabs(ds) <= SOL_RTOL * fmax(fabs(f.s), fabs(g.s))) ds = 0.0;
-        double d0 = dI + ds * cur;
-        if (fabs(d0) <= SOL_RTOL * (fabs(f.I) + fabs(g.I) + (fabs(f.s) + fabs(g.s)) * cur))
-            d0 = 0.0;
-        const bool f_first = d0 < 0.0 || (d0 == 0.0 && (ds < 0.0 || (ds == 0.0 && f.owner <= g.owner)));
-        emit(f_first ? f : g, cur);
-        if (ds != 0.0) {
-            const double x = -dI / ds;  // the lines cross at x
-            if (x > cur && x < end) {
-                // past the crossing, f is lower exactly when f - g decreases
-                const bool f_after = ds < 0.0;
-                if (f_after != f_first) emit(f_after ? f : g, x);
-            }
+// The winner(s) on one elementary interval [cur, end) where F is the line f
+// and G the line g: calls emit(line, start) once or twice (a crossing).
+template <typename E>
+__device__ __forceinline__ void interval_min(const Piece &f, const Piece &g, double cur,
+                                             double end, E &&emit) {
+    double dI = f.I - g.I, ds = f.s - g.s;  // (f - g)(lambda) = dI + ds lambda
+    if (fabs(ds) <= SOL_RTOL * fmax(fabs(f.s), fabs(g.s))) ds = 0.0;
+    double d0 = dI + ds * cur;
+    if (fabs(d0) <= SOL_RTOL * (fabs(f.I) + fabs(g.I) + (fabs(f.s) + fabs(g.s)) * cur)) d0 = 0.0;
+    const bool f_first =
+        d0 < 0.0 || (d0 == 0.0 && (ds < 0.0 || (ds == 0.0 && f.owner <= g.owner)));
+    emit(f_first ? f : g, cur);
+    if (ds != 0.0) {
+        const double x = -dI / ds;  // the lines cross at x
+        if (x > cur && x < end) {
+            // past the crossing, f is lower exactly when f - g decreases
+            const bool f_after = ds < 0.0;
+            if (f_after != f_first) emit(f_after ? f : g, x);
         }
-        if (!(end < INFINITY)) break;
-        cur = end;
-        if (nf == end) ++pf;
-        if (ng == end) ++pg;
     }
-    return w;
 }
 
-// One level of the envelope tree: function i (multiple of 2 * half) absorbs
-// function i + half.  Regions at dbase[i]; counts in pcount[i].
-__global__ void k_envelope_level(int64_t m, int64_t half, const int64_t *dbase,
-                                 const Piece *in, Piece *outb, int64_t *pcount) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t * 2 * half;
+__device__ __forceinline__ bool same_line(const Piece &a, const Piece &b) {
+    return a.owner == b.owner && a.I == b.I && a.s == b.s;
+}
+
+constexpr int EB = 256;  // threads per envelope merge
+
+// Minimum of two concave piecewise-linear functions F (a pieces) and G (b
+// pieces), both starting at 0, by one CTA.  The merged sequence of piece
+// starts is split evenly (merge path); each thread handles the elementary
+// intervals that end at its consumed starts: a counting pass, a block scan of
+// the counts (dropping a thread's first piece when it repeats the previous
+// thread's last one), then the writing pass.  Returns the piece count, or -1
+// when it would exceed cap.
+__device__ int64_t block_min_merge(const Piece *F, int64_t a, const Piece *G, int64_t b,
+                                   Piece *out, int64_t cap) {
+    __shared__ int64_t s_cnt[EB / 32];
+    __shared__ int s_last[EB];
+    __shared__ Piece s_lastp[EB], s_firstp[EB];
+    const int t = threadIdx.x;
+    const int64_t L = a + b;
+    const int64_t p0 = L * t / EB, p1 = L * (t + 1) / EB;
+    // merge-path split: i starts of F among the first p0 consumed
+    int64_t lo = p0 > b ? p0 - b : 0, hi = p0 < a ? p0 : a;
+    while (lo < hi) {
+        const int64_t i = (lo + hi) >> 1;
+        if (F[i].lam <= G[p0 - 1 - i].lam)
+            lo = i + 1;
+        else
+            hi = i;
+    }
+    const int64_t i_start = lo, j_start = p0 - lo;
+    // one walk, run twice: count (write == false) or write at base
+    auto walk = [&](bool write, int64_t base, bool drop_first, Piece &first, Piece &last,
+                    int64_t &count) {
+        int64_t i = i_start, j = j_start, w = 0;
+        bool have = false;
+        Piece prev;
+        auto emit = [&](const Piece &ln, double start) {
+            if (have && same_line(prev, ln)) return;
+            if (!have) first = ln;
+            const bool skip = !have && drop_first;
+            have = true;
+            prev = ln;
+            if (skip) return;
+            if (write && base + w < cap) {
+                Piece q = ln;
+                q.lam = start;
+                out[base + w] = q;
+            }
+            ++w;
+        };
+        for (int64_t p = p0; p < p1; ++p) {
+            if (j >= b || (i < a && F[i].lam <= G[j].lam))
+                ++i;
+            else
+                ++j;
+            if (i < 1 || j < 1) continue;
+            const double cur = fmax(F[i - 1].lam, G[j - 1].lam);
+            const double end = fmin(i < a ? F[i].lam : INFINITY, j < b ? G[j].lam : INFINITY);
+            if (!(cur < end)) continue;
+            interval_min(F[i - 1], G[j - 1], cur, end, emit);
+        }
+        if (have) last = prev;
+        count = w;
+        return have;
+    };
+    Piece first{}, last{};
+    int64_t c = 0;
+    const bool have = walk(false, 0, false, first, last, c);
+    s_last[t] = have ? t : -1;
+    s_lastp[t] = last;
+    s_firstp[t] = first;
+    __syncthreads();
+    // nearest earlier thread that produced a piece (its last line)
+    int prev_t = -1;
+    for (int u = t - 1; u >= 0; --u)
+        if (s_last[u] >= 0) {
+            prev_t = u;
+            break;
+        }
+    const bool drop = have && prev_t >= 0 && same_line(s_lastp[prev_t], s_firstp[t]);
+    const int64_t mine = c - (drop ? 1 : 0);
+    // block exclusive scan of the counts
+    int64_t incl = mine;
+    const int lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_cnt[warp] = incl;
+    __syncthreads();
+    int64_t before = 0, total = 0;
+    for (int w = 0; w < EB / 32; ++w) {
+        if (w < warp) before += s_cnt[w];
+        total += s_cnt[w];
+    }
+    const int64_t base = before + incl - mine;
+    int64_t c2 = 0;
+    walk(true, base, drop, first, last, c2);
+    __syncthreads();
+    return total > cap ? -1 : total;
+}
+
+// One level of the envelope tree, one CTA per merge: function i (a multiple
+// of 2 * half) absorbs function i + half.  Regions at dbase[i]; counts in
+// pcount[i]; a piece count beyond the region sets status bit ST_INTERNAL.
+__global__ void __launch_bounds__(EB) k_envelope_level(int64_t m, int64_t half,
+                                                        const int64_t *dbase, const Piece *in,
+                                                        Piece *outb, int64_t *pcount,
+                                                        uint32_t *status) {
+    const int64_t i = (int64_t)blockIdx.x * 2 * half;
     if (i >= m) return;
     const int64_t bi = dbase[i];
-    const Piece *F = in + bi;
     const int64_t a = pcount[i];
     if (i + half < m) {
         const int64_t bg = dbase[i + half];
-        pcount[i] = min_merge(F, a, in + bg, pcount[i + half], outb + bi);
+        const int64_t cap = dbase[min(m, i + 2 * half)] - bi;
+        const int64_t r = block_min_merge(in + bi, a, in + bg, pcount[i + half], outb + bi, cap);
+        if (threadIdx.x == 0) {
+            if (r < 0) atomicOr(status, ST_INTERNAL);
+            pcount[i] = r < 0 ? cap : r;
+        }
     } else {
-        for (int64_t e = 0; e < a; ++e) outb[bi + e] = F[e];
+        for (int64_t e = threadIdx.x; e < a; e += blockDim.x) outb[bi + e] = in[bi + e];
     }
 }
 
@@ -354,7 +448,7 @@ __global__ void k_solution_out(const Piece *env, const int64_t *pcount, int64_t 
 // then three piece buffers of (entries + m).
 size_t solpath_bytes(int64_t m, int64_t entries) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-    size_t o = 0;
+    size_t o = 256;  // status word
     o += al((size_t)(m + 1) * 8);
     o += al((size_t)m * 8);
     o += 2 * al((size_t)m * (m + 2) * 8);
@@ -371,6 +465,8 @@ cudaError_t launch_solpath(int64_t m, const int64_t *off, const int32_t *len, co
                            int &launches) {
     auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     size_t o = 0;
+    uint32_t *status = reinterpret_cast<uint32_t *>(ws + o);  // read by l1line_status
+    o += 256;
     int64_t *dbase = reinterpret_cast<int64_t *>(ws + o);
     o += al((size_t)(m + 1) * 8);
     int64_t *pcount = reinterpret_cast<int64_t *>(ws + o);
@@ -386,6 +482,7 @@ cudaError_t launch_solpath(int64_t m, const int64_t *off, const int32_t *len, co
     Piece *B = reinterpret_cast<Piece *>(ws + o + pb);
     Piece *P = reinterpret_cast<Piece *>(ws + o + 2 * pb);
     cudaError_t e;
+    if ((e = cudaMemsetAsync(status, 0, sizeof(uint32_t), st)) != cudaSuccess) return e;
     k_zcount<<<(unsigned)m, 256, 0, st>>>(len, m, dbase);
     launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -398,8 +495,8 @@ cudaError_t launch_solpath(int64_t m, const int64_t *off, const int32_t *len, co
     Piece *in = P, *outb = A;
     for (int64_t half = 1; half < m; half *= 2) {
         const int64_t merges = (m + 2 * half - 1) / (2 * half);
-        k_envelope_level<<<(unsigned)((merges + 127) / 128), 128, 0, st>>>(m, half, dbase, in,
-                                                                         outb, pcount);
+        k_envelope_level<<<(unsigned)merges, EB, 0, st>>>(m, half, dbase, in, outb, pcount,
+                                                          status);
         launches++;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         Piece *t = in;
