@@ -441,6 +441,29 @@ def measure_extras(dev, stream, flush):
         "ms_per_step": ms, "breakpoints": entries,
         "breakpoints_per_s": entries / (ms * 1e-3), "pairs_per_s": 2000 * 1999 / (ms * 1e-3)}
     del Xd, pws, off, lam_o, v_o, ln
+    # Algorithms 2 + 3: the whole solution path of the 1000 x 500 lambda-path matrix
+    X, _, _ = datagen.lambda_path("float32")
+    Xd = torch.from_numpy(X).to(dev)
+    with torch.cuda.stream(stream):
+        l1line.solution_path(Xd, stream=stream)
+    stream.synchronize()
+    tms = []
+    for _ in range(3):
+        flush.fill_(4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            st, jh, I, S, V = l1line.solution_path(Xd, stream=stream)
+        stream.synchronize()
+        tms.append((time.perf_counter() - t0) * 1e3)
+    out["solution_path"] = {
+        "workload": "Algorithms 2 and 3 on the n=1000, m=500 float32 lambda-path matrix: every "
+                    "pair's path with residuals, per-jhat objectives, lower envelope "
+                    "(host-timed, includes the host reads of the sizes and the workspace "
+                    "allocation)",
+        "ms_per_step": statistics.median(tms), "pieces": int(st.numel()),
+        "jhat_star": sorted({int(x) for x in jh.tolist()})}
+    del Xd
     # uneven batch: 256 instances, n~U[100,5000], m~U[10,500], lambda=0.2
     batch = datagen.uneven_batch(256)
     Xs = [torch.from_numpy(Xb).to(dev) for Xb, _ in batch]
