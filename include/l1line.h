@@ -242,6 +242,26 @@ int l1line_solution_path_f64(int64_t m, const int64_t *offsets, const double *la
                              size_t workspace_bytes, void *stream);
 
 /*
+ * Successive components (the paper's remark after Proposition 5: apply
+ * Algorithm 1 again to the data projected onto the null space of the
+ * components found so far).  Reading of the projection, which the paper does
+ * not define: component (jhat, v) represents x_i by x_ijhat v, so the
+ * projected point is the residual x_i - x_ijhat v, rounded per operation in
+ * the input precision: x'_ik = fl(x_ik - fl(v_k x_ijhat)) (column jhat becomes
+ * 0).  ncomp fits at one lambda, each on the data deflated by all earlier
+ * components: out_v [ncomp][m], out_obj [ncomp], out_jstar [ncomp] (DEVICE).
+ * Workspace: l1line_components_workspace_bytes (fit workspace + two copies
+ * of X); l1line_status reads its status.
+ */
+size_t l1line_components_workspace_bytes(int dtype, int64_t n, int64_t m);
+int l1line_components_f32(const float *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
+                          float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
+                          size_t workspace_bytes, void *stream);
+int l1line_components_f64(const double *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
+                          double *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
+                          size_t workspace_bytes, void *stream);
+
+/*
  * Learned jhat proposer (not in the paper; an extension of Algorithm 1's
  * outer loop): a small network scores every candidate jhat from three column
  * features, and only the K best-scored candidates are fitted exactly (the

@@ -637,6 +637,68 @@ int l1line_solution_path_f64(int64_t m, const int64_t *offsets, const double *la
                                       workspace, workspace_bytes, stream);
 }
 
+size_t l1line_components_workspace_bytes(int dtype, int64_t n, int64_t m) {
+    const size_t fw = l1line_workspace_bytes(dtype, n, m, 1);
+    if (fw == 0) return 0;
+    const size_t es = dtype == L1L_DTYPE_F32 ? 4 : 8;
+    return fw + 2 * al256((size_t)n * (size_t)m * es);
+}
+
+}  // extern "C"
+
+namespace {
+template <typename T>
+int components_impl(const T *X, int64_t n, int64_t m, double lambda, int64_t ncomp, T *out_v,
+                    double *out_obj, int32_t *out_jstar, void *ws, size_t ws_bytes,
+                    void *stream) {
+    if (!X || !out_v || !out_obj || !out_jstar || n < 1 || m < 1 || ncomp < 1)
+        return L1L_ERR_ARG;
+    if (!(lambda >= 0.0) || std::isinf(lambda)) return L1L_ERR_ARG;
+    const size_t fw = l1line_workspace_bytes(dtype_of<T>(), n, m, 1);
+    const size_t need = l1line_components_workspace_bytes(dtype_of<T>(), n, m);
+    if (fw == 0 || need == 0) return L1L_ERR_UNSUPPORTED;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < need)
+        return L1L_ERR_WORKSPACE;
+    const int sms = num_sms();
+    if (sms <= 0) return L1L_ERR_CUDA;
+    unsigned char *base = static_cast<unsigned char *>(ws);
+    T *buf[2] = {reinterpret_cast<T *>(base + fw),
+                 reinterpret_cast<T *>(base + fw + al256((size_t)n * (size_t)m * sizeof(T)))};
+    const T *cur = X;
+    int launches = 0;
+    for (int64_t c = 0; c < ncomp; ++c) {
+        L1L_TRY(fit_impl<T>(cur, n, m, &lambda, 1, nullptr, 0, out_v + c * m, out_obj + c,
+                            out_jstar + c, ws, fw, stream));
+        launches += g_last_launches;
+        if (c + 1 < ncomp) {
+            T *next = buf[c & 1];
+            if (launch_deflate<T>(cur, next, n, m, out_jstar + c, out_v + c * m, sms,
+                                  static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+                return L1L_ERR_CUDA;
+            cur = next;
+        }
+    }
+    g_last_launches = launches;
+    return L1L_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int l1line_components_f32(const float *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
+                          float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    return components_impl<float>(X, n, m, lambda, ncomp, out_v, out_obj, out_jstar, workspace,
+                                  workspace_bytes, stream);
+}
+
+int l1line_components_f64(const double *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
+                          double *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
+                          size_t workspace_bytes, void *stream) {
+    return components_impl<double>(X, n, m, lambda, ncomp, out_v, out_obj, out_jstar, workspace,
+                                   workspace_bytes, stream);
+}
+
 int l1line_status(void *workspace, void *stream) {
     if (!workspace) return L1L_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);

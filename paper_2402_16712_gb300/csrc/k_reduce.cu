@@ -1,4 +1,6 @@
 // k_reduce.cu -- steps A5 (z_jhat) and A6 (argmin over jhat, gather of v*).
+#include <algorithm>
+
 #include "common.cuh"
 #include "launch.h"
 
@@ -85,6 +87,42 @@ cudaError_t launch_argmin(const double *z_all, const T *v_all, int64_t m, int64_
     launches++;
     return cudaGetLastError();
 }
+
+// Successive components: x'_ik = fl(x_ik - fl(v_k x_ijhat)) (no fused
+// multiply-add), with jhat and v the component just fitted (device values).
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+template <typename T>
+__global__ void k_deflate(const T *__restrict__ X, T *__restrict__ Y, int64_t n, int64_t m,
+                          const int32_t *__restrict__ jstar, const T *__restrict__ v) {
+    const int64_t j = *jstar;
+    const int64_t N = n * m;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / m, k = e - i * m;
+        Y[e] = j >= 0 ? sub_rn(X[e], mul_rn(v[k], X[i * m + j])) : X[e];
+    }
+}
+
+template <typename T>
+cudaError_t launch_deflate(const T *X, T *Y, int64_t n, int64_t m, const int32_t *jstar,
+                           const T *v, int num_sms, cudaStream_t st, int &launches) {
+    const int64_t N = n * m;
+    const int64_t blocks = std::min<int64_t>((N + 255) / 256, (int64_t)num_sms * 8);
+    k_deflate<T><<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, st>>>(X, Y, n, m, jstar, v);
+    launches++;
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_deflate<float>(const float *, float *, int64_t, int64_t,
+                                           const int32_t *, const float *, int, cudaStream_t,
+                                           int &);
+template cudaError_t launch_deflate<double>(const double *, double *, int64_t, int64_t,
+                                            const int32_t *, const double *, int, cudaStream_t,
+                                            int &);
 
 template cudaError_t launch_argmin<float>(const double *, const float *, int64_t, int64_t,
                                           const int32_t *, int64_t, float *, double *, int32_t *,

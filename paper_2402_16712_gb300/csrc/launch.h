@@ -61,6 +61,11 @@ cudaError_t launch_argmin(const double *z_all, const T *v_all, int64_t m, int64_
                           const int32_t *jlist, int64_t nj, T *out_v, double *out_obj,
                           int32_t *out_jstar, cudaStream_t st, int &launches);
 
+// Successive components: Y = X - x_jhat v^T, elementwise, rounded per operation.
+template <typename T>
+cudaError_t launch_deflate(const T *X, T *Y, int64_t n, int64_t m, const int32_t *jstar,
+                           const T *v, int num_sms, cudaStream_t st, int &launches);
+
 // ---- learned jhat proposer (k_propose.cu) ----
 constexpr int MLP_TILE = 64;  // samples per CTA of the network kernels
 size_t mlp_smem_bytes();

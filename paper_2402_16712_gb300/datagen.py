@@ -150,6 +150,30 @@ def planted_torch(spec: Planted, device):
     return X.to(dt).contiguous(), v, rows
 
 
+def comparison(seed, n_outliers, n=100, m=100, dtype="float64"):
+    """The paper's comparison-experiment data (Section "Comparison to
+    Competing Methods"): v with coordinates ~ U(-10, 10) scaled to unit l2
+    norm; each regular point alpha_i v + Laplace(0, 10) noise with alpha_i ~
+    U(-100, 100); n_outliers seeded rows are outliers whose first five
+    coordinates are ~ U(50, 100), the others 0, plus Laplace(0, 1) noise.
+    Returns (X, v, outlier_rows)."""
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(-10.0, 10.0, size=m)
+    v /= np.sqrt((v * v).sum())
+    alpha = rng.uniform(-100.0, 100.0, size=n)
+    X = np.outer(alpha, v) + rng.laplace(0.0, 10.0, size=(n, m))
+    rows = np.sort(rng.choice(n, size=n_outliers, replace=False))
+    out = np.zeros((n_outliers, m))
+    out[:, :5] = rng.uniform(50.0, 100.0, size=(n_outliers, 5))
+    X[rows] = out + rng.laplace(0.0, 1.0, size=(n_outliers, m))
+    return np.ascontiguousarray(X.astype(dtype)), v, rows
+
+
+def comparison_suite(dtype="float64"):
+    """The 30 comparison datasets: five seeds for each outlier count 1..6."""
+    return [comparison(1000 * c + s, c, dtype=dtype)[0] for c in range(1, 7) for s in range(5)]
+
+
 # ---------------------------------------------------------------------------
 # Adversarial inputs for parity tests.
 # ---------------------------------------------------------------------------

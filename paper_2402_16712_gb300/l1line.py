@@ -66,6 +66,11 @@ SIGNATURES = {
                                       _I64, _P, _SZ, _P]),
     "l1line_solution_path_f64": (_I, [_I64, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P,
                                       _I64, _P, _SZ, _P]),
+    "l1line_components_workspace_bytes": (_SZ, [_I, _I64, _I64]),
+    "l1line_components_f32": (_I, [_P, _I64, _I64, ctypes.c_double, _I64, _P, _P, _P, _P, _SZ,
+                                   _P]),
+    "l1line_components_f64": (_I, [_P, _I64, _I64, ctypes.c_double, _I64, _P, _P, _P, _P, _SZ,
+                                   _P]),
     "l1line_set_tuning": (_I, [_P]),
     "l1line_plan": (_I, [_I, _I64, _I64, _I64, _P]),
 }
@@ -419,6 +424,27 @@ def solution_path(X, cap: int = 4096, stream=None):
     if c > cap:
         return solution_path(X, cap=c, stream=stream)
     return start[:c].cpu(), jh[:c].cpu(), I[:c].cpu(), S[:c].cpu(), vs[:c].cpu()
+
+
+def components(X, lam: float, ncomp: int, workspace: Optional[Workspace] = None, stream=None):
+    """ncomp successive components at one lambda: v [ncomp, m], obj [ncomp],
+    jstar [ncomp] (CUDA), workspace."""
+    import torch
+    _check_x(X)
+    n, m = X.shape
+    if workspace is None:
+        nb = int(load().l1line_components_workspace_bytes(_dt(X.dtype), n, m))
+        if nb == 0:
+            raise ValueError("bad shape for the components workspace")
+        workspace = Workspace(nb, X.device)
+    v = torch.empty((ncomp, m), dtype=X.dtype, device=X.device)
+    obj = torch.empty(ncomp, dtype=torch.float64, device=X.device)
+    js = torch.empty(ncomp, dtype=torch.int32, device=X.device)
+    f = load().l1line_components_f32 if X.dtype == torch.float32 else load().l1line_components_f64
+    _check(f(X.data_ptr(), n, m, float(lam), int(ncomp), v.data_ptr(), obj.data_ptr(),
+             js.data_ptr(), ctypes.c_void_p(workspace.ptr), workspace.nbytes, _stream_ptr(stream)),
+           "l1line_components")
+    return v, obj, js, workspace
 
 
 class Tuning(ctypes.Structure):

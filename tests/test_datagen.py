@@ -63,3 +63,20 @@ def test_proposer_spec_ranges():
         assert 1 <= s.nnz <= max(1, s.m // 10) and 0.0 <= s.outlier_frac <= 0.2
     s = datagen.proposer_spec(datagen.PROPOSER_HELDOUT_SEED0, n=5000, m=1000)
     assert (s.n, s.m) == (5000, 1000)
+
+
+def test_comparison_workload_distribution():
+    X, v, rows = datagen.comparison(7, 4, n=400, m=60)
+    assert abs(np.linalg.norm(v) - 1.0) < 1e-12 and np.all(np.abs(v) <= 1.0)
+    assert rows.size == 4
+    out = X[rows]
+    assert np.all((out[:, :5] > 40) & (out[:, :5] < 110))
+    assert np.abs(out[:, 5:]).mean() < 2.0  # Laplace(0, 1) noise only
+    clean = np.setdiff1d(np.arange(400), rows)
+    # projection on v ~ U(-100, 100); residual noise Laplace(0, 10): mean |e| = 10
+    Y = X[clean]
+    alpha = Y @ v
+    assert abs(alpha.std() - 200 / np.sqrt(12)) < 12
+    e = Y - np.outer(alpha, v)
+    assert abs(np.abs(e).mean() - 10.0) < 1.0
+    assert len(datagen.comparison_suite()) == 30

@@ -88,3 +88,14 @@ def test_batched_graph_replay():
         assert torch.equal(j0, j1) and torch.equal(v0, v1) and torch.equal(o0, o1)
     Xs2 = [X.cpu().numpy() for X in Xd]
     _check(Xs2, lams, bat.results(), "graph replay")
+
+
+def test_comparison_suite_batched():
+    # the paper's comparison experiment data (30 datasets of 100 x 100), a
+    # sparsity sweep of 8 lambdas each, in one batched call
+    Xs = datagen.comparison_suite("float64")
+    lams = [np.array([0.0, 5.0, 20.0, 50.0, 100.0, 200.0, 400.0, 800.0])] * len(Xs)
+    bat = l1line.Batched([torch.from_numpy(X).cuda() for X in Xs], [l.copy() for l in lams])
+    bat.run()
+    assert bat.status() == l1line.OK
+    _check(Xs, lams, bat.results(), "comparison suite")
