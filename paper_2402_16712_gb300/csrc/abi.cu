@@ -43,7 +43,7 @@ struct Layout {
 bool make_layout(int dtype, int64_t n, int64_t m, int64_t nl, Layout &L) {
     if (n < 1 || m < 1 || nl < 1) return false;
     const int64_t es = dtype == L1L_DTYPE_F32 ? 4 : 8;
-    const int64_t ldn = (n + 31) & ~int64_t(31);
+    const int64_t ldn = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
     int64_t mm, pairs, xt, chunk_pairs;
     if (!mul_ok(m, m, mm) || !mul_ok(mm, nl, pairs) || !mul_ok(m, ldn, xt)) return false;
     const int64_t nlc = nl < MAX_LAMBDA_PER_LAUNCH ? nl : MAX_LAMBDA_PER_LAUNCH;
@@ -797,7 +797,7 @@ int batch_shape(int dtype, int64_t batch, const int64_t *ns, const int64_t *ms,
         const int64_t nl = loff[b + 1] - loff[b];
         if (ns[b] < 1 || ms[b] < 1 || nl < 1) return L1L_ERR_ARG;
         if (ns[b] > maxr || ms[b] > (1 << 20)) return L1L_ERR_UNSUPPORTED;
-        const int64_t ldn = (ns[b] + 31) & ~int64_t(31);
+        const int64_t ldn = (ns[b] + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
         units += ms[b];
         ztasks += nl * ms[b];
         pairs += nl * ms[b] * ms[b];
@@ -858,7 +858,7 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
     for (int64_t b = 0; b < batch; ++b) pairs += (loff[b + 1] - loff[b]) * ms[b] * ms[b];
     off += al256((size_t)pairs * sizeof(SlowEntry));
     bd->count = (int32_t)batch;
-    bd->lay_npad = (int32_t)((sh.max_n + 31) & ~int64_t(31));
+    bd->lay_npad = (int32_t)((sh.max_n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1));
     bd->cap = plan.cap;
     bd->force_exact = (flags & L1L_FLAG_FORCE_EXACT) ? 1 : 0;
     bd->d0 = plan.d0;
@@ -866,7 +866,7 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
     for (int64_t p = 0; p < batch; ++p) {
         const int b = sh.order[(size_t)p];
         const int64_t n = ns[b], m = ms[b], nl = loff[b + 1] - loff[b];
-        const int64_t ldn = (n + 31) & ~int64_t(31);
+        const int64_t ldn = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
         BatchInst<T> &in = bd->inst[p];
         in.X = Xs[b];
         in.ws_off = (int64_t)off;

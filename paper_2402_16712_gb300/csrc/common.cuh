@@ -241,6 +241,12 @@ constexpr int D0_DEFAULT = 4;
 
 constexpr int MAX_LAMBDA_PER_LAUNCH = 256;
 
+// Rows of the staged column-major copy (and of the pair kernel's shared
+// column arrays) are padded with zeros to a multiple of ROW_PAD, so that the
+// selection's unrolled passes (4 loads of 32 rows per lane group) never need
+// a bound check: a padding row has a zero reciprocal and is not a valid row.
+constexpr int ROW_PAD = 128;
+
 // ---------------------------------------------------------------------------
 // A batch of independent instances, described entirely by value so that the
 // launches can be captured in a CUDA graph without host-memory copies.

@@ -72,7 +72,8 @@ __global__ void __launch_bounds__(256, 3)
         if (threadIdx.x == 0) atomicOr(a.status, ST_BADINDEX);
         return;
     }
-    pairs_unit<T, MULTI>(a, lv, t0, nlc, (int)j, k0, k1, cap, ((int)a.n + 31) & ~31, smem, s_dec);
+    pairs_unit<T, MULTI>(a, lv, t0, nlc, (int)j, k0, k1, cap,
+                         ((int)a.n + ROW_PAD - 1) & ~(ROW_PAD - 1), smem, s_dec);
 }
 
 // Candidate slots per warp (a multiple of 32: 32 lanes x quota).  About 40% of
@@ -84,17 +85,19 @@ template <typename T> static int cap_for(int64_t npad) {
 
 template <typename T> int64_t max_rows_pairs() {
     const size_t budget = 227 * 1024;
-    int64_t n = 32;
-    while (n + 32 <= (int64_t)ROW_MASK + 1 &&
-           PairSmem<T>::col_bytes(n + 32) + PairSmem<T>::warp_bytes(cap_for<T>(n + 32)) <= budget)
-        n += 32;
+    int64_t n = ROW_PAD;
+    while (n + ROW_PAD <= (int64_t)ROW_MASK + 1 &&
+           PairSmem<T>::col_bytes(n + ROW_PAD) +
+                   PairSmem<T>::warp_bytes(cap_for<T>(n + ROW_PAD)) <=
+               budget)
+        n += ROW_PAD;
     return n;
 }
 
 template <typename T>
 PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune) {
     PairPlan p{0, 0, 0, 0, 0, 0, 0};
-    const int64_t npad = (n + 31) & ~int64_t(31);
+    const int64_t npad = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
     if (n > max_rows_pairs<T>()) return p;
     const size_t cb = PairSmem<T>::col_bytes(npad);
     const int d0 = tune.d0 > 0 ? tune.d0 : D0_DEFAULT;

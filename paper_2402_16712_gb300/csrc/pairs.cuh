@@ -248,7 +248,6 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     using A = Approx<T>;
     constexpr uint32_t G = A::G;
     const unsigned FULL = 0xFFFFFFFFu;
-    const int npad_m1 = ((n + 31) & ~31) - 1;
     const float Qf = (float)dc.Q;
     const float hneg0 = 0.5f * (Qf + (float)dc.Lf), hpos0 = 0.5f * (Qf - (float)dc.Lc);
 
@@ -373,40 +372,36 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         // rows are visited in batches of 4 per lane; the global loads of the next
         // batch are issued before the current one is classified, so the L2
         // latency overlaps the work
+        // U * 32 = ROW_PAD rows per batch: every index below the padded row
+        // count is readable and padding rows (reciprocal 0) are not valid
         constexpr int U = 4;
+        static_assert(U * 32 == ROW_PAD, "one batch = one row pad");
         float an[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int i = u * 32 + lane;
-            an[u] = i < n ? xf[i] : 0.0f;
-        }
+        for (int u = 0; u < U; ++u) an[u] = xf[u * 32 + lane];
         for (int i0 = 0; i0 < n; i0 += 32 * U) {
             float ac[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) ac[u] = an[u];
             if (i0 + 32 * U < n) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int i = i0 + 32 * U + u * 32 + lane;
-                    an[u] = i < n ? xf[i] : 0.0f;
-                }
+                for (int u = 0; u < U; ++u) an[u] = xf[i0 + 32 * U + u * 32 + lane];
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                // branch-free; rows past n are clamped to a readable slot and masked
+                // branch-free
                 const int i = i0 + u * 32 + lane;
-                const int ic = min(i, npad_m1);
-                const float iv = inv[ic];
+                const float iv = inv[i];
                 const uint32_t kk = akey(__fmul_rn(ac[u], iv));
-                const bool valid = i < n && iv != 0.0f;
+                const bool valid = iv != 0.0f;
                 const bool below = valid && kk < bt;
                 const bool cand = valid && !below && kk <= at;
-                const int64_t q = colq[ic];
+                const int64_t q = colq[i];
                 Sb += below ? q : 0;
                 // speculative store: the slot is only kept when cnt advances
                 if (cnt < qt) {
                     lk[cnt * 32 + lane] = kk;
-                    li[cnt * 32 + lane] = (uint16_t)ic;
+                    li[cnt * 32 + lane] = (uint16_t)i;
                 }
                 cnt += cand ? 1 : 0;
             }
@@ -581,19 +576,26 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         fq = 0;
     }
     __syncwarp();
-    warp_sort32(fk, fq, lane);
-    const int64_t P = warp_scan_add(fq, lane);
-    const K nxt = __shfl_down_sync(FULL, fk, 1);
-    const bool last = (lane == 31) || (nxt != fk);
-    int r = -2;
-    if (last && fk != Tr::NONE) r = dc.cond(L + P, fk >= Tr::KEY0);
-    const unsigned okm = __ballot_sync(FULL, r == 1);
-    const unsigned unm = __ballot_sync(FULL, r == -1);
-    const unsigned any = okm | unm;
-    if (!any) return SEL_INTERNAL;
-    const int first = __ffs(any) - 1;
-    if ((unm >> first) & 1u) return SEL_SLOW_BAND;
-    tstar = __shfl_sync(FULL, fk, first);
+    // Rank form of "sort, prefix-sum, take the first key that passes": each
+    // candidate sums the weight of the candidates whose key is <= its own
+    // (equal keys get equal sums), tests it, and the smallest key that passes
+    // (or cannot be settled) is the answer.  A few candidates remain here, so
+    // this costs a few shuffles per candidate instead of a 32-lane sort.
+    const int nv = c + ((lo <= CK0 && CK0 <= hi) ? 1 : 0);
+    int64_t S = 0;
+    for (int u = 0; u < nv; ++u) {
+        const K ku = __shfl_sync(FULL, fk, u);
+        const int64_t qu = __shfl_sync(FULL, fq, u);
+        S += ku <= fk ? qu : 0;
+    }
+    int r = 0;
+    if (lane < nv) r = dc.cond(L + S, fk >= Tr::KEY0);
+    K kmin = r != 0 ? fk : Tr::NONE;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) kmin = min(kmin, __shfl_xor_sync(FULL, kmin, o));
+    if (kmin == Tr::NONE) return SEL_INTERNAL;
+    if (__any_sync(FULL, r == -1 && fk == kmin)) return SEL_SLOW_BAND;
+    tstar = kmin;
     return SEL_OK;
 }
 
