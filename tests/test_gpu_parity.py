@@ -165,3 +165,27 @@ def test_lambda_batch_unsorted_and_repeated(dtype):
     lams = rng.permutation(np.concatenate([np.logspace(-3, 1.5, 12), [0.0, 0.3, 0.3]]))
     _, _, ref = check_scan(X, lams, where="unsorted lambdas")
     check_fit(X, lams, ref, where="unsorted lambdas")
+
+
+@pytest.mark.parametrize("dtype", DT)
+@pytest.mark.parametrize("n", [127, 128, 129, 255, 385])
+def test_row_padding_boundaries(dtype, n):
+    # the staged rows are padded to a multiple of 128; counts around it
+    X, _, _ = datagen.planted(datagen.Planted(n, 11, 3, 0.1, 0.1, 5.0, n, np.dtype(dtype).name))
+    _, _, ref = check_scan(X, [0.0, 0.4, 3.0], where=f"n={n}")
+    check_fit(X, [0.0, 0.4, 3.0], ref, where=f"n={n}")
+
+
+@pytest.mark.parametrize("dtype", DT)
+def test_largest_supported_row_count(dtype):
+    # n at the pair kernel's limit (shared memory), a few columns: every pair
+    # against the oracle, and one row more is refused before any launch
+    n = l1line.max_rows(dtype)
+    X, _, _ = datagen.planted(datagen.Planted(n, 5, 2, 0.1, 0.1, 5.0, 77, np.dtype(dtype).name))
+    _, _, ref = check_scan(X, [0.0, 0.25], where=f"n=max={n}")
+    check_fit(X, [0.0, 0.25], ref, where=f"n=max={n}")
+    Xd = torch.zeros((n + 1, 3), dtype=torch.float32 if dtype == np.float32 else torch.float64,
+                     device="cuda")
+    with pytest.raises(l1line.L1LineError) as e:
+        l1line.fit(Xd, [0.1], workspace=l1line.Workspace(1 << 20))
+    assert e.value.code in (l1line.ERR_UNSUPPORTED, l1line.ERR_WORKSPACE)
