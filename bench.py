@@ -487,7 +487,8 @@ def measure_extras(dev, stream, flush):
     pairs = int(sum(int(Xb.shape[1]) * (int(Xb.shape[1]) - 1) for Xb, _ in batch))
     out["uneven_batch"] = {
         "workload": "256 float32 instances, n~U[100,5000], m~U[10,500], lambda=0.2, one "
-                    "persistent pair launch, CUDA graph replay (inputs 658 MB > L2)",
+                    "persistent pair launch per size class, CUDA graph replay (inputs 658 MB "
+                    "> L2)",
         "ms_per_step": ms, "fits_per_s": len(batch) / (ms * 1e-3),
         "pairs_per_s": pairs / (ms * 1e-3), "gpu_launches_per_step": launches,
         "tuning": btune}

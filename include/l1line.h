@@ -410,6 +410,13 @@ int l1line_last_launch_count(void);
  *   d0           half-width, in positions of the 64 weight-proportional
  *                samples of column jhat, of the first bracket around the
  *                weighted median, 1..24 (planner: 6)
+ *   batch_classes  size classes of a batched call, 1..3: the instances,
+ *                ordered by n, are cut into that many runs (where the
+ *                planner's occupancy model places the cuts), each run
+ *                scored by its own pair launch with shared memory laid out
+ *                for its largest n (planner: two classes when the model
+ *                puts them at least 5% below one, else one; l1line_plan
+ *                reports 0)
  * l1line_set_tuning applies to the later calls of the calling thread (NULL
  * restores the planner); a tuning whose candidate lists do not fit shared
  * memory makes those calls return L1L_ERR_UNSUPPORTED.  l1line_plan reports
@@ -421,6 +428,7 @@ typedef struct l1line_tuning {
     int32_t ctas_per_sm;
     int32_t kchunk;
     int32_t d0;
+    int32_t batch_classes;
 } l1line_tuning;
 int l1line_set_tuning(const l1line_tuning *t);
 int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out);

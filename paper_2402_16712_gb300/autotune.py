@@ -68,13 +68,16 @@ def store(k: str, tuning: dict, ms: float, path: Optional[str] = None) -> None:
         os.replace(tmp, p)
 
 
-def candidates(base: dict, kchunk: bool = True):
+def candidates(base: dict, kchunk: bool = True, classes: bool = False):
     """Coordinate sweeps around the planner's plan `base` (l1line.plan):
-    k per CTA (unless kchunk is False), then the bracket width, then warps x
-    CTAs per SM."""
+    k per CTA (unless kchunk is False), the number of size classes of a
+    batched call (if classes), then the bracket width, then warps x CTAs per
+    SM."""
     kc = max(1, base["kchunk"])
     for div in ((2, 3, 4, 6) if kchunk else ()):
         yield {"kchunk": max(1, -(-kc // div))}
+    for k in ((1, 2, 3) if classes else ()):
+        yield {"batch_classes": k}
     for d0 in (3, 4, 5, 7, 8, 10):
         yield {"d0": d0}
     for warps, ctas in ((8, 2), (6, 3), (4, 3), (4, 2), (8, 1)):
@@ -97,7 +100,7 @@ def _time(run: Callable[[], None], reps: int, flush) -> float:
 
 
 def tune(run: Callable[[], None], dtype, n: int, m: int, nj: Optional[int] = None, reps: int = 3,
-         flush=None, log=None, kchunk: bool = True):
+         flush=None, log=None, kchunk: bool = True, classes: bool = False):
     """Time `run` (a call on the current stream) under the planner's plan and
     the candidate tunings; returns (best tuning dict, its ms, table).  Each
     sweep keeps the best value found so far and varies one knob."""
@@ -105,7 +108,7 @@ def tune(run: Callable[[], None], dtype, n: int, m: int, nj: Optional[int] = Non
     base = l1line.plan(dtype, n, m, nj)
     best, best_ms = {}, _time(run, reps, flush)
     table = [({}, best_ms)]
-    for cand in candidates(base, kchunk):
+    for cand in candidates(base, kchunk, classes):
         t = dict(best)
         t.update(cand)
         try:
@@ -132,8 +135,10 @@ def apply(dtype, n: int, m: int, nl: int = 1, kind: str = "fit", run=None, nj=No
     k = key(dtype, n, m, nl, kind)
     hit = load_cache(path).get(k)
     if hit is None and run is not None:
-        # a batched call gives every CTA a whole column: k per CTA is not a knob
-        t, ms, _ = tune(run, dtype, n, m, nj=nj, flush=flush, log=log, kchunk=kind != "batch")
+        # a batched call gives every CTA a whole column: k per CTA is not a
+        # knob, the number of size classes is
+        t, ms, _ = tune(run, dtype, n, m, nj=nj, flush=flush, log=log, kchunk=kind != "batch",
+                        classes=kind == "batch")
         store(k, t, ms, path)
         hit = {"tuning": t}
     t = hit["tuning"] if hit else {}

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <memory>
 #include <mutex>
 #include <numeric>
@@ -735,12 +736,14 @@ int l1line_set_tuning(const l1line_tuning *t) {
         return L1L_OK;
     }
     if (t->warps < 0 || t->warps > 8 || t->ctas_per_sm < 0 || t->ctas_per_sm > 3 ||
-        t->kchunk < 0 || t->d0 < 0 || t->d0 > 24)
+        t->kchunk < 0 || t->d0 < 0 || t->d0 > 24 || t->batch_classes < 0 ||
+        t->batch_classes > MAX_BATCH_CLASSES)
         return L1L_ERR_ARG;
     g_tune.warps = t->warps;
     g_tune.ctas = t->ctas_per_sm;
     g_tune.kchunk = t->kchunk;
     g_tune.d0 = t->d0;
+    g_tune.batch_classes = t->batch_classes;
     return L1L_OK;
 }
 
@@ -756,6 +759,7 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
     out->ctas_per_sm = p.ctas;
     out->kchunk = p.kchunk;
     out->d0 = p.d0;
+    out->batch_classes = g_tune.batch_classes;
     return L1L_OK;
 }
 
@@ -777,11 +781,78 @@ int l1line_profile_events(void *start, void *stop) {
 namespace {
 
 struct BatchShape {
-    std::vector<int> order;  // processing order (largest work first) -> caller index
+    std::vector<int> order;  // processing order (size class, then largest work first) -> caller index
     size_t ws_total = 0;
     int64_t max_n = 0;
     bool multi = false;
 };
+
+// Splits the batch into at most MAX_BATCH_CLASSES size classes by n, each run
+// as its own persistent pair launch with shared memory laid out for the
+// class's largest n: a few large instances otherwise set the occupancy of
+// every small one.  Cost model: a class takes (its pair-rows, the sum of
+// n m^2 nl) / (resident warps of its plan).  Classes are runs of the instances
+// ordered by n (cuts only where n changes); the best split into k classes is
+// found by dynamic programming for each k.  Unless the tuning fixes k, the
+// planner takes two classes when the model puts them at least 5% below one.  Reorders `order`
+// (stably, so largest work first within a class) and returns the instance
+// count of each class, largest n first.
+template <typename T>
+std::vector<int64_t> batch_classes(int64_t batch, const int64_t *ns, const int64_t *ms,
+                                   const int64_t *loff, int sms, const Tune &tb,
+                                   std::vector<int> &order) {
+    const size_t B = (size_t)batch;
+    std::vector<int> byn(order);
+    std::stable_sort(byn.begin(), byn.end(), [&](int x, int y) { return ns[x] > ns[y]; });
+    std::vector<double> S(B + 1, 0.0), rate(B, 0.0);
+    for (size_t p = 0; p < B; ++p) {
+        const int b = byn[p];
+        S[p + 1] = S[p] + (double)ns[b] * ms[b] * ms[b] * (loff[b + 1] - loff[b]);
+        if (p == 0 || ns[b] != ns[byn[p - 1]]) {
+            const PairPlan pl = plan_pairs<T>(ns[b], 1, sms, 1, tb);
+            rate[p] = (double)pl.warps * (double)pl.ctas;  // 0 marks no cut here
+        }
+    }
+    // g[k][p]: the least modelled time of instances [p, B) in k + 1 classes
+    // starting at p; nxt[k][p]: where the second of them starts.
+    const double INF = std::numeric_limits<double>::infinity();
+    std::vector<std::vector<double>> g(MAX_BATCH_CLASSES, std::vector<double>(B + 1, INF));
+    std::vector<std::vector<size_t>> nxt(MAX_BATCH_CLASSES, std::vector<size_t>(B + 1, B));
+    for (size_t p = 0; p < B; ++p)
+        if (rate[p] > 0.0) g[0][p] = (S[B] - S[p]) / rate[p];
+    for (int k = 1; k < MAX_BATCH_CLASSES; ++k)
+        for (size_t p = 0; p < B; ++p) {
+            if (rate[p] <= 0.0) continue;
+            for (size_t q = p + 1; q < B; ++q) {
+                if (g[k - 1][q] == INF) continue;
+                const double t = (S[q] - S[p]) / rate[p] + g[k - 1][q];
+                if (t < g[k][p]) {
+                    g[k][p] = t;
+                    nxt[k][p] = q;
+                }
+            }
+        }
+    int k = 0;
+    if (tb.batch_classes > 0) {
+        for (int kk = tb.batch_classes - 1; kk >= 0 && k == 0; --kk)
+            if (g[kk][0] < INF) k = kk;  // fewer when n takes fewer distinct values
+    } else {
+        // the planner stops at two: a third class measured slower than the
+        // model predicts (each class's launch ends on its own tail)
+        if (g[1][0] < 0.95 * g[0][0]) k = 1;
+    }
+    std::vector<int64_t> counts;
+    std::vector<int> cls((size_t)batch, 0);
+    for (size_t p = 0; k >= 0; --k) {
+        const size_t q = k > 0 ? nxt[k][p] : B;
+        for (size_t r = p; r < q; ++r) cls[(size_t)byn[r]] = (int)counts.size();
+        counts.push_back((int64_t)(q - p));
+        p = q;
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return cls[(size_t)x] < cls[(size_t)y]; });
+    return counts;
+}
 
 // Validates the shapes and lambda offsets; fills `sh`.  Returns an l1l_status.
 int batch_shape(int dtype, int64_t batch, const int64_t *ns, const int64_t *ms,
@@ -838,8 +909,22 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
     if (sms <= 0) return L1L_ERR_CUDA;
     Tune tb = g_tune;
     tb.kchunk = 0;  // the persistent kernel's unit is a whole column jhat
-    const PairPlan plan = plan_pairs<T>(sh.max_n, 1, sms, 1, tb);
-    if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
+    // the processing order holds the size classes one after another
+    const std::vector<int64_t> counts = batch_classes<T>(batch, ns, ms, loff, sms, tb, sh.order);
+    BatchClass cls[MAX_BATCH_CLASSES];
+    int nclasses = 0;
+    for (int64_t p0 = 0; p0 < batch;) {
+        const int64_t p1 = p0 + counts[(size_t)nclasses];
+        int64_t mx = 0;
+        for (int64_t p = p0; p < p1; ++p) mx = std::max(mx, ns[sh.order[(size_t)p]]);
+        BatchClass &c = cls[nclasses++];
+        c.plan = plan_pairs<T>(mx, 1, sms, 1, tb);
+        if (c.plan.warps == 0) return L1L_ERR_UNSUPPORTED;
+        c.lay_npad = (int)((mx + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1));
+        c.u0 = p0;  // instance range for now; converted to units below
+        c.u1 = p1;
+        p0 = p1;
+    }
 
     std::unique_ptr<BatchDesc<T>> bd(new BatchDesc<T>());
     std::memset(bd.get(), 0, sizeof(BatchDesc<T>));
@@ -858,10 +943,8 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
     for (int64_t b = 0; b < batch; ++b) pairs += (loff[b + 1] - loff[b]) * ms[b] * ms[b];
     off += al256((size_t)pairs * sizeof(SlowEntry));
     bd->count = (int32_t)batch;
-    bd->lay_npad = (int32_t)((sh.max_n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1));
-    bd->cap = plan.cap;
     bd->force_exact = (flags & L1L_FLAG_FORCE_EXACT) ? 1 : 0;
-    bd->d0 = plan.d0;
+    bd->d0 = cls[0].plan.d0;
     int64_t units = 0, tiles = 0, ztasks = 0, lams = 0;
     for (int64_t p = 0; p < batch; ++p) {
         const int b = sh.order[(size_t)p];
@@ -904,9 +987,14 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
     bd->tiles = (int32_t)tiles;
     bd->ztasks = (int32_t)ztasks;
     bd->lams = (int32_t)lams;
+    for (int c = 0; c < nclasses; ++c) {
+        cls[c].u0 = bd->unit_begin[cls[c].u0];
+        cls[c].u1 = bd->unit_begin[cls[c].u1];
+    }
     int launches = 0;
-    if (launch_batch<T>(*bd, static_cast<unsigned char *>(ws), out_v, out_obj, out_jstar, plan,
-                        sh.multi, sms, static_cast<cudaStream_t>(stream), launches) != cudaSuccess)
+    if (launch_batch<T>(*bd, static_cast<unsigned char *>(ws), out_v, out_obj, out_jstar, cls,
+                        nclasses, sh.multi, sms, static_cast<cudaStream_t>(stream),
+                        launches) != cudaSuccess)
         return L1L_ERR_CUDA;
     g_last_launches = launches;
     return L1L_OK;

@@ -274,8 +274,6 @@ template <typename T> struct BatchDesc {
     int64_t units;       // (instance, jhat) work units
     int32_t ztasks;      // (instance, lambda, jhat) objective sums
     int32_t lams;        // lambdas over all instances
-    int32_t lay_npad;    // shared-memory layout rows (largest n rounded up to 32)
-    int32_t cap;         // candidate slots per warp
     int32_t force_exact;
     int32_t d0;          // first-bracket half-width of the selection
     BatchInst<T> inst[MAX_BATCH];
@@ -309,7 +307,8 @@ __host__ __device__ inline InstLayout inst_layout(int64_t m, int64_t ldn, int64_
     L.total = o;
     return L;
 }
-// Batch-wide workspace head: status word, exact-path counter, unit counter.
+// Batch-wide workspace head: status word (@0), exact-path counter (@256), one
+// unit counter per size class (@512 + 8 c).
 constexpr size_t BATCH_HEAD = 768;
 struct LambdaPack {
     double lam[MAX_LAMBDA_PER_LAUNCH];

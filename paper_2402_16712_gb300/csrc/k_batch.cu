@@ -81,28 +81,29 @@ __global__ void __launch_bounds__(256) k_colprep_b(const __grid_constant__ Batch
     colprep_column<T>(Xt + (int64_t)j * in.ldn, ci + j, in.n);
 }
 
-// Persistent: every CTA loops, taking the next (instance, jhat) unit from the
-// counter; units are numbered largest instance first.  No CTA waits on
-// another.
+// Persistent: every CTA loops, taking the next (instance, jhat) unit of units
+// [u0, u1) (one size class of the batch) from that class's counter; units are
+// numbered largest instance first.  No CTA waits on another.
 template <typename T, bool MULTI>
 __global__ void __launch_bounds__(256, 3)
-    k_pairs_persist(const __grid_constant__ BatchDesc<T> bd, unsigned char *ws) {
+    k_pairs_persist(const __grid_constant__ BatchDesc<T> bd, unsigned char *ws, int64_t u0,
+                    int64_t u1, int slot, int lay_npad, int cap) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ Decide s_dec[NDEC];
     __shared__ long long s_unit;
-    unsigned long long *counter = reinterpret_cast<unsigned long long *>(ws + 512);
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(ws + 512) + slot;
     for (;;) {
         if (threadIdx.x == 0) s_unit = (long long)atomicAdd(counter, 1ull);
         __syncthreads();
-        const int64_t u = s_unit;
+        const int64_t u = u0 + s_unit;
         __syncthreads();
-        if (u >= bd.units) break;
+        if (u >= u1) break;
         const int b = find_inst<int64_t>(bd.unit_begin, bd.count, u);
         const BatchInst<T> &in = bd.inst[b];
         const ScanArgs<T> a = inst_args<T>(bd, b, ws);
         const LamView lv{bd.lam + bd.lam_begin[b], in.tl_min, in.tl_max};
-        pairs_unit<T, MULTI>(a, lv, 0, in.nl, (int)(u - bd.unit_begin[b]), 0, in.m, bd.cap,
-                             bd.lay_npad, smem, s_dec);
+        pairs_unit<T, MULTI>(a, lv, 0, in.nl, (int)(u - bd.unit_begin[b]), 0, in.m, cap,
+                             lay_npad, smem, s_dec);
     }
 }
 
@@ -185,34 +186,42 @@ __global__ void __launch_bounds__(256) k_argmin_b(const __grid_constant__ BatchD
 
 template <typename T>
 cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, double *out_obj,
-                         int32_t *out_jstar, const PairPlan &plan, bool multi, int num_sms,
-                         cudaStream_t st, int &launches) {
+                         int32_t *out_jstar, const BatchClass *classes, int nclasses, bool multi,
+                         int num_sms, cudaStream_t st, int &launches) {
     cudaError_t e = cudaMemsetAsync(ws, 0, BATCH_HEAD, st);  // status, exact counter, units
     if (e != cudaSuccess) return e;
     k_transpose_b<T><<<bd.tiles, dim3(32, 8), 0, st>>>(bd, ws);
     k_colprep_b<T><<<(unsigned)bd.units, 256, 0, st>>>(bd, ws);
     launches += 2;
     auto kern = multi ? k_pairs_persist<T, true> : k_pairs_persist<T, false>;
-    e = ensure_smem(reinterpret_cast<const void *>(kern), plan.smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = blocks_per_sm(reinterpret_cast<const void *>(kern), plan.warps * 32, plan.smem, &per_sm);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, bd.units);
-    kern<<<(unsigned)grid, plan.warps * 32, plan.smem, st>>>(bd, ws);
+    // one persistent launch per size class, each with shared memory for its largest n
+    for (int c = 0; c < nclasses; ++c) {
+        const BatchClass &bc = classes[c];
+        if (bc.u1 <= bc.u0) continue;
+        e = ensure_smem(reinterpret_cast<const void *>(kern), bc.plan.smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = blocks_per_sm(reinterpret_cast<const void *>(kern), bc.plan.warps * 32, bc.plan.smem,
+                          &per_sm);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, bc.u1 - bc.u0);
+        kern<<<(unsigned)grid, bc.plan.warps * 32, bc.plan.smem, st>>>(
+            bd, ws, bc.u0, bc.u1, c, bc.lay_npad, bc.plan.cap);
+        launches++;
+    }
     k_exact_b<T><<<num_sms * 2, 128, 0, st>>>(bd, ws);
     k_zreduce_b<T><<<bd.ztasks, 32, 0, st>>>(bd, ws);
     k_argmin_b<T><<<bd.lams, 256, 0, st>>>(bd, ws, out_v, out_obj, out_jstar);
-    launches += 4;
+    launches += 3;
     return cudaGetLastError();
 }
 
 template cudaError_t launch_batch<float>(const BatchDesc<float> &, unsigned char *, float *,
-                                         double *, int32_t *, const PairPlan &, bool, int,
+                                         double *, int32_t *, const BatchClass *, int, bool, int,
                                          cudaStream_t, int &);
 template cudaError_t launch_batch<double>(const BatchDesc<double> &, unsigned char *, double *,
-                                          double *, int32_t *, const PairPlan &, bool, int,
+                                          double *, int32_t *, const BatchClass *, int, bool, int,
                                           cudaStream_t, int &);
 
 }  // namespace l1l

@@ -34,7 +34,7 @@ struct PairPlan {
 };
 // Caller overrides of the planner (0 = the planner's choice).
 struct Tune {
-    int warps = 0, ctas = 0, kchunk = 0, d0 = 0;
+    int warps = 0, ctas = 0, kchunk = 0, d0 = 0, batch_classes = 0;
 };
 // nj: number of jhat scored (m for a full scan).
 template <typename T>
@@ -111,10 +111,20 @@ cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo 
                         int32_t *big, uint32_t *big_count, unsigned char *scratch,
                         uint32_t *status, int num_sms, cudaStream_t st, int &launches);
 
-// The batched fit: staging, one persistent pair kernel, exact path, sums, argmin.
+// A size class of a batch: units [u0, u1) run in one persistent launch whose
+// shared memory is laid out for the class's largest n.
+struct BatchClass {
+    int64_t u0, u1;
+    int lay_npad;
+    PairPlan plan;
+};
+constexpr int MAX_BATCH_CLASSES = 3;
+
+// The batched fit: staging, one persistent pair kernel per size class, exact
+// path, sums, argmin.
 template <typename T>
 cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, double *out_obj,
-                         int32_t *out_jstar, const PairPlan &plan, bool multi, int num_sms,
-                         cudaStream_t st, int &launches);
+                         int32_t *out_jstar, const BatchClass *classes, int nclasses, bool multi,
+                         int num_sms, cudaStream_t st, int &launches);
 
 }  // namespace l1l

@@ -450,7 +450,8 @@ def components(X, lam: float, ncomp: int, workspace: Optional[Workspace] = None,
 class Tuning(ctypes.Structure):
     """l1line_tuning: pair-kernel launch overrides (0 = the planner's choice)."""
     _fields_ = [("warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("kchunk", ctypes.c_int32), ("d0", ctypes.c_int32)]
+                ("kchunk", ctypes.c_int32), ("d0", ctypes.c_int32),
+                ("batch_classes", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -30,12 +30,18 @@ def test_candidates_vary_one_knob_group():
     c = list(autotune.candidates({"warps": 8, "ctas_per_sm": 3, "kchunk": 2000, "d0": 6}))
     assert {"kchunk": 1000} in c and {"d0": 4} in c and {"warps": 4, "ctas_per_sm": 3} in c
     assert all(len(x) <= 2 for x in c)
+    assert not any("batch_classes" in x for x in c)
+    cb = list(autotune.candidates({"warps": 8, "ctas_per_sm": 3, "kchunk": 0, "d0": 6},
+                                  kchunk=False, classes=True))
+    assert [x for x in cb if "batch_classes" in x] == [{"batch_classes": k} for k in (1, 2, 3)]
+    assert not any("kchunk" in x for x in cb)
 
 
 def test_tuning_argument_checks():
     __graft_entry__.build()
     l1line.load()
-    for bad in ({"warps": 9}, {"ctas_per_sm": 4}, {"kchunk": -1}, {"d0": 25}, {"warps": -1}):
+    for bad in ({"warps": 9}, {"ctas_per_sm": 4}, {"kchunk": -1}, {"d0": 25}, {"warps": -1},
+                {"batch_classes": 4}, {"batch_classes": -1}):
         with pytest.raises(l1line.L1LineError):
             l1line.set_tuning(bad)
     l1line.set_tuning({"warps": 4, "d0": 8})

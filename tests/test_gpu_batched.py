@@ -1,6 +1,7 @@
-"""Batched fit (one persistent pair launch over uneven instances): every
-instance's result against the oracle, under the parity bar of tests/_parity.py;
-graph capture and replay; degenerate instances."""
+"""Batched fit (one persistent pair launch per size class over uneven
+instances): every instance's result against the oracle, under the parity bar
+of tests/_parity.py; graph capture and replay; degenerate instances; every
+number of size classes."""
 import numpy as np
 import pytest
 import torch
@@ -99,3 +100,37 @@ def test_comparison_suite_batched():
     bat.run()
     assert bat.status() == l1line.OK
     _check(Xs, lams, bat.results(), "comparison suite")
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_size_classes_give_identical_results(dtype):
+    """Instances with n from 60 to 5000 (each shared-memory plan of the pair
+    kernel occurs) under every number of size classes: each run matches the
+    oracle and the runs agree bit for bit."""
+    rng = np.random.default_rng(77)
+    Xs, lams = [], []
+    for b, n in enumerate((5000, 60, 4700, 700, 3600, 1800, 2600, 130, 4100, 2200, 999, 3100)):
+        m = int(rng.integers(2, 20))
+        X, _, _ = datagen.planted(datagen.Planted(n, m, max(1, m // 5), 0.1, 0.15, 10.0,
+                                                  5000 + b, np.dtype(dtype).name))
+        Xs.append(X)
+        lams.append(np.array([0.0, 0.2, 1.5]))
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    runs = []
+    for k in (0, 1, 2, 3):
+        l1line.set_tuning({"batch_classes": k})
+        try:
+            bat = l1line.Batched(Xd, lams)
+            bat.run()
+            if k > 0:  # staging 2, one pair launch per class, exact path, sums, argmin
+                assert l1line.last_launch_count() == 5 + k
+            assert bat.status() == l1line.OK
+            runs.append([tuple(t.clone() for t in r) for r in bat.results()])
+        finally:
+            l1line.set_tuning(None)
+    _check(Xs, lams, runs[1], "batch_classes=1")
+    ib = torch.int32 if dtype == np.float32 else torch.int64
+    for k, r in enumerate(runs):
+        for b, (a, c) in enumerate(zip(runs[1], r)):
+            assert torch.equal(a[0].view(ib), c[0].view(ib)), (k, b)
+            assert torch.equal(a[1], c[1]) and torch.equal(a[2], c[2]), (k, b)
