@@ -235,13 +235,17 @@ __device__ __forceinline__ int hist_cross(const uint32_t *h, int nbins, uint32_t
 // j-th candidate sits at slot j*32 + l (bank l, so every access is free of bank
 // conflicts) and each lane counts its own candidates against a quota of
 // qt = cap/32 slots; only the final <= 31 candidates are gathered across the
-// warp.  Row indices carry a flag bit, EXACT: the stored key is exact.
+// warp.  Row indices carry a flag bit, EXACT: the stored key is exact.  The
+// candidate arrays, the histogram and the column arrays never overlap (hence
+// __restrict__), so the loops over the list below, unrolled by two, can issue
+// the shared-memory loads of one candidate before the atomics of the other.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf, const T *colb,
-                         const float *inv,
-                         const int64_t *colq, const uint16_t *samp, uint32_t *lk, uint16_t *li,
-                         uint32_t *hist, int qt, int n, int d0, const Decide &dc,
+__device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
+                         const T *__restrict__ colb, const float *__restrict__ inv,
+                         const int64_t *__restrict__ colq, const uint16_t *__restrict__ samp,
+                         uint32_t *__restrict__ lk, uint16_t *__restrict__ li,
+                         uint32_t *__restrict__ hist, int qt, int n, int d0, const Decide &dc,
                          typename Traits<T>::K &tstar, int lane) {
     using Tr = Traits<T>;
     using K = typename Tr::K;
@@ -423,6 +427,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         hist_zero(hist, lane);
         __syncwarp();
         int64_t Sb2 = 0;
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             uint32_t kk = lk[p];
@@ -467,6 +472,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         const uint32_t K1 = P1 + ((uint32_t)bs << sh);
         const uint32_t K2 = min(P2, K1 + bmask);
         int w = 0;
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             const uint32_t kk = lk[p];
@@ -494,6 +500,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         const int nbins = (int)(span >> sh) + 1;
         hist_zero(hist, lane);
         __syncwarp();
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             uint32_t kk = lk[p];
@@ -517,6 +524,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         const uint32_t K1 = lo + ((uint32_t)bs << sh);
         const uint32_t K2 = min(hi, K1 + bmask);
         int w = 0;
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const int p = j * 32 + lane;
             const uint32_t kk = lk[p];
@@ -540,6 +548,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     }
     if (c > 31) {  // one coarse key left, many rows: all exact keys equal?
         K kmin = Tr::NONE, kmax = 0;
+#pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
             const int row = li[j * 32 + lane] & ROW_MASK;
             const K ke = Tr::key(Tr::div_rn(xk[row], colb[row]));
