@@ -146,6 +146,38 @@ template <typename V> __device__ __forceinline__ V warp_scan_add(V x, int lane) 
     return x;
 }
 
+// Residual over the padded rows: Xt and the staged column are zero past n, so
+// a padding row adds |0 - v 0| = 0.  Four rows per lane per step, the global
+// loads of the next step issued before this step is summed.
+template <typename T>
+__device__ __forceinline__ T warp_residual_pad(const T *__restrict__ xk, const T *__restrict__ xj,
+                                               int n, T v, int lane) {
+    constexpr int U = 4;
+    static_assert(U * 32 == ROW_PAD, "one step = one row pad");
+    const int np = (n + ROW_PAD - 1) & ~(ROW_PAD - 1);
+    T acc[U], an[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        acc[u] = T(0);
+        an[u] = xk[u * 32 + lane];
+    }
+    for (int i0 = 0; i0 < np; i0 += 32 * U) {
+        T ac[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) ac[u] = an[u];
+        if (i0 + 32 * U < np) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) an[u] = xk[i0 + 32 * U + u * 32 + lane];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) acc[u] += fabs(fma(-v, xj[i0 + u * 32 + lane], ac[u]));
+    }
+    T s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+    return s;
+}
+
 // Outcomes of select_v2.  Every code >= SEL_SLOW hands the pair to the exact
 // path; the code says why (kept in the slow list for diagnostics).
 enum {
@@ -670,7 +702,7 @@ __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int
         return;
     }
     const T v = Tr::value(ts);
-    const T res = warp_residual<T>(xk, colb, n, v, lane);
+    const T res = warp_residual_pad<T>(xk, colb, n, v, lane);
     if (lane == 0) {
         a.v_all[o] = v;
         a.s_all[o] = (double)res + lam * (double)fabs(v);
@@ -812,7 +844,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
         const K ts = __shfl_sync(FULL, fk, first);
         const T v = Tr::value(ts);
         if (ts != prev) {
-            prev_res = warp_residual<T>(xk, w.colb, n, v, lane);
+            prev_res = warp_residual_pad<T>(xk, w.colb, n, v, lane);
             prev = ts;
         }
         if (lane == 0) {
