@@ -506,10 +506,13 @@ def run_profile_case(args):
     X, lams, _ = datagen.paper_size(dt, n=args.n, m=args.m)
     Xd = torch.from_numpy(X).cuda()
     ws = l1line.Workspace.for_shape(Xd.dtype, args.n, args.m, 1)
+    if args.d0:
+        l1line.set_tuning({"d0": args.d0})
     for _ in range(args.fits):
         l1line.fit(Xd, lams, workspace=ws)
     rc = l1line.status(ws)
-    print(f"profile case n={args.n} m={args.m} {dt}: status={l1line.status_string(rc)}")
+    print(f"profile case n={args.n} m={args.m} {dt} d0={args.d0 or 'planner'}: "
+          f"plan={l1line.plan(Xd.dtype, args.n, args.m)} status={l1line.status_string(rc)}")
     return 0 if rc == l1line.OK else 1
 
 
@@ -528,6 +531,8 @@ def main():
     ap.add_argument("--m", type=int, default=N_COLS)
     ap.add_argument("--dtype", default="f32", choices=["f32", "f64"])
     ap.add_argument("--fits", type=int, default=2)
+    ap.add_argument("--d0", type=int, default=0,
+                    help="--profile-case: first-bracket half-width (0 = the planner's)")
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
