@@ -43,6 +43,13 @@ WORKLOAD = ("planted sparse line, n=2000 points x m=2000 coords, float32, 20-spa
 # residual fma + abs-add.  The ALU roofline divides by the SM issue rate.
 ALG_INSTR_PER_ELEM = 8
 SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+# Algorithmic bytes per (jhat, k) pair of the float32 pair kernel for its
+# memory ceilings: shared memory -- 16 bytes per row, the staged column's
+# reciprocal (4), weight (8) and value (4) read once each (as many bytes as a
+# 4-byte key and a 4-byte weight written once and read once); L2 -- column k
+# read once and column jhat once per CTA of T_k pairs, 4 n (1 + 1/T_k) bytes.
+# The peaks are measured in the same run by the library's bandwidth probes.
+SMEM_BYTES_PER_ROW = 16
 
 
 def _env_rank():
@@ -322,9 +329,8 @@ def run_gpu(args):
         return 0
 
     kms = statistics.mean(kern_ms)
-    instr = ALG_INSTR_PER_ELEM * pairs * n
-    peak = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = instr / (kms * 1e-3) / 1e12
+    plan = l1line.plan(torch.float32, n, m)
+    l2_gbs, smem_gbs = measure_ceilings(dev, stream)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
@@ -332,15 +338,12 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "n": n, "m": m, "lambda": float(lams[0]),
                    "pairs_per_fit": pairs, "parallelism": f"replicas x{world} (one instance per GPU)",
                    "l2": "flushed before every timed step (512 MiB write)",
-                   "tuning": {"applied": tuning, "plan": l1line.plan(torch.float32, n, m)}},
+                   "tuning": {"applied": tuning, "plan": plan}},
         "fits_per_s": world * args.steps / (tot_ms * 1e-3),
         "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT,
                 "tuning": tuning64},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinstr/s",
-                     "frac": achieved / peak, "traffic": _profile_traffic(),
-                     "kernel": "k_pairs<float,false>", "kernel_ms": kms,
-                     "basis": f"{ALG_INSTR_PER_ELEM} lane-instructions per (pair,row) element; "
-                              f"peak = {SMS} SMs x {LANES_PER_SM_CLK} lanes x {SM_MAX_MHZ:.0f} MHz"},
+        "roofline": roofline(n, pairs, kms, plan["kchunk"], l2_gbs, smem_gbs,
+                             _profile_traffic()),
         "e2e": {"value": pairs / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches_per_fit * args.steps,
@@ -354,6 +357,50 @@ def run_gpu(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def measure_ceilings(dev, stream):
+    """Measured L2 and shared-memory read bandwidth (GB/s, best of a few
+    probes): a 64 MB L2-resident buffer read 20 times; every SM reading its
+    shared memory conflict-free."""
+    import torch
+
+    from paper_2402_16712_gb300 import l1line
+    buf = torch.ones(64 << 20, dtype=torch.uint8, device=dev)
+    with torch.cuda.stream(stream):
+        l1line.probe_bandwidth(l1line.PROBE_L2, 2, buf, stream)
+        l2 = max(l1line.probe_bandwidth(l1line.PROBE_L2, 20, buf, stream) for _ in range(5))
+        l1line.probe_bandwidth(l1line.PROBE_SMEM, 16, None, stream)
+        sm = max(l1line.probe_bandwidth(l1line.PROBE_SMEM, 4000, None, stream) for _ in range(3))
+    return l2 / 1e9, sm / 1e9
+
+
+def roofline(n, pairs, kms, kchunk, l2_gbs, smem_gbs, traffic):
+    """The pair kernel against its three ceilings; the binding one (the fewest
+    pairs/s) is the headline roofline."""
+    pps = pairs / (kms * 1e-3)
+    alu_peak = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
+    per = {
+        "smem": (SMEM_BYTES_PER_ROW * n, smem_gbs * 1e9, 1e9, "GB/s",
+                 f"{SMEM_BYTES_PER_ROW} shared-memory bytes per (pair,row): staged 1/x_ijhat, "
+                 "q_i and x_ijhat read once each; peak = shared-memory read probe, this run"),
+        "l2": (4.0 * n * (1.0 + 1.0 / max(1, kchunk)), l2_gbs * 1e9, 1e9, "GB/s",
+               f"4 n (1 + 1/T_k) bytes per pair, T_k = {kchunk}; peak = L2 read probe "
+               "(64 MB resident buffer), this run"),
+        "alu": (ALG_INSTR_PER_ELEM * n, alu_peak * 1e12, 1e12, "Tinstr/s",
+                f"{ALG_INSTR_PER_ELEM} lane-instructions per (pair,row); peak = {SMS} SMs x "
+                f"{LANES_PER_SM_CLK} lanes x {SM_MAX_MHZ:.0f} MHz"),
+    }
+    ceilings = {}
+    for name, (work, peak, scale, unit, basis) in per.items():
+        ceilings[name] = {"achieved": pps * work / scale, "peak": peak / scale, "unit": unit,
+                          "frac": pps * work / peak, "ceiling_pairs_per_s": peak / work,
+                          "basis": basis}
+    bound = min(ceilings, key=lambda c: ceilings[c]["ceiling_pairs_per_s"])
+    c = ceilings[bound]
+    return {"bound": bound, "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
+            "frac": c["frac"], "traffic": traffic, "kernel": "k_pairs<float,false>",
+            "kernel_ms": kms, "basis": c["basis"], "ceilings": ceilings}
 
 
 def _replay_ms(g, stream, steps, flush=None):

@@ -441,6 +441,26 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
  * launches between them.  Pass NULLs to switch it off.  Returns L1L_OK. */
 int l1line_profile_events(void *start, void *stop);
 
+/*
+ * Bandwidth probes: the measured denominators of the pair kernel's L2 and
+ * shared-memory ceilings (the fit path never calls them).  Asynchronous on
+ * `stream`; the caller times the launch (CUDA events) and divides
+ * *bytes_read by the time.
+ *   L1L_PROBE_L2    reads `bytes` (>= 16) of the device buffer `buf`
+ *                   (16-byte aligned) `reps` times with 16-byte loads that
+ *                   bypass L1; size it well below the L2 so every pass after
+ *                   the first hits L2.  *bytes_read = reps * floor(bytes/16)*16.
+ *   L1L_PROBE_SMEM  4 CTAs of 512 threads per SM each read reps x 8
+ *                   conflict-free 16-byte shared-memory words; `buf` and
+ *                   `bytes` are ignored.
+ * `sink` is a 4-byte device word the kernels may increment (it keeps the
+ * loads live).  Errors: L1L_ERR_ARG (kind, reps < 1, NULL sink or bytes_read,
+ * L2 probe buffer NULL, unaligned or under 16 bytes), L1L_ERR_CUDA.
+ */
+enum { L1L_PROBE_L2 = 0, L1L_PROBE_SMEM = 1 };
+int l1line_probe(int kind, const void *buf, size_t bytes, int reps, void *sink, void *stream,
+                 double *bytes_read);
+
 #ifdef __cplusplus
 }
 #endif

@@ -19,7 +19,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libl1line.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_prep.cu", "k_pairs.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "k_propose.cu",
-           "k_path.cu", "k_solpath.cu", "abi.cu"]
+           "k_path.cu", "k_solpath.cu", "k_probe.cu", "abi.cu"]
 
 
 def nvcc() -> str:

@@ -763,6 +763,26 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
     return L1L_OK;
 }
 
+int l1line_probe(int kind, const void *buf, size_t bytes, int reps, void *sink, void *stream,
+                 double *bytes_read) {
+    g_last_launches = 0;
+    if (!sink || !bytes_read || reps < 1 || (reinterpret_cast<uintptr_t>(sink) & 3) != 0)
+        return L1L_ERR_ARG;
+    if (kind != L1L_PROBE_L2 && kind != L1L_PROBE_SMEM) return L1L_ERR_ARG;
+    if (kind == L1L_PROBE_L2 &&
+        (!buf || bytes < 16 || (reinterpret_cast<uintptr_t>(buf) & 15) != 0))
+        return L1L_ERR_ARG;
+    const int sms = num_sms();
+    if (sms <= 0) return L1L_ERR_CUDA;
+    int launches = 0;
+    if (launch_probe(kind == L1L_PROBE_L2 ? PROBE_L2 : PROBE_SMEM, buf, bytes, reps,
+                     static_cast<unsigned *>(sink), sms, static_cast<cudaStream_t>(stream),
+                     bytes_read, launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    g_last_launches = launches;
+    return L1L_OK;
+}
+
 int l1line_profile_events(void *start, void *stop) {
     if (start && stop) {
         g_ev_start = static_cast<cudaEvent_t>(start);

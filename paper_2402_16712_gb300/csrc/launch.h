@@ -127,4 +127,9 @@ cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, do
                          int32_t *out_jstar, const BatchClass *classes, int nclasses, bool multi,
                          int num_sms, cudaStream_t st, int &launches);
 
+// Bandwidth probes (k_probe.cu): L2 reads of a resident buffer, shared-memory reads.
+enum { PROBE_L2 = 0, PROBE_SMEM = 1 };
+cudaError_t launch_probe(int kind, const void *buf, size_t bytes, int reps, unsigned *sink,
+                         int num_sms, cudaStream_t st, double *bytes_read, int &launches);
+
 }  // namespace l1l

@@ -36,6 +36,7 @@ SIGNATURES = {
     "l1line_status_string": (ctypes.c_char_p, [_I]),
     "l1line_last_launch_count": (_I, []),
     "l1line_profile_events": (_I, [_P, _P]),
+    "l1line_probe": (_I, [_I, _P, _SZ, _I, _P, _P, _P]),
     "l1line_fit_noalloc_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P]),
     "l1line_batched_workspace_bytes": (_SZ, [_I, _I64, _P, _P, _P]),
     "l1line_fit_batched_f32": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
@@ -488,6 +489,29 @@ def profile_events(start=None, stop=None) -> None:
     else:
         load().l1line_profile_events(ctypes.c_void_p(start.cuda_event),
                                      ctypes.c_void_p(stop.cuda_event))
+
+
+PROBE_L2, PROBE_SMEM = 0, 1
+
+
+def probe_bandwidth(kind: int, reps: int, buf=None, stream=None) -> float:
+    """Run one bandwidth probe (`l1line_probe`) on `stream` and return bytes/s
+    from CUDA events around it.  kind PROBE_L2 reads the device tensor `buf`
+    `reps` times; PROBE_SMEM ignores `buf`."""
+    import torch
+    st = stream or torch.cuda.current_stream()
+    sink = torch.zeros(1, dtype=torch.int32, device=st.device)
+    nbytes = ctypes.c_double(0.0)
+    ptr = ctypes.c_void_p(buf.data_ptr()) if buf is not None else None
+    size = buf.numel() * buf.element_size() if buf is not None else 0
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    _check(load().l1line_probe(kind, ptr, size, reps, ctypes.c_void_p(sink.data_ptr()),
+                               ctypes.c_void_p(st.cuda_stream), ctypes.byref(nbytes)),
+           "l1line_probe")
+    b.record(st)
+    b.synchronize()
+    return nbytes.value / (a.elapsed_time(b) * 1e-3)
 
 
 class Batched:

@@ -154,6 +154,20 @@ def test_proposer_argument_errors(lib):
     assert lib.l1line_features_f32(p, 10, 5, None, None, P(1024), 1 << 30, None) == l1line.ERR_ARG
 
 
+def test_probe_argument_errors(lib):
+    P = ctypes.c_void_p
+    out = ctypes.c_double(0.0)
+    ref = ctypes.byref(out)
+    assert lib.l1line_probe(2, P(256), 1024, 1, P(256), None, ref) == l1line.ERR_ARG  # kind
+    assert lib.l1line_probe(l1line.PROBE_L2, P(256), 1024, 0, P(256), None, ref) == l1line.ERR_ARG
+    assert lib.l1line_probe(l1line.PROBE_L2, None, 1024, 1, P(256), None, ref) == l1line.ERR_ARG
+    assert lib.l1line_probe(l1line.PROBE_L2, P(264), 1024, 1, P(256), None, ref) == l1line.ERR_ARG
+    assert lib.l1line_probe(l1line.PROBE_L2, P(256), 8, 1, P(256), None, ref) == l1line.ERR_ARG
+    assert lib.l1line_probe(l1line.PROBE_SMEM, None, 0, 1, None, None, ref) == l1line.ERR_ARG
+    assert lib.l1line_probe(l1line.PROBE_SMEM, None, 0, 1, P(258), None, ref) == l1line.ERR_ARG
+    assert lib.l1line_probe(l1line.PROBE_SMEM, None, 0, 1, P(256), None, None) == l1line.ERR_ARG
+
+
 def test_committed_network_parameters():
     from paper_2402_16712_gb300 import proposer
     th = proposer.load_theta()
