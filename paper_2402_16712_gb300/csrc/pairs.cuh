@@ -74,7 +74,7 @@ constexpr int NSAMP = 64;   // weight-proportional sample rows per column
 constexpr int HIST_WORDS = 4 * 64;  // per-warp exact histogram (4 chunks x 64 bins)
 
 template <typename T> struct PairSmem {
-    // per CTA: x_ijhat (T), 1/x_ijhat (float, 0 marks x_ijhat == 0), q_i (int64),
+    // per CTA: x_ijhat (T), 1/x_ijhat (float, NaN marks x_ijhat == 0), q_i (int64),
     // the 64 sample rows (uint16)
     __host__ __device__ static size_t col_bytes(int64_t npad) {
         return al16(npad * sizeof(T)) + al16(npad * 4) + al16(npad * 8) + al16(NSAMP * 2);
@@ -339,14 +339,14 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
             const uint32_t bmask = (1u << sh) - 1u;
             const int nbins = (int)(span >> sh) + 1;
-            const uint32_t bt = sat_sub(P1, G), at = sat_add(P2, G);
+            const uint32_t bt = sat_sub(P1, G), at = min(sat_add(P2, G), CKMAX);
             const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
             hist_zero(hist, lane);
             __syncwarp();
             int64_t Sb = 0;
             for (int i = lane; i < n; i += 32) {
                 const float iv = inv[i];
-                if (iv == 0.0f) continue;
+                if (isnan(iv)) continue;  // x_ijhat = 0 or a padding row
                 uint32_t kk = akey(__fmul_rn(xf[i], iv));
                 if (kk < bt) {
                     Sb += colq[i];
@@ -402,14 +402,15 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         // one pass over all rows: exact weight of rows certainly below P1; rows
         // whose approximate key is within G of [P1, P2] become candidates
         const uint32_t bt = sat_sub(P1, G);  // certain below: key' < bt
-        const uint32_t at = sat_add(P2, G);  // certain above: key' > at
+        const uint32_t at = min(sat_add(P2, G), CKMAX);  // certain above: key' > at
         int64_t Sb = 0;
         cnt = 0;
         // rows are visited in batches of 4 per lane; the global loads of the next
         // batch are issued before the current one is classified, so the L2
         // latency overlaps the work
         // U * 32 = ROW_PAD rows per batch: every index below the padded row
-        // count is readable and padding rows (reciprocal 0) are not valid
+        // count is readable, and padding rows (reciprocal NaN) are neither
+        // below nor candidates
         constexpr int U = 4;
         static_assert(U * 32 == ROW_PAD, "one batch = one row pad");
         float an[U];
@@ -429,9 +430,8 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 const int i = i0 + u * 32 + lane;
                 const float iv = inv[i];
                 const uint32_t kk = akey(__fmul_rn(ac[u], iv));
-                const bool valid = iv != 0.0f;
-                const bool below = valid && kk < bt;
-                const bool cand = valid && !below && kk <= at;
+                const bool below = kk < bt;
+                const bool cand = !below && kk <= at;
                 const int64_t q = colq[i];
                 Sb += below ? q : 0;
                 // speculative store: the slot is only kept when cnt advances
@@ -757,7 +757,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     }
     const K Klo = min(Ka, Kb), Khi = max(Ka, Kb);
     const uint32_t cl = ckey((float)Tr::value(Klo)), ch = ckey((float)Tr::value(Khi));
-    const uint32_t bt = sat_sub(cl, G), at = sat_add(ch, G);
+    const uint32_t bt = sat_sub(cl, G), at = min(sat_add(ch, G), CKMAX);
     int64_t Sb = 0;  // exact weight of rows with key < Klo
     int cnt = 0;
     uint16_t *stage = reinterpret_cast<uint16_t *>(w.hist);
@@ -786,7 +786,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
             bool take = false;
             if (i < n) {
                 const float iv = w.inv[i];
-                if (iv != 0.0f) {
+                if (!isnan(iv)) {
                     const uint32_t kk = akey(__fmul_rn(ac[u], iv));
                     if (kk < bt) {
                         Sb += w.colq[i];
@@ -891,7 +891,12 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     for (int i = threadIdx.x; i < npad; i += blockDim.x) {
         const T b = i < n ? xj[i] : T(0);
         colb[i] = b;
-        inv[i] = b != T(0) ? Approx<T>::inv_of(b) : 0.0f;
+        // rows with x_ijhat = 0 (and padding rows) get a NaN reciprocal: their
+        // approximate key is the NaN key CKNONE, above every bracket (bounds
+        // stop at CKMAX), so the level-0 pass needs no validity test.  Their
+        // weight is 0, so even a NaN of the other sign (a key near 0) could
+        // only add zero-weight candidates, which never decide the median.
+        inv[i] = b != T(0) ? Approx<T>::inv_of(b) : __int_as_float(0x7FFFFFFF);
         int e = 0;
         colq[i] = b != T(0) ? fixq(b < T(0) ? -b : b, cinfo.sigma, e) : 0;
     }
