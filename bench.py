@@ -57,6 +57,22 @@ def _env_rank():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def job_ms(local_ms: float, dist=None, device=None) -> float:
+    """The job's time over ranks: the slowest rank's (all-reduce MAX); the
+    local time without a process group."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps: int, units_per_step: float, tot_ms: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * steps * units_per_step / (tot_ms * 1e-3)
+
+
 def _src_hash() -> str:
     h = hashlib.sha256()
     for f in ("k_pairs.cu", "pairs.cuh", "common.cuh"):
@@ -272,11 +288,8 @@ def run_gpu(args):
     rc = l1line.status(ws, stream)
     if rc != l1line.OK:
         raise SystemExit(f"fit failed on the device: {l1line.status_string(rc)}")
-    if dist is not None:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * args.steps * pairs / (tot_ms * 1e-3)
+    tot_ms = job_ms(tot_ms, dist, dev)
+    value = job_value(world, args.steps, pairs, tot_ms)
 
     # ---- float64 input, same workload (reported beside the headline) -------
     l1line.set_tuning(None)
