@@ -552,7 +552,94 @@ def measure_extras(dev, stream, flush):
         "ms_per_step": ms, "fits_per_s": len(batch) / (ms * 1e-3),
         "pairs_per_s": pairs / (ms * 1e-3), "gpu_launches_per_step": launches,
         "tuning": btune}
+    del Xs, bat, g
+    out["small_fit"] = measure_small_fit(dev, stream)
+    out["learned_topk"] = measure_learned(dev, stream, flush)
     return out
+
+
+def measure_small_fit(dev, stream, replays=200):
+    """The smallest workload: n=200, m=20 float64, lambda=0.1; one fit captured
+    in a CUDA graph and replayed back to back (latency-bound; the 32 KB input
+    stays in L2, no flush)."""
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+    X, lams, _ = datagen.one_fit_small("float64")
+    n, m = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    ws = l1line.Workspace.for_shape(torch.float64, n, m, 1, dev)
+    res = (torch.empty((1, m), dtype=torch.float64, device=dev),
+           torch.empty(1, dtype=torch.float64, device=dev),
+           torch.empty(1, dtype=torch.int32, device=dev))
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
+    stream.synchronize()
+    launches = l1line.last_launch_count()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        l1line.fit(Xd, lams, workspace=ws, stream=stream, out=res)
+    ms = _replay_ms(g, stream, replays)
+    if l1line.status(ws, stream) != l1line.OK:
+        raise SystemExit("small fit failed on the device")
+    return {"workload": f"n={n}, m={m} float64, 4-sparse v*, Laplace(0,0.05), 10% N(0,25 I) "
+                        "outliers, lambda=0.1; CUDA graph replayed back to back",
+            "us_per_fit": ms * 1e3, "fits_per_s": 1.0 / (ms * 1e-3),
+            "pairs_per_s": m * (m - 1) / (ms * 1e-3), "gpu_launches_per_step": launches}
+
+
+def measure_learned(dev, stream, flush, count=8, Ks=(32, 512)):
+    """The learned top-K path against the full scan on a sample of held-out
+    5000 x 1000 float32 instances (the committed network; the 200-instance
+    evaluation is the proposer module's `eval`).  Times are CUDA events with L2
+    flushed; zero regret = the learned path's objective equals the scan's bit
+    for bit."""
+    import numpy as np
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line, proposer
+    mlp = proposer.network(dev)
+    n, m = 5000, 1000
+    ws = l1line.Workspace.for_shape(torch.float32, n, m, 1, dev)
+
+    def timed(fn):
+        flush.fill_(5)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+        stream.synchronize()
+        return e0.elapsed_time(e1), r
+
+    full_ms, learned_ms, hits = [], {K: [] for K in Ks}, {K: 0 for K in Ks}
+    for q in range(count):
+        X, lams, _ = datagen.proposer_instance(datagen.PROPOSER_HELDOUT_SEED0 + q, n=n, m=m)
+        Xd = torch.from_numpy(X).to(dev)
+        with torch.cuda.stream(stream):
+            l1line.fit(Xd, lams, workspace=ws, stream=stream)
+        ms, (v, obj, js, _) = timed(lambda: l1line.fit(Xd, lams, workspace=ws, stream=stream))
+        full_ms.append(ms)
+        z_full = obj.cpu().numpy().copy()
+        for K in Ks:
+            with torch.cuda.stream(stream):
+                l1line.fit_proposed(Xd, lams, mlp, K, workspace=ws, stream=stream)
+            ms, (v2, obj2, js2, _, _) = timed(
+                lambda: l1line.fit_proposed(Xd, lams, mlp, K, workspace=ws, stream=stream))
+            learned_ms[K].append(ms)
+            hits[K] += int(np.array_equal(obj2.cpu().numpy().view(np.int64),
+                                          z_full.view(np.int64)))
+    if l1line.status(ws, stream) != l1line.OK:
+        raise SystemExit("learned path failed on the device")
+    fm = float(np.median(full_ms))
+    return {"workload": f"{count} held-out planted instances n={n}, m={m} float32, lambda=0.2 "
+                        "(seeds from the held-out range); learned path = features, network, "
+                        "top-K, exact fit of the K candidates",
+            "full_scan_ms": fm,
+            "K": {str(K): {"ms": float(np.median(learned_ms[K])),
+                           "speedup_vs_full_scan": fm / float(np.median(learned_ms[K])),
+                           "zero_regret_fraction": hits[K] / count} for K in Ks}}
 
 
 def run_profile_case(args):
