@@ -20,15 +20,18 @@
 //            one pass over all rows sums the exact fixed-point weight below
 //            the lower pivot and compacts the rows between the pivots (guard
 //            bands included) into the candidate list;
-//   resolve  guard-band candidates are divided exactly; the exact weight below
-//            and between the pivots decides whether the median lies between
-//            them (else level 0 repeats on the indicated side);
-//   levels   on the candidate list: sample 32, sort, two pivots, count, decide,
-//            compact, until <= 31 candidates or one coarse key remains;
-//   final    exact keys (double: 64-bit) of the candidates plus the penalty
-//            point's key are sorted across the warp; a prefix scan of the
-//            weights finds the smallest key whose cumulative weight passes
-//            half the total (the test of Lemma 1, decided exactly);
+//   resolve  guard-band candidates are divided exactly; an exact 64-bin
+//            weight histogram of [P1, P2] and the exact weight below P1 decide
+//            whether the median lies between the pivots (else level 0 repeats
+//            on the indicated side) and in which bin; that bin's candidates
+//            are kept;
+//   levels   while more than 31 candidates remain: the same exact histogram
+//            over the surviving key range, keep the crossing bin;
+//   final    exact keys (double: 64-bit) of the <= 31 candidates plus the
+//            penalty point's key, one per lane; each lane's cumulative weight
+//            (a shuffle sum over the keys <= its own) is tested and the
+//            smallest passing key is the median (the test of Lemma 1, decided
+//            exactly);
 //   residual sum_i |x_ik - v x_ijhat| over all rows (Algorithm 1, objective).
 //
 // A decision the truncated fixed-point weights cannot settle, a column whose
