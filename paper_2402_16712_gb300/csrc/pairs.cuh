@@ -150,30 +150,54 @@ template <typename V> __device__ __forceinline__ V warp_scan_add(V x, int lane) 
 }
 
 // Residual over the padded rows: Xt and the staged column are zero past n, so
-// a padding row adds |0 - v 0| = 0.  Four rows per lane per step, the global
-// loads of the next step issued before this step is summed.
+// a padding row adds |0 - v 0| = 0.  np is a multiple of ROW_PAD.
+//   float:  eight rows per lane per step, all eight global loads issued before
+//           any is summed, four accumulators (a load issued a step ahead
+//           measured slower at low occupancy);
+//   double: four rows per lane per step, the next step's loads issued before
+//           this step is summed (eight double loads in flight spill at the
+//           kernel's register cap).
 template <typename T>
 __device__ __forceinline__ T warp_residual_pad(const T *__restrict__ xk, const T *__restrict__ xj,
                                                int n, T v, int lane) {
-    constexpr int U = 4;
-    static_assert(U * 32 == ROW_PAD, "one step = one row pad");
     const int np = (n + ROW_PAD - 1) & ~(ROW_PAD - 1);
-    T acc[U], an[U];
+    T acc[4] = {T(0), T(0), T(0), T(0)};
+    if constexpr (sizeof(T) == 4) {
+        constexpr int U = 8;
+        static_assert(32 * U == 2 * ROW_PAD, "a step is two row pads");
+        int i0 = 0;
+        for (; i0 + 32 * U <= np; i0 += 32 * U) {
+            T ac[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        acc[u] = T(0);
-        an[u] = xk[u * 32 + lane];
-    }
-    for (int i0 = 0; i0 < np; i0 += 32 * U) {
-        T ac[U];
+            for (int u = 0; u < U; ++u) ac[u] = xk[i0 + u * 32 + lane];
 #pragma unroll
-        for (int u = 0; u < U; ++u) ac[u] = an[u];
-        if (i0 + 32 * U < np) {
-#pragma unroll
-            for (int u = 0; u < U; ++u) an[u] = xk[i0 + 32 * U + u * 32 + lane];
+            for (int u = 0; u < U; ++u)
+                acc[u & 3] += fabs(fma(-v, xj[i0 + u * 32 + lane], ac[u]));
         }
+        if (i0 < np) {  // one row pad left
+            T ac[U / 2];
 #pragma unroll
-        for (int u = 0; u < U; ++u) acc[u] += fabs(fma(-v, xj[i0 + u * 32 + lane], ac[u]));
+            for (int u = 0; u < U / 2; ++u) ac[u] = xk[i0 + u * 32 + lane];
+#pragma unroll
+            for (int u = 0; u < U / 2; ++u) acc[u] += fabs(fma(-v, xj[i0 + u * 32 + lane], ac[u]));
+        }
+    } else {
+        constexpr int U = 4;
+        static_assert(U * 32 == ROW_PAD, "one step = one row pad");
+        T an[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) an[u] = xk[u * 32 + lane];
+        for (int i0 = 0; i0 < np; i0 += 32 * U) {
+            T ac[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) ac[u] = an[u];
+            if (i0 + 32 * U < np) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) an[u] = xk[i0 + 32 * U + u * 32 + lane];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc[u] += fabs(fma(-v, xj[i0 + u * 32 + lane], ac[u]));
+        }
     }
     T s = (acc[0] + acc[1]) + (acc[2] + acc[3]);
 #pragma unroll
