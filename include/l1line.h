@@ -417,6 +417,11 @@ int l1line_last_launch_count(void);
  *                for its largest n (planner: two classes when the model
  *                puts them at least 5% below one, else one; l1line_plan
  *                reports 0)
+ *   column       where the pair kernel keeps x_ijhat: 1 shared memory, 2 the
+ *                column copy in global memory (L2), which leaves shared memory
+ *                to more resident warps (planner: global for double input;
+ *                for float input global only when that admits more resident
+ *                warps; l1line_plan reports 1 or 2)
  * l1line_set_tuning applies to the later calls of the calling thread (NULL
  * restores the planner); a tuning whose candidate lists do not fit shared
  * memory makes those calls return L1L_ERR_UNSUPPORTED.  l1line_plan reports
@@ -429,6 +434,7 @@ typedef struct l1line_tuning {
     int32_t kchunk;
     int32_t d0;
     int32_t batch_classes;
+    int32_t column;
 } l1line_tuning;
 int l1line_set_tuning(const l1line_tuning *t);
 int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out);

@@ -737,13 +737,14 @@ int l1line_set_tuning(const l1line_tuning *t) {
     }
     if (t->warps < 0 || t->warps > 8 || t->ctas_per_sm < 0 || t->ctas_per_sm > 3 ||
         t->kchunk < 0 || t->d0 < 0 || t->d0 > 24 || t->batch_classes < 0 ||
-        t->batch_classes > MAX_BATCH_CLASSES)
+        t->batch_classes > MAX_BATCH_CLASSES || t->column < 0 || t->column > 2)
         return L1L_ERR_ARG;
     g_tune.warps = t->warps;
     g_tune.ctas = t->ctas_per_sm;
     g_tune.kchunk = t->kchunk;
     g_tune.d0 = t->d0;
     g_tune.batch_classes = t->batch_classes;
+    g_tune.column = t->column;
     return L1L_OK;
 }
 
@@ -760,6 +761,7 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
     out->kchunk = p.kchunk;
     out->d0 = p.d0;
     out->batch_classes = g_tune.batch_classes;
+    out->column = p.cs ? 1 : 2;
     return L1L_OK;
 }
 

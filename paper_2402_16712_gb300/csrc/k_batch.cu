@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_colprep_b(const __grid_constant__ Batch
 // Persistent: every CTA loops, taking the next (instance, jhat) unit of units
 // [u0, u1) (one size class of the batch) from that class's counter; units are
 // numbered largest instance first.  No CTA waits on another.
-template <typename T, bool MULTI>
+template <typename T, bool MULTI, bool CS>
 __global__ void __launch_bounds__(256, 3)
     k_pairs_persist(const __grid_constant__ BatchDesc<T> bd, unsigned char *ws, int64_t u0,
                     int64_t u1, int slot, int lay_npad, int cap) {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256, 3)
         const BatchInst<T> &in = bd.inst[b];
         const ScanArgs<T> a = inst_args<T>(bd, b, ws);
         const LamView lv{bd.lam + bd.lam_begin[b], in.tl_min, in.tl_max};
-        pairs_unit<T, MULTI>(a, lv, 0, in.nl, (int)(u - bd.unit_begin[b]), 0, in.m, cap,
+        pairs_unit<T, MULTI, CS>(a, lv, 0, in.nl, (int)(u - bd.unit_begin[b]), 0, in.m, cap,
                              lay_npad, smem, s_dec);
     }
 }
@@ -193,11 +193,14 @@ cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, do
     k_transpose_b<T><<<bd.tiles, dim3(32, 8), 0, st>>>(bd, ws);
     k_colprep_b<T><<<(unsigned)bd.units, 256, 0, st>>>(bd, ws);
     launches += 2;
-    auto kern = multi ? k_pairs_persist<T, true> : k_pairs_persist<T, false>;
     // one persistent launch per size class, each with shared memory for its largest n
     for (int c = 0; c < nclasses; ++c) {
         const BatchClass &bc = classes[c];
         if (bc.u1 <= bc.u0) continue;
+        auto kern = multi ? (bc.plan.cs ? k_pairs_persist<T, true, true>
+                                        : k_pairs_persist<T, true, false>)
+                          : (bc.plan.cs ? k_pairs_persist<T, false, true>
+                                        : k_pairs_persist<T, false, false>);
         e = ensure_smem(reinterpret_cast<const void *>(kern), bc.plan.smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;

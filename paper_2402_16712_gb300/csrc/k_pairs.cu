@@ -58,7 +58,7 @@ cudaError_t blocks_per_sm(const void *fn, int threads, size_t smem, int *out) {
     return cudaSuccess;
 }
 
-template <typename T, bool MULTI>
+template <typename T, bool MULTI, bool CS>
 __global__ void __launch_bounds__(256, 3)
     k_pairs(ScanArgs<T> a, const __grid_constant__ LambdaPack lp, int t0, int nlc, int kchunk,
             int cap) {
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256, 3)
         if (threadIdx.x == 0) atomicOr(a.status, ST_BADINDEX);
         return;
     }
-    pairs_unit<T, MULTI>(a, lv, t0, nlc, (int)j, k0, k1, cap,
+    pairs_unit<T, MULTI, CS>(a, lv, t0, nlc, (int)j, k0, k1, cap,
                          ((int)a.n + ROW_PAD - 1) & ~(ROW_PAD - 1), smem, s_dec);
 }
 
@@ -87,20 +87,18 @@ template <typename T> int64_t max_rows_pairs() {
     const size_t budget = 227 * 1024;
     int64_t n = ROW_PAD;
     while (n + ROW_PAD <= (int64_t)ROW_MASK + 1 &&
-           PairSmem<T>::col_bytes(n + ROW_PAD) +
+           PairSmem<T>::col_bytes(n + ROW_PAD, false) +
                    PairSmem<T>::warp_bytes(cap_for<T>(n + ROW_PAD)) <=
                budget)
         n += ROW_PAD;
     return n;
 }
 
+// The resident-warp plan for one placement of x_ijhat (cs: shared memory).
 template <typename T>
-PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune) {
-    PairPlan p{0, 0, 0, 0, 0, 0, 0};
-    const int64_t npad = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
-    if (n > max_rows_pairs<T>()) return p;
-    const size_t cb = PairSmem<T>::col_bytes(npad);
-    const int d0 = tune.d0 > 0 ? tune.d0 : D0_DEFAULT;
+static PairPlan plan_placement(int64_t npad, bool cs, int d0, const Tune &tune) {
+    PairPlan p{0, 0, 0, 0, 0, 0, 0, 0};
+    const size_t cb = PairSmem<T>::col_bytes(npad, cs);
     // Per-lane candidate quota wanted: the level-0 bracket (+-d0 of 64 weight
     // samples) holds ~2.5% of the rows per sample position, i.e. mu = 0.025 d0
     // n/32 per lane; ask for mu + 3.5 sqrt(mu) + 1 so that the busiest of 32
@@ -134,7 +132,34 @@ PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &t
     p.cap = cap;
     p.ctas = nc;
     p.d0 = d0;
+    p.cs = cs ? 1 : 0;
     p.smem = cb + (size_t)w * PairSmem<T>::warp_bytes(cap);
+    return p;
+}
+
+template <typename T>
+PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune) {
+    PairPlan p{0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t npad = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
+    if (n > max_rows_pairs<T>()) return p;
+    const int d0 = tune.d0 > 0 ? tune.d0 : D0_DEFAULT;
+    // Where x_ijhat lives.  Shared memory saves the residual pass an L2 read
+    // per row; global memory frees n * sizeof(T) bytes per CTA.  Measured:
+    // float keeps it in shared memory unless the smaller footprint admits more
+    // resident warps (2000 x 2000: equal plans, shared 3% faster; 5000 x 1000:
+    // 8 -> 14 warps per SM, global 11% faster); double reads it from global
+    // memory (2000 x 2000: 5% faster at equal plans).
+    const PairPlan ps = tune.column == 2 ? p : plan_placement<T>(npad, true, d0, tune);
+    const PairPlan pg = tune.column == 1 ? p : plan_placement<T>(npad, false, d0, tune);
+    const int rs = ps.warps * ps.ctas, rg = pg.warps * pg.ctas;
+    if (rs == 0 && rg == 0) return p;
+    if (rg == 0)
+        p = ps;
+    else if (rs == 0)
+        p = pg;
+    else
+        p = (sizeof(T) == 8 || rg > rs) ? pg : ps;
+    const int w = p.warps, nc = p.ctas;
     int64_t chunks;
     if (tune.kchunk > 0) {
         chunks = (m + std::min<int64_t>(m, tune.kchunk) - 1) / std::min<int64_t>(m, tune.kchunk);
@@ -167,7 +192,8 @@ template <typename T>
 cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
                          const PairPlan &plan, cudaStream_t st, int &launches) {
     // separate instantiations keep the single-lambda kernel small
-    auto kern = nlc >= 3 ? k_pairs<T, true> : k_pairs<T, false>;
+    auto kern = nlc >= 3 ? (plan.cs ? k_pairs<T, true, true> : k_pairs<T, true, false>)
+                         : (plan.cs ? k_pairs<T, false, true> : k_pairs<T, false, false>);
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), plan.smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)a.nj, (unsigned)plan.kchunks);

@@ -31,10 +31,12 @@ struct PairPlan {
     int cap;   // per-warp candidate-list capacity
     int ctas;  // CTAs per SM the shared memory is sized for
     int d0;    // first-bracket half-width of the selection
+    int cs;    // 1: x_ijhat staged in shared memory; 0: read from global memory
 };
 // Caller overrides of the planner (0 = the planner's choice).
 struct Tune {
     int warps = 0, ctas = 0, kchunk = 0, d0 = 0, batch_classes = 0;
+    int column = 0;  // 1: x_ijhat in shared memory, 2: in global memory
 };
 // nj: number of jhat scored (m for a full scan).
 template <typename T>

@@ -77,10 +77,12 @@ constexpr int NSAMP = 64;   // weight-proportional sample rows per column
 constexpr int HIST_WORDS = 4 * 64;  // per-warp exact histogram (4 chunks x 64 bins)
 
 template <typename T> struct PairSmem {
-    // per CTA: x_ijhat (T), 1/x_ijhat (float, NaN marks x_ijhat == 0), q_i (int64),
-    // the 64 sample rows (uint16)
-    __host__ __device__ static size_t col_bytes(int64_t npad) {
-        return al16(npad * sizeof(T)) + al16(npad * 4) + al16(npad * 8) + al16(NSAMP * 2);
+    // per CTA: x_ijhat (T; only when `cs`, else it is read from the column
+    // copy in global memory), 1/x_ijhat (float, NaN marks x_ijhat == 0), q_i
+    // (int64), the 64 sample rows (uint16)
+    __host__ __device__ static size_t col_bytes(int64_t npad, bool cs) {
+        return (cs ? al16(npad * sizeof(T)) : 0) + al16(npad * 4) + al16(npad * 8) +
+               al16(NSAMP * 2);
     }
     // per warp: candidate keys (uint32), row indices (uint16; bit 15 = exact key)
     // and the histogram (uint32)
@@ -885,8 +887,11 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
 
 // One work unit: column jhat = j of an instance and the k in [k0, k1), all
 // lambdas of the launch.  Called by every thread of a CTA; `smem` is laid out
-// for lay_npad rows (column arrays, then one candidate list per warp).
-template <typename T, bool MULTI>
+// for lay_npad rows (column arrays, then one candidate list per warp).  CS:
+// x_ijhat is staged in shared memory; otherwise the warps read it from the
+// column copy in global memory (L2-resident), which frees shared memory for
+// more resident warps when n is large.
+template <typename T, bool MULTI, bool CS>
 __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int nlc, int j,
                            int64_t k0, int64_t k1, int cap, int lay_npad, unsigned char *smem,
                            Decide *s_dec) {
@@ -897,27 +902,28 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     const int npad = lay_npad;  // shared-memory layout stride (>= n rounded up to 32)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
-    T *colb = reinterpret_cast<T *>(smem);
-    size_t off = al16((size_t)npad * sizeof(T));
+    const T *xj = a.Xt + (int64_t)j * ldn;
+    T *colb_s = reinterpret_cast<T *>(smem);
+    const T *colb = CS ? colb_s : xj;
+    size_t off = CS ? al16((size_t)npad * sizeof(T)) : 0;
     float *inv = reinterpret_cast<float *>(smem + off);
     off += al16((size_t)npad * 4);
     int64_t *colq = reinterpret_cast<int64_t *>(smem + off);
     off += al16((size_t)npad * 8);
     uint16_t *samp = reinterpret_cast<uint16_t *>(smem + off);
     unsigned char *wbase =
-        smem + PairSmem<T>::col_bytes(npad) + (size_t)warp * PairSmem<T>::warp_bytes(cap);
+        smem + PairSmem<T>::col_bytes(npad, CS) + (size_t)warp * PairSmem<T>::warp_bytes(cap);
     uint32_t *lk = reinterpret_cast<uint32_t *>(wbase);
     uint16_t *li = reinterpret_cast<uint16_t *>(wbase + al16((size_t)cap * 4));
     uint32_t *hist = reinterpret_cast<uint32_t *>(wbase + al16((size_t)cap * 4) +
                                                   al16((size_t)cap * 2));
     // prologue scratch: the first 256 bytes of warp 0's candidate list
-    long long *s_wsum = reinterpret_cast<long long *>(smem + PairSmem<T>::col_bytes(npad));
+    long long *s_wsum = reinterpret_cast<long long *>(smem + PairSmem<T>::col_bytes(npad, CS));
 
     const ColInfo cinfo = a.ci[j];
-    const T *xj = a.Xt + (int64_t)j * ldn;
     for (int i = threadIdx.x; i < npad; i += blockDim.x) {
         const T b = i < n ? xj[i] : T(0);
-        colb[i] = b;
+        if (CS) colb_s[i] = b;
         // rows with x_ijhat = 0 (and padding rows) get a NaN reciprocal: their
         // approximate key is the NaN key CKNONE, above every bracket (bounds
         // stop at CKMAX), so the level-0 pass needs no validity test.  Their

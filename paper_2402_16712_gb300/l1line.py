@@ -452,7 +452,7 @@ class Tuning(ctypes.Structure):
     """l1line_tuning: pair-kernel launch overrides (0 = the planner's choice)."""
     _fields_ = [("warps", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("kchunk", ctypes.c_int32), ("d0", ctypes.c_int32),
-                ("batch_classes", ctypes.c_int32)]
+                ("batch_classes", ctypes.c_int32), ("column", ctypes.c_int32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

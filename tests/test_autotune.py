@@ -35,13 +35,17 @@ def test_candidates_vary_one_knob_group():
                                   kchunk=False, classes=True))
     assert [x for x in cb if "batch_classes" in x] == [{"batch_classes": k} for k in (1, 2, 3)]
     assert not any("kchunk" in x for x in cb)
+    # the other placement of x_ijhat than the plan's
+    assert {"column": 2} in c and {"column": 1} in c
+    assert [x for x in autotune.candidates({"kchunk": 1, "d0": 6, "column": 2})
+            if "column" in x] == [{"column": 1}]
 
 
 def test_tuning_argument_checks():
     __graft_entry__.build()
     l1line.load()
     for bad in ({"warps": 9}, {"ctas_per_sm": 4}, {"kchunk": -1}, {"d0": 25}, {"warps": -1},
-                {"batch_classes": 4}, {"batch_classes": -1}):
+                {"batch_classes": 4}, {"batch_classes": -1}, {"column": 3}, {"column": -1}):
         with pytest.raises(l1line.L1LineError):
             l1line.set_tuning(bad)
     l1line.set_tuning({"warps": 4, "d0": 8})
