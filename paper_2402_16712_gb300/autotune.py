@@ -71,18 +71,19 @@ def store(k: str, tuning: dict, ms: float, path: Optional[str] = None) -> None:
 def candidates(base: dict, kchunk: bool = True, classes: bool = False):
     """Coordinate sweeps around the planner's plan `base` (l1line.plan):
     k per CTA (unless kchunk is False), the number of size classes of a
-    batched call (if classes), the other placement of x_ijhat, then the
-    bracket width, then warps x CTAs per SM."""
+    batched call (if classes), the bracket width, the other placement of
+    x_ijhat, then warps x CTAs per SM."""
     kc = max(1, base["kchunk"])
     for div in ((2, 3, 4, 6) if kchunk else ()):
         yield {"kchunk": max(1, -(-kc // div))}
     for k in ((1, 2, 3) if classes else ()):
         yield {"batch_classes": k}
+    for d0 in (3, 4, 5, 7, 8, 10):
+        yield {"d0": d0}
+    # after the bracket width: which placement is faster depends on it
     for c in (1, 2):
         if c != base.get("column"):
             yield {"column": c}
-    for d0 in (3, 4, 5, 7, 8, 10):
-        yield {"d0": d0}
     for warps, ctas in ((8, 2), (6, 3), (4, 3), (4, 2), (8, 1)):
         yield {"warps": warps, "ctas_per_sm": ctas}
 
