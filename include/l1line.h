@@ -414,9 +414,9 @@ int l1line_last_launch_count(void);
  *                ordered by n, are cut into that many runs (where the
  *                planner's occupancy model places the cuts), each run
  *                scored by its own pair launch with shared memory laid out
- *                for its largest n (planner: two classes when the model
- *                puts them at least 5% below one, else one; l1line_plan
- *                reports 0)
+ *                for its largest n (planner: one more class while the
+ *                model puts it at least 5% below the best with one fewer;
+ *                l1line_plan reports 0)
  *   column       where the pair kernel keeps x_ijhat: 1 shared memory, 2 the
  *                column copy in global memory (L2), which leaves shared memory
  *                to more resident warps (planner: global for double input;

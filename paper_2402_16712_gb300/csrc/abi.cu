@@ -816,7 +816,8 @@ struct BatchShape {
 // n m^2 nl) / (resident warps of its plan).  Classes are runs of the instances
 // ordered by n (cuts only where n changes); the best split into k classes is
 // found by dynamic programming for each k.  Unless the tuning fixes k, the
-// planner takes two classes when the model puts them at least 5% below one.  Reorders `order`
+// planner adds a class while the model puts it at least 5% below the best
+// with one class fewer.  Reorders `order`
 // (stably, so largest work first within a class) and returns the instance
 // count of each class, largest n first.
 template <typename T>
@@ -859,9 +860,8 @@ std::vector<int64_t> batch_classes(int64_t batch, const int64_t *ns, const int64
         for (int kk = tb.batch_classes - 1; kk >= 0 && k == 0; --kk)
             if (g[kk][0] < INF) k = kk;  // fewer when n takes fewer distinct values
     } else {
-        // the planner stops at two: a third class measured slower than the
-        // model predicts (each class's launch ends on its own tail)
-        if (g[1][0] < 0.95 * g[0][0]) k = 1;
+        for (int kk = 1; kk < MAX_BATCH_CLASSES; ++kk)
+            if (g[kk][0] < 0.95 * g[k][0]) k = kk;
     }
     std::vector<int64_t> counts;
     std::vector<int> cls((size_t)batch, 0);
