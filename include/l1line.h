@@ -197,7 +197,13 @@ int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *l
  * double, same size, or NULL) receives each entry's residual
  * sum_i |x_ik - v x_ijhat| (double sums), so that on the entry's lambda
  * interval the pair's term of z_jhat is out_resid + lambda |out_v|.
+ *
+ * n is limited by the path kernels' shared memory (one staged column and
+ * eight 256-entry lists per CTA): l1line_path_max_rows(dtype) returns the
+ * largest n; larger n make l1line_path_workspace_bytes return 0 and the
+ * calls return L1L_ERR_UNSUPPORTED.
  */
+int64_t l1line_path_max_rows(int dtype);
 size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m);
 int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets,
                           void *workspace, size_t workspace_bytes, void *stream);

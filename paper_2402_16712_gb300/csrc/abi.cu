@@ -241,6 +241,8 @@ struct PathLayout {
 };
 
 bool make_path_layout(int dtype, int64_t n, int64_t m, PathLayout &P) {
+    if (n > (dtype == L1L_DTYPE_F32 ? path_max_rows<float>() : path_max_rows<double>()))
+        return false;
     if (!make_layout(dtype, n, m, 1, P.L)) return false;
     int64_t mm;
     if (!mul_ok(m, m, mm) || mm > ((int64_t)1 << 40)) return false;
@@ -547,6 +549,12 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
                             void *stream) {
     return proposed_impl<double>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
                                  out_jstar, workspace, workspace_bytes, stream);
+}
+
+int64_t l1line_path_max_rows(int dtype) {
+    if (dtype == L1L_DTYPE_F32) return path_max_rows<float>();
+    if (dtype == L1L_DTYPE_F64) return path_max_rows<double>();
+    return 0;
 }
 
 size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m) {

@@ -544,6 +544,14 @@ template <typename T> size_t path_smem_bytes(int64_t n) {
            (size_t)PW * PATH_CAP * (sizeof(typename Traits<T>::K) + 4);
 }
 
+// Largest n whose staged column and lists fit one CTA of the path kernels
+// (and that the fit, which solves lambda = 0, accepts).
+template <typename T> int64_t path_max_rows() {
+    int64_t n = 32;
+    while (n + 32 <= max_rows_pairs<T>() && path_smem_bytes<T>(n + 32) <= 227 * 1024) n += 32;
+    return n;
+}
+
 template <typename T>
 cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo *ci, int64_t n,
                         int64_t m, int64_t ldn, const T *v0, int64_t *bound_or_off,
@@ -600,6 +608,8 @@ cudaError_t launch_path(bool count, const T *Xt, const float *Xf, const ColInfo 
 
 template size_t path_slice_bytes<float>(int64_t);
 template size_t path_slice_bytes<double>(int64_t);
+template int64_t path_max_rows<float>();
+template int64_t path_max_rows<double>();
 template cudaError_t launch_path<float>(bool, const float *, const float *, const ColInfo *,
                                         int64_t, int64_t, int64_t, const float *, int64_t *,
                                         int64_t *, double *, float *, double *, int32_t *,

@@ -104,6 +104,7 @@ size_t path_scan_scratch(int64_t N);
 cudaError_t launch_scan_i64(int64_t *a, int64_t N, int64_t *tmp, cudaStream_t st, int &launches);
 int path_big_workers();
 template <typename T> size_t path_slice_bytes(int64_t n);
+template <typename T> int64_t path_max_rows();
 // count: bound_or_off = [m*m + 1] offsets out (exclusive scan of the bounds);
 // write: bound_or_off = those offsets in, lam / val / len out.
 template <typename T>

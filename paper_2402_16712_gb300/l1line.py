@@ -36,6 +36,7 @@ SIGNATURES = {
     "l1line_status_string": (ctypes.c_char_p, [_I]),
     "l1line_last_launch_count": (_I, []),
     "l1line_profile_events": (_I, [_P, _P]),
+    "l1line_path_max_rows": (_I64, [_I]),
     "l1line_probe": (_I, [_I, _P, _SZ, _I, _P, _P, _P]),
     "l1line_fit_noalloc_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P]),
     "l1line_batched_workspace_bytes": (_SZ, [_I, _I64, _P, _P, _P]),

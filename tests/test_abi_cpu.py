@@ -54,6 +54,13 @@ def test_workspace_and_limits(lib):
     assert l1line.workspace_bytes(np.float32, 1 << 40, 1 << 40, 1) == 0  # overflow caught
     assert l1line.max_rows(np.float32) >= 5000 and l1line.max_rows(np.float64) >= 5000
     assert lib.l1line_max_rows(7) == 0
+    # the path kernels stage a column and eight 256-entry lists per CTA: a lower limit
+    for dt in (l1line.DTYPE_F32, l1line.DTYPE_F64):
+        pm = lib.l1line_path_max_rows(dt)
+        assert 5000 <= pm <= lib.l1line_max_rows(dt) and pm % 32 == 0
+        assert lib.l1line_path_workspace_bytes(dt, pm, 10) > 0
+        assert lib.l1line_path_workspace_bytes(dt, pm + 1, 10) == 0
+    assert lib.l1line_path_max_rows(7) == 0
 
 
 def _scan(lib, X=256, n=4, m=3, lam=(0.5,), nl=None, ws=1024, wsb=1 << 30, flags=0):

@@ -121,3 +121,14 @@ def test_paths_paper_size_sampled():
         gl, gv = lam[off[p]:off[p] + L], v[off[p]:off[p] + L]
         assert np.array_equal(_bits(gv), _bits(rv))
         assert np.all(np.abs(gl - rl) <= 2.0 ** -40 * colnorm[j])
+
+
+@pytest.mark.parametrize("dtype", ["float32", "float64"])
+def test_paths_at_the_largest_row_count(dtype):
+    # n = the path kernels' row limit (their staged column and lists fill a CTA's
+    # shared memory); one more row is refused
+    dt = l1line.DTYPE_F32 if dtype == "float32" else l1line.DTYPE_F64
+    n = int(l1line.load().l1line_path_max_rows(dt))
+    X, _, _ = datagen.planted(datagen.Planted(n, 3, 1, 0.1, 0.1, 5.0, 17, dtype))
+    _check_pairs(X, _all_pairs(3), exact_lambda=False)
+    assert l1line.load().l1line_path_workspace_bytes(dt, n + 1, 3) == 0
