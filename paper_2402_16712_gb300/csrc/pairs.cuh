@@ -289,6 +289,104 @@ __device__ __forceinline__ int hist_cross(const uint32_t *h, int nbins, uint32_t
     return bsel;
 }
 
+// Bins of the level-0 bracket [p1, p2].  Uniform: equal key ranges.  A
+// bracket that crosses 0 spans every binade of tiny magnitudes on both sides,
+// where few ratios lie (key space is logarithmic near 0), so equal key ranges
+// would crowd its candidates into the one or two bins of the largest
+// magnitudes.  Crossing layout instead: on each side, equal bins over the
+// 7.75 binades of largest magnitude (the wing, up to 31 bins of a quarter
+// binade or less), the innermost of them widened to reach key 0:
+//   negative side [p1, CK0): bins 0 .. n0-1, bin b = p1 + [b, b+1) << sh0,
+//                            the last one ends at CK0 - 1;
+//   positive side [CK0, p2]: bins n0 .. n0+n1-1, bin n0 + j = s1 + [j, j+1) << sh1,
+//                            the first one starts at CK0 (the penalty point's key).
+// Bin indices are computed without branches on the key (no divergence).
+struct BinMap {
+    uint32_t p1, p2, s1;
+    int sh0, sh1, n0, n1;
+    bool cross;
+
+    // fewest shift with at most maxbins bins over len keys
+    static __device__ __forceinline__ int shift_for(uint32_t len, int maxbins) {
+        int s = 0;
+        while (((len - 1u) >> s) >= (uint32_t)maxbins) ++s;
+        return s;
+    }
+    __device__ void init(uint32_t P1, uint32_t P2, int xb) {
+        p1 = P1;
+        p2 = P2;
+        constexpr uint32_t WING = 31u << 21;  // 7.75 binades of keys
+        cross = P1 < CK0 && CK0 <= P2 && (P2 - P1) > 2u * WING;
+        if (!cross) {
+            const uint32_t span = P2 - P1;
+            sh0 = span >= (uint32_t)xb ? (32 - __clz((int)span)) - 6 : 0;
+            n0 = (int)(span >> sh0) + 1;
+            n1 = 0;
+            sh1 = 0;
+            s1 = P2;
+            return;
+        }
+        const int wb = xb / 2;  // bins per side
+        // negative side: the wing starts at p1; its last bin reaches CK0 - 1
+        const uint32_t len0 = (CK0 - P1) < WING ? CK0 - P1 : WING;
+        sh0 = shift_for(len0, wb);
+        n0 = (int)((len0 - 1u) >> sh0) + 1;
+        // positive side: the wing ends at p2; its first bin starts at CK0
+        const uint32_t len1 = (P2 - CK0 + 1u) < WING ? P2 - CK0 + 1u : WING;
+        sh1 = shift_for(len1, wb);
+        n1 = (int)((len1 - 1u) >> sh1) + 1;
+        s1 = P2 - ((uint32_t)n1 << sh1) + 1u;  // bins n0 + j start at s1 + j << sh1 (j >= 1)
+    }
+    __device__ __forceinline__ int nbins() const { return n0 + n1; }
+    // kk in [p1, p2]
+    __device__ __forceinline__ int bin(uint32_t kk) const {
+        if (!cross) return (int)((kk - p1) >> sh0);
+        const int bneg = min((int)((kk - p1) >> sh0), n0 - 1);
+        const uint32_t kp = kk > s1 ? kk : s1;
+        const int bpos = n0 + min((int)((kp - s1) >> sh1), n1 - 1);
+        return kk < CK0 ? bneg : bpos;
+    }
+    __device__ __forceinline__ uint32_t lower(int b) const {
+        if (!cross) return p1 + ((uint32_t)b << sh0);
+        if (b < n0) return p1 + ((uint32_t)b << sh0);
+        if (b == n0) return CK0;
+        return s1 + ((uint32_t)(b - n0) << sh1);
+    }
+    __device__ __forceinline__ uint32_t upper(int b) const {
+        if (!cross || b < n0 - 1 || b >= n0) {
+            const uint64_t v = b < n0 ? (uint64_t)p1 + ((uint64_t)(b + 1) << sh0) - 1u
+                                      : (uint64_t)s1 + ((uint64_t)(b - n0 + 1) << sh1) - 1u;
+            return v > p2 ? p2 : (uint32_t)v;
+        }
+        return CK0 - 1u;  // the last negative bin
+    }
+};
+
+// hist_cross over the bins of a BinMap (at most XB of them).
+__device__ __forceinline__ int hist_cross_map(const uint32_t *h, const BinMap &bm, int64_t Sbase,
+                                              const Decide &dc, int64_t *below, int lane) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int nbins = bm.nbins();
+    const int b0 = 2 * lane, b1 = 2 * lane + 1;
+    const int64_t s0 = b0 < nbins ? hist_get(h, b0) : 0;
+    const int64_t s1 = b1 < nbins ? hist_get(h, b1) : 0;
+    const int64_t incl = warp_scan_add(s0 + s1, lane);
+    const int64_t ex = incl - s0 - s1;
+    const int c0 = b0 < nbins ? dc.cond(Sbase + ex + s0, bm.upper(b0) >= CK0) : 0;
+    const int c1 = b1 < nbins ? dc.cond(Sbase + ex + s0 + s1, bm.upper(b1) >= CK0) : 0;
+    const unsigned m0 = __ballot_sync(FULL, c0 != 0), m1 = __ballot_sync(FULL, c1 != 0);
+    const unsigned any = m0 | m1;
+    if (!any) return -1;
+    const int ln = __ffs(any) - 1;
+    const bool first_is_b0 = (m0 >> ln) & 1u;
+    const int bsel = 2 * ln + (first_is_b0 ? 0 : 1);
+    const int csel = __shfl_sync(FULL, first_is_b0 ? c0 : c1, ln);
+    const int64_t bel = __shfl_sync(FULL, first_is_b0 ? ex : ex + s0, ln);
+    if (csel < 0) return -2;
+    *below = Sbase + bel;
+    return bsel;
+}
+
 // ---------------------------------------------------------------------------
 // Weighted median of one pair.  Returns SEL_* and the exact key in tstar.
 //
@@ -478,12 +576,11 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             count_pass = true;
             continue;
         }
-        // exact histogram of the candidates over [P1, P2]; rows near P1, P2 or a
-        // bin edge are divided exactly first; Sb2 = exact weight below P1
-        const uint32_t span = P2 - P1;
-        const int sh = span >= (uint32_t)XB ? (32 - __clz((int)span)) - 6 : 0;
-        const uint32_t bmask = (1u << sh) - 1u;
-        const int nbins = (int)(span >> sh) + 1;
+        // exact histogram of the candidates over the bins of [P1, P2]; rows
+        // within G of P1, P2 or their bin's edges are divided exactly first;
+        // Sb2 = exact weight below P1
+        BinMap bm;
+        bm.init(P1, P2, XB);
         const uint32_t g1 = sat_add(P1, G), g2 = sat_sub(P2, G);
         hist_zero(hist, lane);
         __syncwarp();
@@ -493,8 +590,8 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             const int p = j * 32 + lane;
             uint32_t kk = lk[p];
             const uint16_t id = li[p];
-            const uint32_t off = (kk - P1) & bmask;
-            const bool clear = kk >= g1 && kk <= g2 && off >= G && off + G <= bmask;
+            // clear: the keys G either side fall in the same bin
+            const bool clear = kk >= g1 && kk <= g2 && bm.bin(kk - G) == bm.bin(kk + G);
             if (!clear) {
                 kk = A::exact_ck(xk[id], colb[id]);
                 lk[p] = kk;
@@ -504,7 +601,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             if (kk < P1)
                 Sb2 += q;
             else if (kk <= P2)
-                hist_add(hist, (int)((kk - P1) >> sh), q);
+                hist_add(hist, bm.bin(kk), q);
         }
         Sb += warp_sum_i64(Sb2);
         __syncwarp();
@@ -518,7 +615,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             continue;
         }
         int64_t below = 0;
-        const int bs = hist_cross(hist, nbins, P1, P2, sh, Sb, dc, &below, lane);
+        const int bs = hist_cross_map(hist, bm, Sb, dc, &below, lane);
         __syncwarp();
         if (bs == -2) return SEL_SLOW_BAND;
         if (bs < 0) {  // median above P2: retry over P2
@@ -530,8 +627,8 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             continue;
         }
         // the median is in bin bs: keep its candidates (lane-local, in place)
-        const uint32_t K1 = P1 + ((uint32_t)bs << sh);
-        const uint32_t K2 = min(P2, K1 + bmask);
+        const uint32_t K1 = bm.lower(bs);
+        const uint32_t K2 = bm.upper(bs);
         int w = 0;
 #pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
