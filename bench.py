@@ -77,7 +77,7 @@ def _src_hash() -> str:
     """Hash of the pair kernel's code (comments and whitespace stripped, so a
     comment edit does not orphan the committed ncu summaries)."""
     h = hashlib.sha256()
-    for f in ("k_pairs.cu", "pairs.cuh", "common.cuh"):
+    for f in ("k_pairs.cu", "pairs.cuh", "common.cuh", "binmap.cuh"):
         src = open(os.path.join(ROOT, "paper_2402_16712_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
