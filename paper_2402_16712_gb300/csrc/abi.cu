@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "../../include/l1line.h"
+#include "batch_split.h"
 #include "common.cuh"
 #include "launch.h"
 
@@ -822,10 +823,10 @@ struct BatchShape {
 // class's largest n: a few large instances otherwise set the occupancy of
 // every small one.  Cost model: a class takes (its pair-rows, the sum of
 // n m^2 nl) / (resident warps of its plan).  Classes are runs of the instances
-// ordered by n (cuts only where n changes); the best split into k classes is
-// found by dynamic programming for each k.  Unless the tuning fixes k, the
-// planner adds a class while the model puts it at least 5% below the best
-// with one class fewer.  Reorders `order`
+// ordered by n (cuts only where n changes); best_split (batch_split.h) finds
+// the best split into k classes by dynamic programming for each k.  Unless
+// the tuning fixes k, the planner adds a class while the model puts it at
+// least 5% below the best with one class fewer.  Reorders `order`
 // (stably, so largest work first within a class) and returns the instance
 // count of each class, largest n first.
 template <typename T>
@@ -844,40 +845,14 @@ std::vector<int64_t> batch_classes(int64_t batch, const int64_t *ns, const int64
             rate[p] = (double)pl.warps * (double)pl.ctas;  // 0 marks no cut here
         }
     }
-    // g[k][p]: the least modelled time of instances [p, B) in k + 1 classes
-    // starting at p; nxt[k][p]: where the second of them starts.
-    const double INF = std::numeric_limits<double>::infinity();
-    std::vector<std::vector<double>> g(MAX_BATCH_CLASSES, std::vector<double>(B + 1, INF));
-    std::vector<std::vector<size_t>> nxt(MAX_BATCH_CLASSES, std::vector<size_t>(B + 1, B));
-    for (size_t p = 0; p < B; ++p)
-        if (rate[p] > 0.0) g[0][p] = (S[B] - S[p]) / rate[p];
-    for (int k = 1; k < MAX_BATCH_CLASSES; ++k)
-        for (size_t p = 0; p < B; ++p) {
-            if (rate[p] <= 0.0) continue;
-            for (size_t q = p + 1; q < B; ++q) {
-                if (g[k - 1][q] == INF) continue;
-                const double t = (S[q] - S[p]) / rate[p] + g[k - 1][q];
-                if (t < g[k][p]) {
-                    g[k][p] = t;
-                    nxt[k][p] = q;
-                }
-            }
-        }
-    int k = 0;
-    if (tb.batch_classes > 0) {
-        for (int kk = tb.batch_classes - 1; kk >= 0 && k == 0; --kk)
-            if (g[kk][0] < INF) k = kk;  // fewer when n takes fewer distinct values
-    } else {
-        for (int kk = 1; kk < MAX_BATCH_CLASSES; ++kk)
-            if (g[kk][0] < 0.95 * g[k][0]) k = kk;
-    }
+    const std::vector<size_t> starts =
+        best_split(S, rate, MAX_BATCH_CLASSES, tb.batch_classes, 0.05);
     std::vector<int64_t> counts;
     std::vector<int> cls((size_t)batch, 0);
-    for (size_t p = 0; k >= 0; --k) {
-        const size_t q = k > 0 ? nxt[k][p] : B;
-        for (size_t r = p; r < q; ++r) cls[(size_t)byn[r]] = (int)counts.size();
+    for (size_t i = 0; i < starts.size(); ++i) {
+        const size_t p = starts[i], q = i + 1 < starts.size() ? starts[i + 1] : B;
+        for (size_t r = p; r < q; ++r) cls[(size_t)byn[r]] = (int)i;
         counts.push_back((int64_t)(q - p));
-        p = q;
     }
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return cls[(size_t)x] < cls[(size_t)y]; });
