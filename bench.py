@@ -152,11 +152,21 @@ class Clocks:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def _host_cores() -> int:
+    """Host cores this process may run on.  Not OpenMP's default team size:
+    torchrun sets OMP_NUM_THREADS=1 for every rank, while the oracle timings
+    run on rank 0 alone and use all the cores."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(X, lam, target_s=12.0):
     """The oracle as it stands on the host cores, on a bounded sample: the first
     J jhat columns (all k), J grown until the run takes a few seconds."""
     import oracle
-    nth = oracle.max_threads()
+    nth = _host_cores()
     J = max(1, nth)
     while True:
         t0 = time.perf_counter()
@@ -180,7 +190,7 @@ def run_reference(args):
     import oracle
     X, lams, _ = datagen.paper_size("float32")
     lam = float(lams[0])
-    nth = oracle.max_threads()
+    nth = _host_cores()
     m = X.shape[1]
     # each step: a sample of jhat columns sized to a couple of seconds
     J = nth

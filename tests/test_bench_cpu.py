@@ -31,3 +31,35 @@ def test_roofline_names_the_timed_placement_and_binding_l2():
     assert r["bound"] == "l2" and r["kernel"] == "k_pairs<float, 0, 0>"
     assert r["achieved"] == pytest.approx(1.999e8 * 4 * 2000 * 1.001 / 1e9)
     assert r["traffic"] == 1.7e7
+
+
+def _free_port():
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def test_reference_arm_under_two_ranks_prints_one_line_on_all_cores():
+    """The oracle arm launched like the multi-GPU bench: rank 0 alone times the
+    oracle, on every host core although torchrun sets OMP_NUM_THREADS=1, and
+    prints the one JSON line; the other rank exits 0 without work."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
+    lines = [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+    assert len(lines) == 1
+    line = lines[0]
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    assert line["cpu_baseline"]["cores"] == bench._host_cores()
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
