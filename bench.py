@@ -107,33 +107,15 @@ class Clocks:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
-        self.index = self.select(index)
+        self.index = index
         self.proc = None
-
-    @staticmethod
-    def select(index: int, run=subprocess.run) -> str:
-        """nvidia-smi's id for CUDA device `index`: its UUID when nvidia-smi
-        knows it (CUDA's numbering differs from nvidia-smi's under
-        CUDA_VISIBLE_DEVICES), else the index itself."""
-        try:
-            import torch
-            u = str(torch.cuda.get_device_properties(index).uuid)
-            if not u.startswith(("GPU-", "MIG-")):
-                u = "GPU-" + u
-            r = run(["nvidia-smi", "-i", u, "--query-gpu=uuid", "--format=csv,noheader"],
-                    capture_output=True, text=True, timeout=20)
-            if r.returncode == 0 and r.stdout.strip().lower() == u.lower():
-                return u
-        except Exception:
-            pass
-        return str(index)
         self.path = f"/tmp/l1line_clocks_{os.getpid()}.csv"
 
     def start(self):
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", self.index, f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:

@@ -63,43 +63,3 @@ def test_reference_arm_under_two_ranks_prints_one_line_on_all_cores():
     assert line["cpu_baseline"]["cores"] == bench._host_cores()
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
-
-
-class _Props:
-    uuid = "0a1b2c3d-0000-1111-2222-333344445555"
-
-
-class _Done:
-    def __init__(self, rc, out):
-        self.returncode, self.stdout = rc, out
-
-
-def test_clock_sampler_selects_the_gpu_by_uuid(monkeypatch):
-    import torch
-
-    import bench
-    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: _Props())
-    want = "GPU-" + _Props.uuid
-    seen = []
-
-    def smi_knows(cmd, **kw):
-        seen.append(cmd)
-        return _Done(0, want.upper() + "\n")
-
-    assert bench.Clocks.select(3, run=smi_knows) == want
-    assert seen[0][:3] == ["nvidia-smi", "-i", want]
-    # nvidia-smi does not know the UUID, or fails: the CUDA index
-    assert bench.Clocks.select(3, run=lambda c, **k: _Done(6, "")) == "3"
-    assert bench.Clocks.select(3, run=lambda c, **k: _Done(0, "GPU-other\n")) == "3"
-
-
-def test_clock_sampler_falls_back_to_the_index_without_a_device(monkeypatch):
-    import torch
-
-    import bench
-
-    def no_device(i):
-        raise RuntimeError("no CUDA device")
-
-    monkeypatch.setattr(torch.cuda, "get_device_properties", no_device)
-    assert bench.Clocks.select(1, run=lambda c, **k: _Done(0, "")) == "1"
