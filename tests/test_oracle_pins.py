@@ -244,6 +244,50 @@ def test_large_lambda_closed_form(dtype):
         assert abs(r["obj"][t] - want) <= 1e-12 * want
 
 
+
+LAMBDA_GRID = [0.0, 0.05, 0.3, 1.0, 2.5, 7.0, 40.0, 1e4]
+
+
+def _sandwich(z_all, v_all, lams):
+    """Largest violation, over jhat and lambda pairs, of the two bounds that
+    make z_jhat(lambda) = min_v [sum_ik |x_ik - v_k x_ijhat| + lambda ||v||_1]
+    concave in lambda with supergradient ||v(lambda)||_1 (the objective of
+    Algorithm 1 per jhat; v_jhat = 1 is part of ||v||_1):
+        z(b) <= z(a) + (b - a) ||v(a)||_1    (v(a) is feasible at b)
+        z(b) >= z(a) + (b - a) ||v(b)||_1    (v(b) is feasible at a)
+    in units of the objective's scale."""
+    P = np.abs(v_all.astype(np.float64)).sum(axis=2)  # [lambda, jhat]
+    worst = 0.0
+    for a in range(len(lams)):
+        for b in range(a + 1, len(lams)):
+            d = lams[b] - lams[a]
+            scale = np.abs(z_all[a]) + np.abs(z_all[b]) + d * (P[a] + P[b])
+            up = z_all[b] - (z_all[a] + d * P[a])
+            lo = (z_all[a] + d * P[b]) - z_all[b]
+            worst = max(worst, float(np.max(np.maximum(up, lo) / scale)))
+    return worst
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_objective_is_concave_in_lambda_with_norm_supergradient(dtype):
+    """Per jhat, the oracle's z and v over a lambda grid satisfy both
+    feasibility bounds above (Lemma 1 optimality per k, the penalty term and
+    v_jhat = 1 of the objective all enter), ||v||_1 never grows with lambda,
+    and no z exceeds that of v = e_jhat, feasible at every lambda:
+    sum_{k != jhat} ||x_k||_1 + lambda."""
+    X, _, _ = datagen.planted(datagen.Planted(40, 7, 3, 0.1, 0.15, 5.0, 23,
+                                              np.dtype(dtype).name))
+    r = oracle.fit(X, LAMBDA_GRID)
+    m = X.shape[1]
+    assert np.array_equal(r["v_all"][:, np.arange(m), np.arange(m)], np.ones((len(LAMBDA_GRID), m)))
+    assert _sandwich(r["z_all"], r["v_all"], LAMBDA_GRID) <= 1e-12
+    P = np.abs(r["v_all"].astype(np.float64)).sum(axis=2)
+    assert (np.diff(P, axis=0) <= 1e-12 * P[:-1]).all()
+    col = np.abs(X.astype(np.float64)).sum(axis=0)
+    for t, lam in enumerate(LAMBDA_GRID):
+        e_obj = col.sum() - col + lam
+        assert (r["z_all"][t] <= e_obj * (1 + 1e-12)).all(), (lam, r["z_all"][t] - e_obj)
+
 def test_single_coordinate_and_zero_column():
     X = np.array([[1.5], [-2.0], [0.25]])
     r = oracle.fit(X, [0.0, 0.7])
