@@ -72,3 +72,25 @@ def test_prototype_types_match_the_binding(name):
     assert _same(want_ret, res), (name, ret, res)
     for p, a in zip(params, argtypes):
         assert _same(_ctype_of(p), a), (name, p, a)
+
+
+def test_header_compiles_as_plain_c(tmp_path):
+    """C callers include the header directly: it must be C99 (no C++-only
+    constructs) and warning-free under -pedantic."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "l1line.h"\n'
+                   "int main(void) {\n"
+                   "    l1line_tuning t = {1, 2, 3, 4, 0, 1};\n"
+                   "    int (*fit)(const float *, int64_t, int64_t, const double *, int64_t,\n"
+                   "               float *, double *, int32_t *, void *, size_t, void *) =\n"
+                   "        l1line_fit_f32;\n"
+                   "    return (fit != 0 && t.warps == 1) ? 0 : 1;\n"
+                   "}\n")
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(ROOT, "include"), "-c", str(src), "-o",
+                    str(tmp_path / "use_header.o")], check=True)
