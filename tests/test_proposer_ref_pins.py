@@ -86,6 +86,43 @@ def test_adam_first_step_is_signed_learning_rate():
     assert np.allclose(m1, 0.1 * g) and np.allclose(m2, 0.001 * g * g)
 
 
+
+def test_adam_first_step_with_epsilon_outside_the_root():
+    """Adam (Kingma & Ba) divides by sqrt(v_hat) + eps; at step 1 the bias
+    corrections give m_hat = g and v_hat = g^2, so the step is exactly
+    -lr g / (|g| + eps), which for |g| near eps is far from -lr sign(g)."""
+    g = np.array([1e-6, -3e-8, 0.0, 2.0, -1e-9])
+    th = np.zeros(5)
+    t1, _, _ = P.adam(th, g, np.zeros(5), np.zeros(5), 1, 0.01, eps=1e-8)
+    want = -0.01 * g / (np.abs(g) + 1e-8)
+    assert np.allclose(t1, want, rtol=1e-12, atol=0)
+    assert abs(t1[0] + 0.01 / 1.01) < 1e-15  # 1e-6 / (1e-6 + 1e-8) = 1 / 1.01
+
+
+def test_relu_derivative_at_zero_is_zero():
+    """A hidden unit whose pre-activation is exactly 0 (zero weights and bias)
+    passes no gradient: ReLU'(0) = 0, so its incoming weights and bias get 0
+    while its outgoing weight w3 still sees h2 = 0."""
+    rng = np.random.default_rng(7)
+    W1, b1, W2, b2, w3, b3 = P.unpack(_theta(3))
+    u = 5
+    W2 = W2.copy(); b2 = b2.copy(); w3 = w3.copy()
+    W2[u, :] = 0.0
+    b2[u] = 0.0
+    w3[u] = 1.5
+    th = P.pack(W1, b1, W2, b2, w3, b3)
+    F = rng.normal(size=(6, 3))
+    ds = rng.normal(size=6)
+    _, (a1, h1, a2, h2) = P.forward(th, F, keep=True)
+    assert (a2[:, u] == 0.0).all()
+    dW1, db1, dW2, db2, dw3, db3 = P.unpack(P.backward(th, F, ds))
+    assert (dW2[u, :] == 0.0).all() and db2[u] == 0.0
+    assert dw3[u] == 0.0  # h2[:, u] = relu(0) = 0
+    # the other units are untouched by unit u: their layer-2 gradients are the
+    # closed form g2 = ds w3 [a2 > 0]
+    g2 = np.outer(ds, w3) * (a2 > 0)
+    assert np.allclose(db2, g2.sum(axis=0), rtol=1e-13, atol=1e-15)
+
 def test_raw_features_hand_values():
     X = np.array([[3.0, 0.0, -1.0],
                   [-4.0, 0.0, 2.0],
