@@ -58,12 +58,18 @@ def _check_against_alg1(X, extra):
         zq = float(zi) + float(sl) * q
         assert abs(zq - ref["obj"][0]) <= 1e-12 * max(1.0, abs(ref["obj"][0])), (q, zq, ref["obj"])
         jr = int(ref["jstar"][0])
-        if j != jr:  # only on an exact tie of objectives
-            assert abs(ref["z_all"][0][j] - ref["z_all"][0][jr]) <= 1e-12 * abs(ref["obj"][0])
+        if j != jr:
+            # only on a near-tie from rounding: objectives equal in double mean
+            # identical lines, which the smallest jhat names (Algorithm 1's
+            # strict argmin), so an exact tie must give the same jhat
+            zj, zr = ref["z_all"][0][j], ref["z_all"][0][jr]
+            assert zj != zr and abs(zj - zr) <= 1e-12 * abs(ref["obj"][0]), (q, j, jr, zj, zr)
         assert np.array_equal(np.array(v), ref["v_all"][0][j].astype(np.float64)), (q, j)
 
 
-@pytest.mark.parametrize("seed", [0, 1, 2])
+# seeds 51 and 58 give lines of two intervals that start at the same lambda
+# (a crossing on a breakpoint): the one that holds after it must be kept
+@pytest.mark.parametrize("seed", [0, 1, 2, 51, 58])
 def test_solution_path_equals_algorithm1_on_integers(seed):
     X = datagen.small_integers(9, 5, seed, lo=-5, hi=5, zero_frac=0.2, dtype="float64")
     _check_against_alg1(X, np.linspace(0.0, 30.0, 13))
