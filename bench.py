@@ -177,8 +177,15 @@ def cpu_baseline(X, lam, target_s=12.0):
         J = min(X.shape[1], int(J * max(2.0, target_s / 4 / max(dt, 1e-3))))
     m = X.shape[1]
     pairs = J * (m - 1)
+    # the same oracle on one core, on a sample of about the same duration
+    J1 = max(1, J // nth)
+    t0 = time.perf_counter()
+    oracle.fit(X, [lam], jlist=list(range(J1)), nthreads=1, want_all=False)
+    dt1 = time.perf_counter() - t0
     return {"value": pairs / dt, "unit": UNIT, "cores": nth, "kind": "oracle",
             "sample": f"{J} of {m} jhat columns x all {m - 1} k (one lambda), {dt:.2f} s",
+            "single_core": {"value": J1 * (m - 1) / dt1, "unit": UNIT, "cores": 1,
+                            "sample": f"{J1} of {m} jhat columns x all {m - 1} k, {dt1:.2f} s"},
             "seconds": dt, "fits_per_s": (pairs / dt) / (m * (m - 1))}
 
 
@@ -380,7 +387,8 @@ def run_gpu(args):
     line.update(extras)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_baseline(X, float(lams[0])).items()
-                                if k in ("value", "unit", "cores", "kind", "sample")}
+                                if k in ("value", "unit", "cores", "kind", "sample",
+                                         "single_core")}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

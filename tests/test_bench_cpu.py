@@ -63,3 +63,15 @@ def test_reference_arm_under_two_ranks_prints_one_line_on_all_cores():
     assert line["cpu_baseline"]["cores"] == bench._host_cores()
     assert line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def test_cpu_baseline_reports_all_cores_and_one():
+    import numpy as np
+
+    import bench
+    X = np.random.default_rng(0).normal(size=(300, 60)).astype(np.float32)
+    r = bench.cpu_baseline(X, 0.5, target_s=0.2)
+    assert r["kind"] == "oracle" and r["unit"] == "pairs/s" and r["value"] > 0
+    assert r["cores"] == bench._host_cores()
+    one = r["single_core"]
+    assert one["cores"] == 1 and one["value"] > 0 and "jhat columns" in one["sample"]
