@@ -288,6 +288,28 @@ def test_objective_is_concave_in_lambda_with_norm_supergradient(dtype):
         e_obj = col.sum() - col + lam
         assert (r["z_all"][t] <= e_obj * (1 + 1e-12)).all(), (lam, r["z_all"][t] - e_obj)
 
+
+def test_copies_of_the_preserved_column_closed_form():
+    """Columns k that are c times column jhat have every ratio equal to c with
+    weight |x_ijhat|, plus the penalty point (0, lambda).  With S = ||x_jhat||_1
+    the weighted median's right end point is c while lambda <= S when c > 0
+    (the cumulative weight at 0 is lambda, at most half of S + lambda), but
+    only while lambda < S when c < 0 (at lambda = S the cumulative weight at c
+    is exactly half, so the scan moves on to 0): Lemma 1's strict test."""
+    base = np.array([3.0, -1.0, 0.0, 2.0, -4.0, 0.0, 1.0])
+    other = np.array([1.0, 2.0, -3.0, 0.0, 5.0, -1.0, 2.0])
+    X = np.stack([base, base, -base, 2.0 * base, -0.5 * base, other], axis=1)
+    S = float(np.abs(base).sum())
+    lams = [0.0, S - 0.5, S, S + 0.5]
+    r = oracle.fit(X, lams)
+    for t, lam in enumerate(lams):
+        v = r["v_all"][t, 0]
+        assert v[0] == 1.0
+        assert v[1] == (1.0 if lam <= S else 0.0), (lam, v)
+        assert v[2] == (-1.0 if lam < S else 0.0), (lam, v)
+        assert v[3] == (2.0 if lam <= S else 0.0), (lam, v)
+        assert v[4] == (-0.5 if lam < S else 0.0), (lam, v)
+
 def test_single_coordinate_and_zero_column():
     X = np.array([[1.5], [-2.0], [0.25]])
     r = oracle.fit(X, [0.0, 0.7])
