@@ -151,3 +151,23 @@ def test_breakpoint_lambdas_in_exact_rationals(seed):
             assert len(got) == len(ex), (j, k, got, ex)
             for (gl, gv), (el, ev) in zip(got, ex):
                 assert gv == float(ev) and gl == float(max(el, Fraction(0))), (j, k, got, ex)
+
+
+@pytest.mark.parametrize("c", [1.0, -1.0, 2.0, -0.5, 0.25])
+def test_path_of_a_copy_of_the_preserved_column(c):
+    """Column k = c x column jhat: every ratio is c with weight |x_ijhat|, so
+    v_k is c until the penalty weight lambda reaches S = ||x_jhat||_1 and 0
+    from there on: the path is (0, c), (S, 0) for either sign (at lambda = S
+    itself the strict test keeps c > 0 and gives 0 for c < 0, the path's
+    breakpoint convention).  Rows with x_ijhat = 0 change nothing."""
+    base = np.array([3.0, -1.0, 0.0, 2.0, -4.0, 0.0, 1.0])
+    X = np.stack([base, c * base, np.ones(7)], axis=1)
+    lam, v = oracle.path(X, 0, 1)
+    S = float(np.abs(base).sum())
+    assert list(lam) == [0.0, S] and list(v) == [c, 0.0], (lam, v)
+    # the column of ones: ratios 1/x_i0 (the sign of x_i0) with weights
+    # |x_i0|; with no zero ratio, v_k is 0 exactly when the penalty point's
+    # weight outweighs the difference of the two sides: lambda_max = |P - N|
+    lam1, v1 = oracle.path(X, 0, 2)
+    P, N = base[base > 0].sum(), -base[base < 0].sum()
+    assert v1[-1] == 0.0 and lam1[0] == 0.0 and lam1[-1] == abs(P - N), (lam1, v1)
