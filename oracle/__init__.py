@@ -1,7 +1,8 @@
 """CPU oracle for the l1-regularised l1 best-fit line (Ling & Brooks, arXiv 2402.16712).
 
-TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  The product path
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()``, and the
+CPU-baseline leg and ``--impl reference`` arm of ``bench.py`` may import this
+package (``__graft_entry__.build()`` compiles it).  The product path
 (the CUDA library and its binding) never touches it, and it shares no code with
 that path.
 
