@@ -584,7 +584,50 @@ def measure_extras(dev, stream, flush):
     del Xs, bat, g
     out["small_fit"] = measure_small_fit(dev, stream)
     out["learned_topk"] = measure_learned(dev, stream, flush)
+    try:
+        out["comparison_suite"] = measure_comparison(dev, stream, flush)
+    except Exception as e:  # a context line only: never costs the headline
+        out["comparison_suite"] = {"error": f"{type(e).__name__}: {e}"}
     return out
+
+
+def measure_comparison(dev, stream, flush, steps=5):
+    """The comparison experiment's data (30 float64 datasets of 100 x 100,
+    five seeds per outlier count 1..6) with a sparsity sweep of 8 lambdas
+    each, all in one batched call; CUDA events around each call, L2 flushed
+    before it."""
+    import numpy as np
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+
+    l1line.set_tuning(None)  # the planner's launch
+    Xs = datagen.comparison_suite("float64")
+    lam = np.array([0.0, 5.0, 20.0, 50.0, 100.0, 200.0, 400.0, 800.0])
+    bat = l1line.Batched([torch.from_numpy(X).to(dev) for X in Xs], [lam.copy() for _ in Xs],
+                         device=dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            bat.run(stream)
+        for a, b in ev:
+            flush.fill_(2)
+            a.record(stream)
+            bat.run(stream)
+            b.record(stream)
+    stream.synchronize()
+    if bat.status(stream) != l1line.OK:
+        raise RuntimeError("batched fit failed on the device")
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    fits = len(Xs) * lam.size
+    pairs = sum(X.shape[1] * (X.shape[1] - 1) for X in Xs) * lam.size
+    return {"workload": "the comparison experiment's data: 30 float64 datasets of 100 x 100 "
+                        "(five seeds per outlier count 1..6), 8 lambdas each, one batched "
+                        "call, L2 flushed",
+            "ms_per_step": ms, "fits_per_s": fits / (ms * 1e-3),
+            "pair_lambdas_per_s": pairs / (ms * 1e-3),
+            "gpu_launches_per_step": l1line.last_launch_count()}
 
 
 def measure_small_fit(dev, stream, replays=200):
