@@ -75,3 +75,62 @@ def test_cpu_baseline_reports_all_cores_and_one():
     assert r["cores"] == bench._host_cores()
     one = r["single_core"]
     assert one["cores"] == 1 and one["value"] > 0 and "jhat columns" in one["sample"]
+
+
+def test_comparison_line_host_logic(monkeypatch):
+    """measure_comparison's host code with the CUDA pieces faked: it builds
+    one batched call over the 30 datasets x 8 lambdas and reports rates from
+    the event times (an error there would only show as an 'error' entry in
+    the bench line, so it is checked here)."""
+    import contextlib
+
+    import torch
+
+    import bench
+    from paper_2402_16712_gb300 import l1line
+
+    calls = {"run": 0}
+
+    class FakeBatched:
+        def __init__(self, Xs, lams, device=None):
+            assert len(Xs) == 30 and all(tuple(X.shape) == (100, 100) for X in Xs)
+            assert all(list(lm) == [0.0, 5.0, 20.0, 50.0, 100.0, 200.0, 400.0, 800.0]
+                       for lm in lams)
+
+        def run(self, stream=None):
+            calls["run"] += 1
+
+        def status(self, stream=None):
+            return l1line.OK
+
+    class FakeEvent:
+        n = 0
+
+        def __init__(self, enable_timing=False):
+            FakeEvent.n += 1
+            self.t = FakeEvent.n
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 2.0  # ms
+
+    class Fill:
+        def fill_(self, v):
+            pass
+
+    class Stream:
+        def synchronize(self):
+            pass
+
+    monkeypatch.setattr(l1line, "Batched", FakeBatched)
+    monkeypatch.setattr(l1line, "set_tuning", lambda t=None: None)
+    monkeypatch.setattr(l1line, "last_launch_count", lambda: 8)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    r = bench.measure_comparison("cpu", Stream(), Fill(), steps=5)
+    assert calls["run"] == 3 + 5
+    assert r["ms_per_step"] == 2.0 and r["gpu_launches_per_step"] == 8
+    assert r["fits_per_s"] == 240 / 2e-3
+    assert r["pair_lambdas_per_s"] == 30 * 100 * 99 * 8 / 2e-3
