@@ -584,11 +584,48 @@ def measure_extras(dev, stream, flush):
     del Xs, bat, g
     out["small_fit"] = measure_small_fit(dev, stream)
     out["learned_topk"] = measure_learned(dev, stream, flush)
-    try:
-        out["comparison_suite"] = measure_comparison(dev, stream, flush)
-    except Exception as e:  # a context line only: never costs the headline
-        out["comparison_suite"] = {"error": f"{type(e).__name__}: {e}"}
+    for key, fn in (("comparison_suite", measure_comparison), ("components", measure_components)):
+        try:
+            out[key] = fn(dev, stream, flush)
+        except Exception as e:  # context lines only: never cost the headline
+            out[key] = {"error": f"{type(e).__name__}: {e}"}
     return out
+
+
+def measure_components(dev, stream, flush, ncomp=3, steps=5):
+    """Successive components: ncomp fits of the 1000 x 500 float32 lambda-path
+    matrix at lambda = 0.5, each on the previous residual x_i - x_ijhat v (one
+    library call; CUDA events around each call, L2 flushed before it)."""
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+
+    l1line.set_tuning(None)  # the planner's launch
+    X, _, _ = datagen.lambda_path("float32")
+    Xd = torch.from_numpy(X).to(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        _, _, _, ws = l1line.components(Xd, 0.5, ncomp, stream=stream)
+        for _ in range(2):
+            l1line.components(Xd, 0.5, ncomp, workspace=ws, stream=stream)
+        for a, b in ev:
+            flush.fill_(3)
+            a.record(stream)
+            _, _, js, _ = l1line.components(Xd, 0.5, ncomp, workspace=ws, stream=stream)
+            b.record(stream)
+    stream.synchronize()
+    if l1line.status(ws, stream) != l1line.OK:
+        raise RuntimeError("components failed on the device")
+    ms = statistics.median(a.elapsed_time(b) for a, b in ev)
+    n, m = X.shape
+    return {"workload": f"{ncomp} successive components of the n={n}, m={m} float32 "
+                        "lambda-path matrix at lambda=0.5 (fit, deflate, repeat), one library "
+                        "call, L2 flushed",
+            "ms_per_step": ms, "components_per_s": ncomp / (ms * 1e-3),
+            "pairs_per_s": ncomp * m * (m - 1) / (ms * 1e-3),
+            "jhat_star": [int(j) for j in js.tolist()],
+            "gpu_launches_per_step": l1line.last_launch_count()}
 
 
 def measure_comparison(dev, stream, flush, steps=5):

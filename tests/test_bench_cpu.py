@@ -134,3 +134,52 @@ def test_comparison_line_host_logic(monkeypatch):
     assert r["ms_per_step"] == 2.0 and r["gpu_launches_per_step"] == 8
     assert r["fits_per_s"] == 240 / 2e-3
     assert r["pair_lambdas_per_s"] == 30 * 100 * 99 * 8 / 2e-3
+
+
+def test_components_line_host_logic(monkeypatch):
+    """measure_components' host code with the CUDA pieces faked: one
+    workspace for every call, three components per call, rates from the event
+    times."""
+    import contextlib
+
+    import torch
+
+    import bench
+    from paper_2402_16712_gb300 import l1line
+
+    seen = []
+
+    def fake_components(X, lam, ncomp, workspace=None, stream=None):
+        assert tuple(X.shape) == (1000, 500) and lam == 0.5 and ncomp == 3
+        seen.append(workspace)
+        return None, None, torch.tensor([7, 3, 11], dtype=torch.int32), "ws"
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 4.0
+
+    class Fill:
+        def fill_(self, v):
+            pass
+
+    class Stream:
+        def synchronize(self):
+            pass
+
+    monkeypatch.setattr(l1line, "components", fake_components)
+    monkeypatch.setattr(l1line, "status", lambda ws, stream=None: l1line.OK)
+    monkeypatch.setattr(l1line, "set_tuning", lambda t=None: None)
+    monkeypatch.setattr(l1line, "last_launch_count", lambda: 17)
+    monkeypatch.setattr(torch.cuda, "Event", FakeEvent)
+    monkeypatch.setattr(torch.cuda, "stream", lambda s: contextlib.nullcontext())
+    r = bench.measure_components("cpu", Stream(), Fill(), ncomp=3, steps=5)
+    assert seen[0] is None and all(w == "ws" for w in seen[1:]) and len(seen) == 1 + 2 + 5
+    assert r["ms_per_step"] == 4.0 and r["components_per_s"] == 3 / 4e-3
+    assert r["pairs_per_s"] == 3 * 500 * 499 / 4e-3 and r["jhat_star"] == [7, 3, 11]
+    assert r["gpu_launches_per_step"] == 17
