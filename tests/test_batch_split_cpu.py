@@ -17,7 +17,7 @@ def test_split_matches_brute_force(tmp_path):
     if cxx is None:
         pytest.skip("no host C++ compiler")
     exe = str(tmp_path / "batch_split_check")
-    subprocess.run([cxx, "-O2", "-std=c++17",
+    subprocess.run([cxx, "-O2", "-std=c++17", "-Wall", "-Wextra", "-Werror",
                     os.path.join(HERE, "native", "batch_split_check.cpp"), "-o", exe],
                    check=True)
     r = subprocess.run([exe], capture_output=True, text=True)
