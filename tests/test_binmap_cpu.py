@@ -17,8 +17,8 @@ def test_bin_layout_tiles_every_bracket(tmp_path):
     if cxx is None:
         pytest.skip("no host C++ compiler")
     exe = str(tmp_path / "binmap_check")
-    subprocess.run([cxx, "-O2", "-std=c++17", "-Wall", "-Wextra", "-Werror", os.path.join(HERE, "native", "binmap_check.cpp"),
-                    "-o", exe], check=True)
+    subprocess.run([cxx, "-O2", "-std=c++17", "-Wall", "-Wextra", "-Werror",
+                    os.path.join(HERE, "native", "binmap_check.cpp"), "-o", exe], check=True)
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "failures 0" in r.stdout
