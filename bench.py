@@ -461,8 +461,10 @@ def _replay_ms(g, stream, steps, flush=None):
 
 
 def measure_extras(dev, stream, flush):
-    """The lambda-path and uneven-batch workloads, each captured once into a
-    CUDA graph and replayed (reported beside the headline, not in `value`)."""
+    """The other workloads, reported beside the headline (not in `value`):
+    the lambda batch and the uneven batch (each captured once into a CUDA graph
+    and replayed), Algorithms 2 and 3, the small fit, the learned proposer, the
+    comparison data and successive components."""
     import numpy as np
     import torch
 
@@ -780,7 +782,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the lambda-path and uneven-batch lines")
+                    help="only the headline line (skip the lambda-path, path, batch, small-fit, "
+                         "proposer, comparison and components lines)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run --fits plain fits of an n x m instance (for ncu), no timing")
     ap.add_argument("--n", type=int, default=N_ROWS)
