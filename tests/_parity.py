@@ -7,6 +7,7 @@ Bar (stated once, used by every parity test):
     input) or 1e-12 (float64 input), and atol = 8 u sum_k |v_k| sum_i |x_ijhat|,
     the size of the rounding of the products v_k x_ijhat that a near-perfect
     fit (residuals far below |x|) cannot hide; u = 2^-24 or 2^-53.
+  * s_jhat,k (every pair): the same bar term by term, atol = 8 u |v_k| sum_i |x_ijhat|.
   * jhat*: equal, or the two objectives tie within the z tolerance; v* is then
     the bit-exact v^jhat* of the index the GPU chose.
 """
@@ -72,12 +73,30 @@ def assert_z_close(X, zg, zr, v_all, where="", cols=None):
                              f"err={err[i]:.3e} lim={lim[i]:.3e}")
 
 
+def assert_s_close(X, sg, sr, vr, where="", cols=None):
+    """Per-pair residuals s_jhat,k (every entry): the z bar applied to one
+    term, |s_gpu - s_ref| <= rtol |s_ref| + 8 u |v_k| sum_i |x_ijhat|."""
+    X = np.asarray(X)
+    f32 = X.dtype == np.float32
+    u = 2.0 ** -24 if f32 else 2.0 ** -53
+    rtol = 1e-5 if f32 else 1e-12
+    col = np.abs(X.astype(np.float64)).sum(axis=0)
+    if cols is not None:
+        col = col[np.asarray(cols)]
+    lim = rtol * np.abs(sr) + 8.0 * u * np.abs(np.asarray(vr, dtype=np.float64)) * col[:, None]
+    err = np.abs(np.asarray(sg) - sr)
+    if not (err <= lim).all():
+        i = np.unravel_index(np.argmax(err - lim), err.shape)
+        raise AssertionError(f"{where}: s differs at {i}: gpu={sg[i]!r} ref={sr[i]!r} "
+                             f"err={err[i]:.3e} lim={lim[i]:.3e}")
+
+
 def check_scan(X, lams, flags=0, where=""):
     vg, sg, zg = gpu_scan(X, lams, flags)
     ref = oracle.fit(X, lams)
     assert_v_equal(vg, ref["v_all"], where + " v_all")
     assert_z_close(X, zg, ref["z_all"], ref["v_all"], where + " z_all")
-    assert_z_close(X, sg.sum(axis=-1), ref["s_all"].sum(axis=-1), ref["v_all"], where + " s_all")
+    assert_s_close(X, sg, ref["s_all"], ref["v_all"], where + " s_all")
     return vg, zg, ref
 
 
