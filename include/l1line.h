@@ -54,7 +54,8 @@ typedef enum {
     L1L_ERR_NONFINITE = -2,   /* X holds NaN or inf (reported by l1line_status)   */
     L1L_ERR_CUDA = -3,        /* a CUDA runtime call failed                        */
     L1L_ERR_WORKSPACE = -4,   /* workspace missing, too small or misaligned        */
-    L1L_ERR_TIMEOUT = -5,     /* a bounded device-side wait ran out                */
+    L1L_ERR_TIMEOUT = -5,     /* reserved: no kernel of this library waits on
+                                 another, so no call returns it                    */
     L1L_ERR_UNSUPPORTED = -6, /* size beyond what the kernels support (see below)  */
     L1L_ERR_INTERNAL = -7     /* a device-side invariant failed                    */
 } l1l_status;
@@ -69,7 +70,9 @@ enum {
 };
 
 /* Largest n (rows) the shared-memory pair kernels accept, per dtype.  Larger
- * n, m > 2^31 - 1 or n_lambda > 65535 return L1L_ERR_UNSUPPORTED. */
+ * n, m > 2^31 - 1, n_lambda > 65535, or m * m * min(n_lambda, 256) > 2^31
+ * (the exact path's pair list of one launch; m <= 46,340 for one lambda)
+ * return L1L_ERR_UNSUPPORTED. */
 int64_t l1line_max_rows(int dtype);
 
 /* Bytes of device workspace needed by l1line_scan_* and l1line_fit_* for the
@@ -368,8 +371,8 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
  * whose device memory is owned by its own allocator, a plugin given no access
  * to one, or a latency-critical loop that must not pay for the implicit
  * synchronisation of an allocation.  For them this entry point does what
- * l1line_fit_f32 does, with the same arguments, results and status codes, but
- * takes no workspace: it uses a fixed scratch array of
+ * l1line_fit_f32 does, with the same arguments and results, but takes no
+ * workspace: it uses a fixed scratch array of
  * L1L_NOALLOC_SCRATCH_BYTES that the library declares in device memory, which
  * every GPU that loads the library holds until the process exits.
  *  - Sizes whose workspace (l1line_workspace_bytes(L1L_DTYPE_F32, n, m,
@@ -382,8 +385,12 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
  *    calls that overlap on the GPU race and corrupt each other's results.
  *    Serialise them (one stream, or events).  Each call resets the parts of
  *    the scratch that must start at zero and overwrites the rest.
- *  - Device-side status (a non-finite X) is recorded in the scratch, which is
- *    not exposed; such input gives meaningless results.
+ *  - Its return value carries only the host-side codes (L1L_ERR_ARG,
+ *    L1L_ERR_UNSUPPORTED, L1L_ERR_CUDA, L1L_OK).  The device-side status of
+ *    l1line_fit_f32 (read by l1line_status) stays in the scratch, which is
+ *    not exposed, so L1L_ERR_NONFINITE is never reported: a NaN or infinity
+ *    in X returns L1L_OK with meaningless results.  Check X first where that
+ *    can happen.
  * X, out_v, out_obj and out_jstar are device pointers as for l1line_fit_f32;
  * lambdas is a host pointer.  Nothing is allocated or freed.
  */
@@ -394,8 +401,8 @@ int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m, const double *l
 
 /* Synchronise `stream` and return the device-side status recorded in the
  * workspace by the last call that used it (L1L_OK, L1L_ERR_NONFINITE,
- * L1L_ERR_TIMEOUT, L1L_ERR_INTERNAL, or L1L_ERR_ARG for a jhat list entry out
- * of range), or L1L_ERR_CUDA. */
+ * L1L_ERR_INTERNAL, or L1L_ERR_ARG for a jhat list entry out of range), or
+ * L1L_ERR_CUDA. */
 int l1line_status(void *workspace, void *stream);
 
 /* Human-readable text of a status code (static storage). */

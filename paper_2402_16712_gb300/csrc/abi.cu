@@ -50,7 +50,10 @@ bool make_layout(int dtype, int64_t n, int64_t m, int64_t nl, Layout &L) {
     if (!mul_ok(m, m, mm) || !mul_ok(mm, nl, pairs) || !mul_ok(m, ldn, xt)) return false;
     const int64_t nlc = nl < MAX_LAMBDA_PER_LAUNCH ? nl : MAX_LAMBDA_PER_LAUNCH;
     if (!mul_ok(mm, nlc, chunk_pairs)) return false;
-    if (pairs > INT64_MAX / 16 || xt > INT64_MAX / 16 || chunk_pairs > INT64_MAX / 32) return false;
+    if (pairs > INT64_MAX / 16 || xt > INT64_MAX / 16) return false;
+    // the exact path's list of one launch is counted by a uint32 (slow_count)
+    // and walked with a uint32 index: keep it far from wrapping
+    if (chunk_pairs > ((int64_t)1 << 31)) return false;
     size_t off = 0;
     L.status = off;
     off += 256;
@@ -882,7 +885,8 @@ int batch_shape(int dtype, int64_t batch, const int64_t *ns, const int64_t *ms,
         sh.multi = sh.multi || nl >= 3;
     }
     if (loff[batch] > MAX_BATCH_LAMBDAS) return L1L_ERR_UNSUPPORTED;
-    if (units > 0x7FFFFFFF || ztasks > 0x7FFFFFFF || pairs > ((int64_t)1 << 40))
+    // pairs bounds the exact path's list, counted by a uint32
+    if (units > 0x7FFFFFFF || ztasks > 0x7FFFFFFF || pairs > ((int64_t)1 << 31))
         return L1L_ERR_UNSUPPORTED;
     sh.ws_total = BATCH_HEAD + al256((size_t)pairs * sizeof(SlowEntry)) + regions;
     sh.order.resize((size_t)batch);

@@ -91,6 +91,17 @@ def test_argument_errors_return_before_launch(lib):
     assert lib.l1line_status(None, None) == l1line.ERR_WORKSPACE
 
 
+def test_exact_list_capacity_stays_within_its_uint32_counter(lib):
+    # one launch lists at most m * m * min(n_lambda, 256) pairs for the exact
+    # path; its counter is a uint32, so shapes past 2^31 entries are refused
+    assert lib.l1line_workspace_bytes(0, 10, 2048, 256) > 0        # 2^30 entries
+    assert lib.l1line_workspace_bytes(0, 10, 4096, 128) > 0        # 2^31 entries
+    assert lib.l1line_workspace_bytes(0, 10, 4096, 256) == 0       # 2^32 entries
+    assert lib.l1line_workspace_bytes(0, 10, 65536, 1) == 0        # 2^32 entries
+    assert lib.l1line_workspace_bytes(1, 10, 46341, 1) == 0
+    assert _scan(lib, m=65536) == l1line.ERR_UNSUPPORTED
+
+
 def test_binding_has_no_cpu_fallback(tmp_path):
     with pytest.raises(RuntimeError):
         saved = l1line._lib
