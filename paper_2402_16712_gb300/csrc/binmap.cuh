@@ -98,4 +98,77 @@ struct BinMap {
     }
 };
 
+// Bins of the 32-bit selection's bracket histogram: the same two layouts, with
+// every inner bin edge on a multiple of 2^sh of the key (offset from p1 in the
+// uniform layout), so that "the keys G below and above a key fall in one bin"
+// is one shift-compare (same()).
+//   uniform [p1, p2]: bin b = keys p1 + [b, b+1) << sh, at most 64 bins;
+//   crossing (p1 < key 0 <= p2, wider than two wings): quarter-binade bins
+//   (2^21 keys, aligned) on each side, the 32 of the negative side from
+//   p1 up, the 32 of the positive side down to p2; the innermost bin of each
+//   side also takes every smaller magnitude, up to key 0 (negative side) or
+//   from key 0 (positive side).  Inner multiples of 2^21 within those two
+//   catch-all bins are not edges; same() treats them as edges (a key next to
+//   one is divided exactly although it need not be).
+struct BinMapA {
+    uint32_t p1, p2, base;
+    int sh, tp1, tp2, nneg, npos;
+    bool cross;
+    static constexpr int QSH = 21;  // quarter binade of the key
+    __host__ __device__ void init(uint32_t P1, uint32_t P2) {
+        p1 = P1;
+        p2 = P2;
+        constexpr uint32_t WING = 31u << 21;
+        cross = P1 < CK0 && CK0 <= P2 && (P2 - P1) > 2u * WING;
+        if (!cross) {
+            const uint32_t span = P2 - P1;
+            sh = span >= 64u ? bitlen32(span) - 6 : 0;
+            base = P1;
+            nneg = (int)(span >> sh) + 1;
+            npos = 0;
+            tp1 = tp2 = 0;
+            return;
+        }
+        sh = QSH;
+        base = 0;
+        tp1 = (int)(P1 >> QSH);
+        tp2 = (int)(P2 >> QSH);
+        const int t0 = (int)(CK0 >> QSH);
+        nneg = (t0 - tp1) < 32 ? t0 - tp1 : 32;
+        npos = (tp2 - t0 + 1) < 32 ? tp2 - t0 + 1 : 32;
+    }
+    __host__ __device__ __forceinline__ int nbins() const { return nneg + npos; }
+    // kk in [p1, p2]
+    __host__ __device__ __forceinline__ int bin(uint32_t kk) const {
+        if (!cross) return (int)((kk - base) >> sh);
+        const int t = (int)(kk >> QSH);
+        const int dn = t - tp1, dp = tp2 - t;
+        const int bneg = dn < nneg - 1 ? dn : nneg - 1;
+        const int bpos = nneg + npos - 1 - (dp < npos - 1 ? dp : npos - 1);
+        return kk < CK0 ? bneg : bpos;
+    }
+    // kk - G and kk + G in [p1, p2]: true when both lie in kk's bin (keys
+    // next to an inner multiple of 2^21 of a catch-all bin count as not)
+    __host__ __device__ __forceinline__ bool same(uint32_t kk, uint32_t G) const {
+        return ((kk - G - base) >> sh) == ((kk + G - base) >> sh);
+    }
+    __host__ __device__ __forceinline__ uint32_t lower(int b) const {
+        if (!cross) return p1 + ((uint32_t)b << sh);
+        if (b < nneg) return b == 0 ? p1 : (uint32_t)(tp1 + b) << QSH;
+        const int bp = b - nneg;
+        if (bp == 0) return CK0;
+        return (uint32_t)(tp2 - (npos - 1 - bp)) << QSH;
+    }
+    __host__ __device__ __forceinline__ uint32_t upper(int b) const {
+        if (!cross) {
+            const uint64_t v = (uint64_t)p1 + ((uint64_t)(b + 1) << sh) - 1u;
+            return v > p2 ? p2 : (uint32_t)v;
+        }
+        if (b < nneg) return b == nneg - 1 ? CK0 - 1u : ((uint32_t)(tp1 + b + 1) << QSH) - 1u;
+        const int bp = b - nneg;
+        if (bp == npos - 1) return p2;
+        return (uint32_t)(((uint64_t)(tp2 - (npos - 1 - bp)) + 1u) << QSH) - 1u;
+    }
+};
+
 }  // namespace l1l

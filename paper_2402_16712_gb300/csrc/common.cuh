@@ -16,7 +16,7 @@ namespace l1l {
 enum : uint32_t {
     ST_NONFINITE = 1u << 0,
     ST_INTERNAL = 1u << 1,
-    ST_TIMEOUT = 1u << 2,
+    ST_TIMEOUT = 1u << 2,    // reserved: no kernel waits on another
     ST_BADINDEX = 1u << 3,  // a jhat list entry outside [0, m)
 };
 
@@ -76,6 +76,15 @@ struct ColInfo {
     int32_t n_valid;    // rows with x_ijhat != 0
     int32_t n_inexact;  // rows whose q_i was truncated
     int32_t flags;      // COL_WIDE: magnitudes outside the approximate-key range
+    // The same weights at 32 bits (float input's fast path): q32_i =
+    // q_i >> shift32 = floor(w_i 2^(sigma - shift32)), with shift32 the
+    // fewest bits that bring the total Q32 below 2^32, so every partial sum
+    // of q32 fits a uint32 exactly.  n_inexact32 counts the rows whose q32
+    // was truncated (the certainty band of the 32-bit decisions).
+    uint32_t Q32;
+    int32_t shift32;
+    int32_t n_inexact32;
+    int32_t pad_;
 };
 
 // A column is "wide" when some nonzero |x| lies outside the range in which the
@@ -153,13 +162,21 @@ struct Decide {
     int64_t e;   // n_inexact
 
     __device__ __forceinline__ void init(const ColInfo &ci, double lambda) {
-        Q = ci.Q;
-        e = ci.n_inexact;
+        init_at(ci.Q, ci.sigma, ci.n_inexact, lambda);
+    }
+    // The same test on the 32-bit weights q32 (scale sigma - shift32).
+    __device__ __forceinline__ void init32(const ColInfo &ci, double lambda) {
+        init_at((int64_t)ci.Q32, ci.sigma - ci.shift32, ci.n_inexact32, lambda);
+    }
+    __device__ __forceinline__ void init_at(int64_t Qs, int sigma, int64_t inexact,
+                                            double lambda) {
+        Q = Qs;
+        e = inexact;
         const int64_t SAT = (int64_t)1 << 62;
         if (lambda == 0.0) {
             Lf = Lc = 0;
         } else {
-            double lp = ldexp(lambda, ci.sigma);
+            double lp = ldexp(lambda, sigma);
             if (!(lp < 4611686018427387904.0)) {
                 Lf = Lc = SAT;
             } else if (lp < 1.0) {

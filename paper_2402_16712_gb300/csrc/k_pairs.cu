@@ -117,7 +117,7 @@ static PairPlan plan_placement(int64_t npad, bool cs, int d0, const Tune &tune) 
         const int64_t per_cta = 233472 / ctas - 1024 - 1024;
         for (int cand = w_hi; cand >= w_lo; --cand) {
             if (ctas * cand <= best || ctas * cand > 24) continue;
-            const int64_t fit = ((per_cta - (int64_t)cb) / cand - HIST_WORDS * 4) / 6;
+            const int64_t fit = PairSmem<T>::cap_fit((per_cta - (int64_t)cb) / cand);
             const int64_t c32 = std::min<int64_t>(npad, fit) & ~int64_t(31);
             if (fit > 0 && c32 >= 32 * qt_need) {
                 w = cand;

@@ -79,16 +79,33 @@ constexpr int HIST_WORDS = 4 * 64;  // per-warp exact histogram (4 chunks x 64 b
 
 template <typename T> struct PairSmem {
     // per CTA: x_ijhat (T; only when `cs`, else it is read from the column
-    // copy in global memory), 1/x_ijhat (float, NaN marks x_ijhat == 0), q_i
-    // (int64), the 64 sample rows (uint16)
+    // copy in global memory), 1/x_ijhat (float, NaN marks x_ijhat == 0), the
+    // weights (double input: 64-bit q_i; float input: 32-bit q32_i), the 64
+    // sample rows (uint16)
     __host__ __device__ static size_t col_bytes(int64_t npad, bool cs) {
-        return (cs ? al16(npad * sizeof(T)) : 0) + al16(npad * 4) + al16(npad * 8) +
-               al16(NSAMP * 2);
+        return (cs ? al16(npad * sizeof(T)) : 0) + al16(npad * 4) +
+               al16(npad * (sizeof(T) == 4 ? 4 : 8)) + al16(NSAMP * 2);
     }
-    // per warp: candidate keys (uint32), row indices (uint16; bit 15 = exact key)
-    // and the histogram (uint32)
-    __host__ __device__ static size_t warp_bytes(int64_t cap) {
+    // per warp, 64-bit selection: candidate keys (uint32), row indices
+    // (uint16; bit 15 = exact key) and the histogram (4 x 64 uint32)
+    __host__ __device__ static size_t bytes64(int64_t cap) {
         return al16(cap * 4) + al16(cap * 2) + al16(HIST_WORDS * 4);
+    }
+    // per warp, 32-bit selection (float input): 8-byte entries and a 64-word
+    // histogram, overlaid by the arrays of its 64-bit fallback
+    __host__ __device__ static size_t bytes32(int64_t cap) { return al16(cap * 8) + al16(64 * 4); }
+    __host__ __device__ static size_t warp_bytes(int64_t cap) {
+        if (sizeof(T) == 8) return bytes64(cap);
+        const size_t a = bytes32(cap), b = bytes64(cap);
+        return a > b ? a : b;
+    }
+    // the largest capacity (a multiple of 32) whose per-warp region fits `bytes`
+    __host__ __device__ static int64_t cap_fit(int64_t bytes) {
+        const int64_t c64 = (bytes - HIST_WORDS * 4 - 32) / 6;
+        const int64_t c32 = sizeof(T) == 8 ? c64 : (bytes - 64 * 4 - 16) / 8;
+        int64_t c = (c64 < c32 ? c64 : c32) & ~int64_t(31);
+        while (c > 0 && warp_bytes(c) > (size_t)bytes) c -= 32;
+        return c;
     }
 };
 
@@ -314,6 +331,30 @@ __device__ __forceinline__ int hist_cross_map(const uint32_t *h, const BinMap &b
     return bsel;
 }
 
+// Sources of the 64-bit fixed-point weight q_i of row i.  WqSmem: the staged
+// array (double input).  WqFly: computed from x_ijhat on the spot (float
+// input, whose fast path stages 32-bit weights; the 64-bit selection is its
+// rare fallback).
+struct WqSmem {
+    const int64_t *__restrict__ q;
+    __device__ __forceinline__ int64_t operator()(int i) const { return q[i]; }
+};
+template <typename T> struct WqFly {
+    const T *colb;
+    int sigma;
+    __device__ __forceinline__ int64_t operator()(int i) const {
+        const T b = colb[i];
+        int e = 0;
+        return b != T(0) ? fixq(b < T(0) ? -b : b, sigma, e) : 0;
+    }
+};
+
+}  // namespace l1l
+
+#include "select32.cuh"
+
+namespace l1l {
+
 // ---------------------------------------------------------------------------
 // Weighted median of one pair.  Returns SEL_* and the exact key in tstar.
 //
@@ -326,10 +367,10 @@ __device__ __forceinline__ int hist_cross_map(const uint32_t *h, const BinMap &b
 // __restrict__), so the loops over the list below, unrolled by two, can issue
 // the shared-memory loads of one candidate before the atomics of the other.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, typename WQ>
 __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                          const T *__restrict__ colb, const float *__restrict__ inv,
-                         const int64_t *__restrict__ colq, const uint16_t *__restrict__ samp,
+                         const WQ colq, const uint16_t *__restrict__ samp,
                          uint32_t *__restrict__ lk, uint16_t *__restrict__ li,
                          uint32_t *__restrict__ hist, int qt, int n, int d0, const Decide &dc,
                          typename Traits<T>::K &tstar, int lane) {
@@ -373,8 +414,12 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     };
     // d0: half-width of the first bracket in sample positions (6 of 64: ~15%
     // of the rows in the bracket, ~1.5% misses)
+    // pivots 2G + 1 keys outside the sample keys, so that the sample rows (and
+    // rows tied with them) lie clear of the guard bands
     uint32_t P1 = pick(jx - d0, lo0);
     uint32_t P2 = pick(jx + d0, hi0);
+    P1 = max(sat_sub(P1, 2 * G + 1), lo0);
+    P2 = min(sat_add(P2, 2 * G + 1), hi0);
     if (P1 > P2) P1 = P2;
     bool sampled = true;     // the bracket still comes from the sample
     bool count_pass = false;  // next attempt: narrow by a histogram over all rows
@@ -403,7 +448,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 if (isnan(iv)) continue;  // x_ijhat = 0 or a padding row
                 uint32_t kk = akey(__fmul_rn(xf[i], iv));
                 if (kk < bt) {
-                    Sb += colq[i];
+                    Sb += colq(i);
                     continue;
                 }
                 if (kk > at) continue;
@@ -411,9 +456,9 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 if (!(kk >= g1 && kk <= g2 && off >= G && off + G <= bmask))
                     kk = A::exact_ck(xk[i], colb[i]);
                 if (kk < P1)
-                    Sb += colq[i];
+                    Sb += colq(i);
                 else if (kk <= P2)
-                    hist_add(hist, (int)((kk - P1) >> sh), colq[i]);
+                    hist_add(hist, (int)((kk - P1) >> sh), colq(i));
             }
             Sb = warp_sum_i64(Sb);
             __syncwarp();
@@ -486,7 +531,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 const uint32_t kk = akey(__fmul_rn(ac[u], iv));
                 const bool below = kk < bt;
                 const bool cand = !below && kk <= at;
-                const int64_t q = colq[i];
+                const int64_t q = colq(i);
                 Sb += below ? q : 0;
                 // speculative store: the slot is only kept when cnt advances
                 if (cnt < qt) {
@@ -524,7 +569,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 lk[p] = kk;
                 li[p] = id | EXACT_BIT;
             }
-            const int64_t q = colq[id];
+            const int64_t q = colq(id);
             if (kk < P1)
                 Sb2 += q;
             else if (kk <= P2)
@@ -537,7 +582,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         if (r1 == 1) {  // median below P1: retry under P1
             hi0 = P1 - 1;
             P2 = hi0;
-            P1 = sampled ? pick(jx - 3 * max(d0, 1) - 1, lo0) : lo0;
+            P1 = sampled ? max(sat_sub(pick(jx - 3 * max(d0, 1) - 1, lo0), 2 * G + 1), lo0) : lo0;
             if (P1 > P2) P1 = lo0;
             continue;
         }
@@ -549,7 +594,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             if (P2 >= hi0) return SEL_INTERNAL;
             lo0 = P2 + 1;
             P1 = lo0;
-            P2 = sampled ? pick(jx + 3 * max(d0, 1) + 1, hi0) : hi0;
+            P2 = sampled ? min(sat_add(pick(jx + 3 * max(d0, 1) + 1, hi0), 2 * G + 1), hi0) : hi0;
             if (P2 < P1) P2 = hi0;
             continue;
         }
@@ -598,7 +643,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 id = (uint16_t)row | EXACT_BIT;
                 li[p] = id;
             }
-            hist_add(hist, (int)((kk - lo) >> sh), colq[id & ROW_MASK]);
+            hist_add(hist, (int)((kk - lo) >> sh), colq(id & ROW_MASK));
         }
         __syncwarp();
         int64_t below = 0;
@@ -664,7 +709,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     if (lane < c) {
         const int row = reinterpret_cast<const uint16_t *>(hist)[lane];
         fk = Tr::key(Tr::div_rn(xk[row], colb[row]));
-        fq = colq[row];
+        fq = colq(row);
     } else if (lane == c && lo <= CK0 && CK0 <= hi) {
         fk = Tr::KEY0;
         fq = 0;
@@ -700,33 +745,108 @@ struct LamView {
 };
 
 // Everything one warp needs to solve the pairs of its CTA's column jhat.
+// The fast path's weights are colq (double input, 64-bit) or q32 (float
+// input, 32-bit); s_dec and decide_for use the same scale.
 template <typename T> struct WarpCtx {
     const T *colb;
     const float *inv;
-    const int64_t *colq;
+    const int64_t *colq;   // double input
+    const uint32_t *q32;   // float input
     const uint16_t *samp;
-    uint32_t *lk;
+    uint32_t *lk;          // 64-bit selection's lists and histogram
     uint16_t *li;
     uint32_t *hist;
+    uint2 *lst;            // 32-bit selection's list and histogram (float input)
+    uint32_t *hist32;
     const Decide *s_dec;  // per-lambda thresholds for the first NDEC lambdas
     int qt, n;
     int d0;               // first-bracket half-width in sample positions
     ColInfo cinfo;
+    __device__ __forceinline__ int64_t q(int i) const {
+        if constexpr (sizeof(T) == 4)
+            return (int64_t)q32[i];
+        else
+            return colq[i];
+    }
 };
 constexpr int NDEC = 32;
 
+// The exact test of lambda tl on the fast path's weight scale.
+template <typename T>
+__device__ __forceinline__ void decide_init(Decide &dc, const ColInfo &ci, double lam) {
+    if constexpr (sizeof(T) == 4)
+        dc.init32(ci, lam);
+    else
+        dc.init(ci, lam);
+}
 template <typename T>
 __device__ __forceinline__ Decide decide_for(const WarpCtx<T> &w, const LamView &lp, int tl) {
     Decide dc;
     if (tl < NDEC)
         dc = w.s_dec[tl];
     else
-        dc.init(w.cinfo, lp.lam[tl]);
+        decide_init<T>(dc, w.cinfo, lp.lam[tl]);
     return dc;
 }
 
-// Writes v and s of (lambda t0+tl, jhat, k), or lists the pair for the exact path.
+// The 64-bit selection of a float pair that the 32-bit weights could not
+// settle (rare): a separate, not inlined function, so that its code stays out
+// of the hot loop's instruction stream.
 template <typename T>
+__device__ __noinline__ int select_fallback64(const T *xk, const float *xf, const T *colb,
+                                              const float *inv, const uint16_t *samp,
+                                              uint32_t *lk, uint16_t *li, uint32_t *hist,
+                                              int qt, int n, int d0, int64_t Q, int sigma,
+                                              int inexact, double lam, uint32_t *ts, int lane) {
+    Decide d64;
+    d64.init_at(Q, sigma, inexact, lam);
+    typename Traits<T>::K k = 0;
+    const int st = select_v2<T>(xk, xf, colb, inv, WqFly<T>{colb, sigma}, samp, lk, li, hist, qt,
+                                n, d0, d64, k, lane);
+    *ts = (uint32_t)k;
+    return st;
+}
+
+// The full selection of one (lambda, pair): float input tries 32-bit weights
+// and repeats the pair on 64-bit weights (computed from x_ijhat) when those
+// cannot settle it; double input selects on its staged 64-bit weights.
+template <typename T>
+__device__ __forceinline__ int select_pair(const T *xk, const float *xf, const WarpCtx<T> &w,
+                                           const LamView &lp, int tl,
+                                           typename Traits<T>::K &ts, int lane) {
+    const Decide dc = decide_for(w, lp, tl);
+    if constexpr (sizeof(T) == 4) {
+        uint32_t t32 = 0;
+        const int st = select_w32(xk, w.colb, w.inv, w.q32, w.samp, w.lst, w.hist32, w.qt, w.n,
+                                  w.d0, dc, t32, lane);
+        if (st != SEL_W64) {
+            ts = t32;
+            return st;
+        }
+        __syncwarp();
+        uint32_t t64 = 0;
+        const int st64 = select_fallback64<T>(xk, xf, w.colb, w.inv, w.samp, w.lk, w.li, w.hist,
+                                              w.qt, w.n, w.d0, w.cinfo.Q, w.cinfo.sigma,
+                                              w.cinfo.n_inexact, lp.lam[tl], &t64, lane);
+        ts = t64;
+        return st64;
+    } else {
+        return select_v2<T>(xk, xf, w.colb, w.inv, WqSmem{w.colq}, w.samp, w.lk, w.li, w.hist,
+                            w.qt, w.n, w.d0, dc, ts, lane);
+    }
+}
+
+// Residual of one pair (CS: x_ijhat staged in shared memory).
+template <typename T, bool CS>
+__device__ __forceinline__ T pair_residual(const T *xk, const T *colb, int n, T v, int lane) {
+    if constexpr (sizeof(T) == 4)
+        return warp_residual_f4<CS>(xk, colb, n, v, lane);
+    else
+        return warp_residual_pad<T>(xk, colb, n, v, lane);
+}
+
+// Writes v and s of (lambda t0+tl, jhat, k), or lists the pair for the exact path.
+template <typename T, bool CS>
 __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int st,
                           typename Traits<T>::K ts, const T *xk, const T *colb, int n,
                           double lam, int lane) {
@@ -755,7 +875,7 @@ __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int
         return;
     }
     const T v = Tr::value(ts);
-    const T res = warp_residual_pad<T>(xk, colb, n, v, lane);
+    const T res = pair_residual<T, CS>(xk, colb, n, v, lane);
     if (lane == 0) {
         a.v_all[o] = v;
         a.s_all[o] = (double)res + lam * (double)fabs(v);
@@ -763,7 +883,7 @@ __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int
 }
 
 // One lambda of one pair: the full selection.
-template <typename T>
+template <typename T, bool CS>
 __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int tl, int64_t j,
                           int64_t k, const T *xk, const float *xf, const WarpCtx<T> &w,
                           bool slow_pair, int lane) {
@@ -773,11 +893,9 @@ __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int t
     if (slow_pair) {
         st = SEL_SLOW;
     } else if (w.cinfo.n_valid > 0) {
-        const Decide dc = decide_for(w, lp, tl);
-        st = select_v2<T>(xk, xf, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, w.n, w.d0, dc,
-                          ts, lane);
+        st = select_pair<T>(xk, xf, w, lp, tl, ts, lane);
     }
-    emit_pair<T>(a, t0 + tl, j, k, st, ts, xk, w.colb, w.n, lp.lam[tl], lane);
+    emit_pair<T, CS>(a, t0 + tl, j, k, st, ts, xk, w.colb, w.n, lp.lam[tl], lane);
 }
 
 // Lambda batch (step A7).  The weighted median moves monotonically toward 0
@@ -787,7 +905,7 @@ __device__ void solve_one(const ScanArgs<T> &a, const LamView &lp, int t0, int t
 // pass, exact divisions only near the bounds) together with the exact weight
 // below, and decide every lambda from one sort and prefix scan of those rows.
 // Returns false (nothing written) when more than 31 rows lie between.
-template <typename T>
+template <typename T, bool CS>
 __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int nlc, int64_t j,
                             int64_t k, const T *__restrict__ xk, const float *__restrict__ xf,
                             const WarpCtx<T> &w, int lane) {
@@ -798,16 +916,8 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     const unsigned FULL = 0xFFFFFFFFu;
     const int n = w.n;
     K Ka = Tr::KEY0, Kb = Tr::KEY0;
-    {
-        const Decide da = decide_for(w, lp, lp.tl_min);
-        if (select_v2<T>(xk, xf, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, da, Ka,
-                         lane) != SEL_OK)
-            return false;
-        const Decide db = decide_for(w, lp, lp.tl_max);
-        if (select_v2<T>(xk, xf, w.colb, w.inv, w.colq, w.samp, w.lk, w.li, w.hist, w.qt, n, w.d0, db, Kb,
-                         lane) != SEL_OK)
-            return false;
-    }
+    if (select_pair<T>(xk, xf, w, lp, lp.tl_min, Ka, lane) != SEL_OK) return false;
+    if (select_pair<T>(xk, xf, w, lp, lp.tl_max, Kb, lane) != SEL_OK) return false;
     const K Klo = min(Ka, Kb), Khi = max(Ka, Kb);
     const uint32_t cl = ckey((float)Tr::value(Klo)), ch = ckey((float)Tr::value(Khi));
     const uint32_t bt = sat_sub(cl, G), at = min(sat_add(ch, G), CKMAX);
@@ -842,11 +952,11 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
                 if (!isnan(iv)) {
                     const uint32_t kk = akey(__fmul_rn(ac[u], iv));
                     if (kk < bt) {
-                        Sb += w.colq[i];
+                        Sb += w.q(i);
                     } else if (kk <= at) {
                         const K ke = Tr::key(Tr::div_rn(xk[i], w.colb[i]));
                         if (ke < Klo)
-                            Sb += w.colq[i];
+                            Sb += w.q(i);
                         else if (ke <= Khi)
                             take = true;
                     }
@@ -870,7 +980,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     if (lane < c) {
         const int row = stage[lane];
         fk = Tr::key(Tr::div_rn(xk[row], w.colb[row]));
-        fq = w.colq[row];
+        fq = w.q(row);
     } else if (lane == c && Klo <= Tr::KEY0 && Tr::KEY0 <= Khi) {
         fk = Tr::KEY0;
     }
@@ -890,14 +1000,14 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
         const unsigned any = okm | unm;
         const int first = any ? __ffs(any) - 1 : 0;
         if (!any || ((unm >> first) & 1u)) {  // undecided here: full selection
-            solve_one<T>(a, lp, t0, tl, j, k, xk, xf, w, false, lane);
+            solve_one<T, CS>(a, lp, t0, tl, j, k, xk, xf, w, false, lane);
             prev = Tr::NONE;
             continue;
         }
         const K ts = __shfl_sync(FULL, fk, first);
         const T v = Tr::value(ts);
         if (ts != prev) {
-            prev_res = warp_residual_pad<T>(xk, w.colb, n, v, lane);
+            prev_res = pair_residual<T, CS>(xk, w.colb, n, v, lane);
             prev = ts;
         }
         if (lane == 0) {
@@ -932,8 +1042,10 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     size_t off = CS ? al16((size_t)npad * sizeof(T)) : 0;
     float *inv = reinterpret_cast<float *>(smem + off);
     off += al16((size_t)npad * 4);
+    // fast-path weights: 64-bit q_i (double input) or 32-bit q32_i (float input)
     int64_t *colq = reinterpret_cast<int64_t *>(smem + off);
-    off += al16((size_t)npad * 8);
+    uint32_t *q32 = reinterpret_cast<uint32_t *>(smem + off);
+    off += al16((size_t)npad * (sizeof(T) == 4 ? 4 : 8));
     uint16_t *samp = reinterpret_cast<uint16_t *>(smem + off);
     unsigned char *wbase =
         smem + PairSmem<T>::col_bytes(npad, CS) + (size_t)warp * PairSmem<T>::warp_bytes(cap);
@@ -941,6 +1053,8 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     uint16_t *li = reinterpret_cast<uint16_t *>(wbase + al16((size_t)cap * 4));
     uint32_t *hist = reinterpret_cast<uint32_t *>(wbase + al16((size_t)cap * 4) +
                                                   al16((size_t)cap * 2));
+    uint2 *lst = reinterpret_cast<uint2 *>(wbase);
+    uint32_t *hist32 = reinterpret_cast<uint32_t *>(wbase + al16((size_t)cap * 8));
     // prologue scratch: the first 256 bytes of warp 0's candidate list
     long long *s_wsum = reinterpret_cast<long long *>(smem + PairSmem<T>::col_bytes(npad, CS));
 
@@ -955,7 +1069,11 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         // only add zero-weight candidates, which never decide the median.
         inv[i] = b != T(0) ? Approx<T>::inv_of(b) : __int_as_float(0x7FFFFFFF);
         int e = 0;
-        colq[i] = b != T(0) ? fixq(b < T(0) ? -b : b, cinfo.sigma, e) : 0;
+        const int64_t qi = b != T(0) ? fixq(b < T(0) ? -b : b, cinfo.sigma, e) : 0;
+        if constexpr (sizeof(T) == 4)
+            q32[i] = (uint32_t)((uint64_t)qi >> cinfo.shift32);
+        else
+            colq[i] = qi;
     }
     for (int q = threadIdx.x; q < NSAMP; q += blockDim.x) samp[q] = 0;  // always a valid row
     __syncthreads();
@@ -965,16 +1083,23 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         const int nt = blockDim.x;
         const int chunk = (n + nt - 1) / nt;
         const int r0 = min(n, threadIdx.x * chunk), r1 = min(n, r0 + chunk);
+        auto wq = [&](int r) -> long long {
+            if constexpr (sizeof(T) == 4)
+                return (long long)q32[r];
+            else
+                return colq[r];
+        };
         long long mine = 0;
-        for (int r = r0; r < r1; ++r) mine += colq[r];
+        for (int r = r0; r < r1; ++r) mine += wq(r);
         long long incl = warp_scan_add(mine, lane);
         if (lane == 31) s_wsum[warp] = incl;
         __syncthreads();
         long long before = incl - mine;
         for (int w = 0; w < warp; ++w) before += s_wsum[w];
-        const double per = (double)NSAMP / (double)cinfo.Q;
+        const double per =
+            (double)NSAMP / (double)(sizeof(T) == 4 ? (long long)cinfo.Q32 : cinfo.Q);
         for (int r = r0; r < r1; ++r) {
-            const long long after = before + colq[r];
+            const long long after = before + wq(r);
             const double x0 = (double)before * per - 0.5, x1 = (double)after * per - 0.5;
             int s0 = (int)floor(x0) + 1, s1 = (int)floor(x1);
             s0 = max(s0, 0);
@@ -985,16 +1110,20 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         __syncthreads();
     }
     // per-lambda thresholds of the exact test depend on (jhat, lambda) only
-    for (int tl = threadIdx.x; tl < min(nlc, NDEC); tl += blockDim.x) s_dec[tl].init(cinfo, lp.lam[tl]);
+    for (int tl = threadIdx.x; tl < min(nlc, NDEC); tl += blockDim.x)
+        decide_init<T>(s_dec[tl], cinfo, lp.lam[tl]);
     __syncthreads();
     WarpCtx<T> wc;
     wc.colb = colb;
     wc.inv = inv;
     wc.colq = colq;
+    wc.q32 = q32;
     wc.samp = samp;
     wc.lk = lk;
     wc.li = li;
     wc.hist = hist;
+    wc.lst = lst;
+    wc.hist32 = hist32;
     wc.s_dec = s_dec;
     wc.qt = cap / 32;
     wc.d0 = a.d0;
@@ -1016,12 +1145,12 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         const bool slow_pair = a.force_exact || jwide ||
                                (sizeof(T) == 8 && (a.ci[k].flags & COL_WIDE));
         if (MULTI && nlc >= 3 && !slow_pair && cinfo.n_valid > 0 &&
-            lambda_path<T>(a, lp, t0, nlc, j, k, xk, xf, wc, lane)) {
+            lambda_path<T, CS>(a, lp, t0, nlc, j, k, xk, xf, wc, lane)) {
             __syncwarp();
             continue;
         }
         for (int tl = 0; tl < nlc; ++tl)
-            solve_one<T>(a, lp, t0, tl, j, k, xk, xf, wc, slow_pair, lane);
+            solve_one<T, CS>(a, lp, t0, tl, j, k, xk, xf, wc, slow_pair, lane);
         __syncwarp();
     }
     __syncthreads();  // the CTA may stage another column next

@@ -102,12 +102,43 @@ __device__ __forceinline__ void colprep_column(const T *__restrict__ col, ColInf
         s_inx[warp] = inx;
     }
     __syncthreads();
+    long long Q = 0;
+    int I = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        Q += s_q[w];
+        I += s_inx[w];
+    }
+    // 32-bit weights: drop the fewest low bits that bring the total below
+    // 2^32 (floor(floor(x) / 2^s) = floor(x / 2^s), so q32 = q >> s is the
+    // weight rounded down at scale sigma - s, and sum q32 <= Q / 2^s < 2^32)
+    const int qbits = Q > 0 ? 64 - __clzll(Q) : 0;
+    const int shift = qbits > 32 ? qbits - 32 : 0;
+    const uint64_t lowmask = (1ull << shift) - 1ull;
+    long long q32 = 0;
+    int inx32 = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        T b = col[i];
+        if (b != T(0)) {
+            int e = 0;
+            const uint64_t qi = (uint64_t)fixq(absval(b), sigma, e);
+            q32 += (long long)(qi >> shift);
+            inx32 += (e || (qi & lowmask) != 0) ? 1 : 0;
+        }
+    }
+    q32 = warp_sum_i64(q32);
+    inx32 = __reduce_add_sync(0xFFFFFFFFu, inx32);
+    __syncthreads();  // s_q / s_inx are reused
+    if (lane == 0) {
+        s_q[warp] = q32;
+        s_inx[warp] = inx32;
+    }
+    __syncthreads();
     if (threadIdx.x == 0) {
-        long long Q = 0;
-        int I = 0;
+        long long Q32 = 0;
+        int I32 = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            Q += s_q[w];
-            I += s_inx[w];
+            Q32 += s_q[w];
+            I32 += s_inx[w];
         }
         ColInfo c;
         c.Q = Q;
@@ -115,6 +146,10 @@ __device__ __forceinline__ void colprep_column(const T *__restrict__ col, ColInf
         c.n_valid = nv;
         c.n_inexact = I;
         c.flags = (nv > 0 && (Emin < WideRange<T>::lo || E > WideRange<T>::hi)) ? COL_WIDE : 0;
+        c.Q32 = (uint32_t)Q32;
+        c.shift32 = shift;
+        c.n_inexact32 = I32;
+        c.pad_ = 0;
         *out = c;
     }
 }
