@@ -44,10 +44,10 @@ WORKLOAD = ("planted sparse line, n=2000 points x m=2000 coords, float32, 20-spa
 ALG_INSTR_PER_ELEM = 8
 SMS, LANES_PER_SM_CLK, SM_MAX_MHZ = 152, 128, 2070.0
 # Algorithmic bytes per (jhat, k) pair of the float32 pair kernel for its
-# memory ceilings: shared memory -- 16 bytes per row, the staged column's
-# reciprocal (4), weight (8) and value (4) read once each (as many bytes as a
-# 4-byte key and a 4-byte weight written once and read once); L2 -- column k
-# read once and column jhat once per CTA of T_k pairs, 4 n (1 + 1/T_k) bytes.
+# memory ceilings: shared memory -- 16 bytes per row, a 4-byte key and a 4-byte
+# weight written once and read once (the kernel itself reads 12 staged bytes
+# per row: reciprocal, 32-bit weight and value); L2 -- column k read once and
+# column jhat once per CTA of T_k pairs, 4 n (1 + 1/T_k) bytes.
 # The peaks are measured in the same run by the library's bandwidth probes.
 SMEM_BYTES_PER_ROW = 16
 
@@ -73,11 +73,69 @@ def job_value(world: int, steps: int, units_per_step: float, tot_ms: float) -> f
     return world * steps * units_per_step / (tot_ms * 1e-3)
 
 
+def sharded_summary(world: int, steps: int, pairs: int, step_ms, identical) -> dict:
+    """The line of one fit split over `world` ranks by jhat (strong scaling):
+    `step_ms` are the slowest rank's per-step times; every step is ONE fit, so
+    the job's value is one fit's pairs per step time, whatever the world size."""
+    tot = sum(step_ms)
+    return {"workload": "one 2000 x 2000 float32 fit split over the ranks by jhat "
+                        "(contiguous jhat ranges, fit_subset on each rank; the argmin over "
+                        "jhat is the one exchange: three small all-reduces per fit)",
+            "scaling": "strong", "n_gpus": world, "steps": steps,
+            "ms_per_step": tot / steps, "value": steps * pairs / (tot * 1e-3), "unit": UNIT,
+            "fits_per_s": steps / (tot * 1e-3), "identical_to_one_gpu": identical}
+
+
+def measure_sharded(dev, stream, dist, steps, warmup, flush=None):
+    """One fit of the seed-0 2000 x 2000 matrix split over this job's ranks
+    (sharded.fit_sharded: every rank holds the same matrix and scores its own
+    jhat range; NCCL all-reduces pick the argmin).  Each step is timed with
+    CUDA events on the launching stream (the collectives follow it there),
+    L2 flushed first; the per-step times are max-reduced over ranks.  Rank 0
+    also checks the result against its own one-GPU fit, bit for bit."""
+    import numpy as np
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line, sharded
+    X, lams, _ = datagen.paper_size("float32", seed=0)
+    n, m = X.shape
+    Xd = torch.from_numpy(X).to(dev)
+    ws = l1line.Workspace.for_shape(torch.float32, n, m, 1, dev)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            out = sharded.fit_sharded(Xd, lams, workspace=ws, stream=stream)
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    if dist is not None:
+        dist.barrier()
+    with torch.cuda.stream(stream):
+        for a, b in ev:
+            if flush is not None:
+                flush.fill_(7)
+            a.record(stream)
+            out = sharded.fit_sharded(Xd, lams, workspace=ws, stream=stream)
+            b.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = [job_ms(a.elapsed_time(b), dist, dev) for a, b in ev]
+    identical = None
+    if dist is None or dist.get_rank() == 0:
+        v1, o1, j1, _ = l1line.fit(Xd, lams, workspace=ws, stream=stream)
+        if stream is not None:
+            stream.synchronize()
+        vs, os_, js = (t.cpu().numpy() for t in out)
+        identical = bool(np.array_equal(v1.cpu().numpy().view(np.uint32), vs.view(np.uint32))
+                         and np.array_equal(o1.cpu().numpy().view(np.int64), os_.view(np.int64))
+                         and np.array_equal(j1.cpu().numpy(), js))
+    world = dist.get_world_size() if dist is not None else 1
+    return sharded_summary(world, steps, m * (m - 1), ms, identical)
+
+
 def _src_hash() -> str:
     """Hash of the pair kernel's code (comments and whitespace stripped, so a
     comment edit does not orphan the committed ncu summaries)."""
     h = hashlib.sha256()
-    for f in ("k_pairs.cu", "pairs.cuh", "common.cuh", "binmap.cuh"):
+    for f in ("k_pairs.cu", "pairs.cuh", "select32.cuh", "common.cuh", "binmap.cuh"):
         src = open(os.path.join(ROOT, "paper_2402_16712_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
@@ -358,6 +416,8 @@ def run_gpu(args):
     d2h = vh.numel() * 4 + 8 + 4
 
     extras = {} if args.no_extras else measure_extras(dev, stream, flush)
+    if world > 1:  # one fit split over the ranks (strong scaling), beside the replicas
+        extras["sharded"] = measure_sharded(dev, stream, dist, max(3, args.steps // 2), 3, flush)
 
     if rank != 0:
         if dist is not None:
@@ -753,6 +813,50 @@ def measure_learned(dev, stream, flush, count=8, Ks=(32, 512)):
                            "zero_regret_fraction": hits[K] / count} for K in Ks}}
 
 
+def run_sharded(args):
+    """--sharded: the headline is one 2000 x 2000 fit split over this job's
+    ranks by jhat (strong scaling); see measure_sharded."""
+    import torch
+
+    from paper_2402_16712_gb300 import l1line
+    rank, world, local = _env_rank()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0 or world == 1:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist is not None:
+        dist.barrier()
+    l1line.load()
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    clk = Clocks(dev.index)
+    clk.start()
+    r = measure_sharded(dev, stream, dist, args.steps, args.warmup, flush)
+    clocks = clk.stop()
+    launches = l1line.last_launch_count()
+    if rank == 0:
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": N_ROWS, "m": N_COLS, "lambda": LAMBDA,
+                           "pairs_per_fit": N_COLS * (N_COLS - 1),
+                           "parallelism": f"jhat-sharded x{world} (one fit over all ranks)",
+                           "l2": "flushed before every timed step (512 MiB write)"},
+                "fits_per_s": r["fits_per_s"], "identical_to_one_gpu": r["identical_to_one_gpu"],
+                "gpu_launches": launches * args.steps, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_profile_case(args):
     """A plain run of a few fits at a given shape (no timing), for ncu."""
     import torch
@@ -784,6 +888,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="only the headline line (skip the lambda-path, path, batch, small-fit, "
                          "proposer, comparison and components lines)")
+    ap.add_argument("--sharded", action="store_true",
+                    help="headline = one 2000 x 2000 fit split over the ranks by jhat (strong "
+                         "scaling, NCCL argmin), checked bit for bit against the one-GPU fit")
     ap.add_argument("--profile-case", action="store_true",
                     help="run --fits plain fits of an n x m instance (for ncu), no timing")
     ap.add_argument("--n", type=int, default=N_ROWS)
@@ -799,6 +906,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.sharded:
+        return run_sharded(args)
     return run_gpu(args)
 
 

@@ -523,44 +523,40 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
 
 // Residual sum_i |x_ik - v x_ijhat| over the padded rows (padding rows are 0
 // in both columns), float input, four consecutive rows per lane per 128-row
-// group and two groups per step (eight loads in flight); xj in shared memory
-// when XS, else in global memory.
+// group and four groups per step: the step's sixteen loads are in flight
+// together (column k comes from L2, so the pass is bound by load latency, not
+// arithmetic); xj in shared memory when XS, else in global memory.
 template <bool XS>
 __device__ __forceinline__ float warp_residual_f4(const float *__restrict__ xk,
                                                   const float *__restrict__ xj, int n, float v,
                                                   int lane) {
     const int ng = (n + 127) >> 7;
-    const float4 *a4 = reinterpret_cast<const float4 *>(xk);
-    const float4 *b4 = reinterpret_cast<const float4 *>(xj);
-    // plain loads: the compiler batches them across steps
-    auto ldb = [&](int g4) -> float4 {
+    const float4 *a4 = reinterpret_cast<const float4 *>(xk) + lane;
+    const float4 *b4 = reinterpret_cast<const float4 *>(xj) + lane;
+    auto ldb = [&](int g) -> float4 {
         if constexpr (XS)
-            return b4[g4];
+            return b4[g * 32];
         else
-            return __ldg(b4 + g4);
+            return __ldg(b4 + g * 32);
     };
     float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    auto add4 = [&](const float4 &a, const float4 &b) {
+        acc0 += fabsf(fmaf(-v, b.x, a.x));
+        acc1 += fabsf(fmaf(-v, b.y, a.y));
+        acc2 += fabsf(fmaf(-v, b.z, a.z));
+        acc3 += fabsf(fmaf(-v, b.w, a.w));
+    };
     int g = 0;
-    for (; g + 1 < ng; g += 2) {
-        const float4 a = __ldg(a4 + g * 32 + lane), c = __ldg(a4 + (g + 1) * 32 + lane);
-        const float4 b = ldb(g * 32 + lane), d = ldb((g + 1) * 32 + lane);
-        acc0 += fabsf(fmaf(-v, b.x, a.x));
-        acc1 += fabsf(fmaf(-v, b.y, a.y));
-        acc2 += fabsf(fmaf(-v, b.z, a.z));
-        acc3 += fabsf(fmaf(-v, b.w, a.w));
-        acc0 += fabsf(fmaf(-v, d.x, c.x));
-        acc1 += fabsf(fmaf(-v, d.y, c.y));
-        acc2 += fabsf(fmaf(-v, d.z, c.z));
-        acc3 += fabsf(fmaf(-v, d.w, c.w));
+    for (; g + 3 < ng; g += 4) {
+        float4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = __ldg(a4 + (g + u) * 32);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) b[u] = ldb(g + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) add4(a[u], b[u]);
     }
-    if (g < ng) {
-        const float4 a = __ldg(a4 + g * 32 + lane);
-        const float4 b = ldb(g * 32 + lane);
-        acc0 += fabsf(fmaf(-v, b.x, a.x));
-        acc1 += fabsf(fmaf(-v, b.y, a.y));
-        acc2 += fabsf(fmaf(-v, b.z, a.z));
-        acc3 += fabsf(fmaf(-v, b.w, a.w));
-    }
+    for (; g < ng; ++g) add4(__ldg(a4 + g * 32), ldb(g));
     float s = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);

@@ -183,3 +183,71 @@ def test_components_line_host_logic(monkeypatch):
     assert r["ms_per_step"] == 4.0 and r["components_per_s"] == 3 / 4e-3
     assert r["pairs_per_s"] == 3 * 500 * 499 / 4e-3 and r["jhat_star"] == [7, 3, 11]
     assert r["gpu_launches_per_step"] == 17
+
+
+def _sharded_leg_on_rank(rank, world):
+    """bench.measure_sharded on one gloo rank with the CUDA pieces faked: the
+    'fit' of a jhat list returns the best of a fixed objective table over it,
+    so the sharded result must equal the one-GPU fit's."""
+    import numpy as np
+    import torch
+
+    import bench
+    from paper_2402_16712_gb300 import l1line
+
+    m = 2000
+    z = (np.arange(m, dtype=np.float64) - 1234.0) ** 2 + 3.0  # argmin at jhat 1234
+
+    def best(jl, nl=1):
+        jl = np.asarray(jl)
+        j = int(jl[np.argmin(z[jl])])
+        v = torch.full((nl, m), float(j), dtype=torch.float32)
+        return v, torch.tensor([z[j]], dtype=torch.float64), torch.tensor([j], dtype=torch.int32)
+
+    def fake_fit_subset(X, lambdas, jhat, workspace=None, stream=None, out=None):
+        v, o, j = best(jhat.numpy())
+        return v, o, j, workspace
+
+    def fake_fit(X, lambdas, workspace=None, stream=None, out=None):
+        v, o, j = best(np.arange(m))
+        return v, o, j, workspace
+
+    class FakeEvent:
+        def __init__(self, enable_timing=False):
+            pass
+
+        def record(self, stream=None):
+            pass
+
+        def elapsed_time(self, other):
+            return 1.0 + rank  # ms: the slower rank sets the job's time
+
+    l1line.fit_subset = fake_fit_subset
+    l1line.fit = fake_fit
+    l1line.Workspace.for_shape = classmethod(lambda cls, *a, **k: None)
+    torch.cuda.Event = FakeEvent
+    torch.cuda.synchronize = lambda *a, **k: None
+    import torch.distributed as dist
+    return bench.measure_sharded(torch.device("cpu"), None, dist, 3, 1)
+
+
+def test_sharded_bench_leg_two_ranks():
+    """The bench's one-fit-over-all-ranks leg on two gloo ranks: the jhat
+    ranges, the cross-rank argmin, the max-over-ranks step time, the strong-
+    scaling value (one fit's pairs per step) and the bit-identity check."""
+    from tests._dist import run_ranks
+    out = run_ranks(_sharded_leg_on_rank, 2)
+    r0, r1 = out[0], out[1]
+    assert r0["identical_to_one_gpu"] is True and r1["identical_to_one_gpu"] is None
+    for r in (r0, r1):
+        assert r["scaling"] == "strong" and r["n_gpus"] == 2 and r["steps"] == 3
+        assert r["ms_per_step"] == pytest.approx(2.0)  # rank 1's 2 ms per step
+        assert r["value"] == pytest.approx(2000 * 1999 / 2.0e-3)
+
+
+def test_sharded_summary_arithmetic():
+    import bench
+    r = bench.sharded_summary(4, 2, 3_998_000, [5.0, 7.0], True)
+    assert r["ms_per_step"] == 6.0 and r["fits_per_s"] == pytest.approx(2 / 12e-3)
+    assert r["value"] == pytest.approx(2 * 3_998_000 / 12e-3)
+    assert r["identical_to_one_gpu"] is True and r["scaling"] == "strong"
