@@ -12,7 +12,14 @@ rides along.  L2 is flushed (a 512 MiB write) before every timed step.
 
 Under torchrun each rank fits its own seeded instance on its own GPU (weak
 scaling, no collective on the data path); the job's value is all ranks' pairs
-divided by the slowest rank's time.
+divided by the slowest rank's time.  The line then also carries `sharded`: one
+fit split over all ranks by jhat (strong scaling); --sharded makes that the
+headline.
+
+Context lines beside the headline (not in `value`): the float64 fit, the
+lambda batch, Algorithm 2 over every pair (with its HBM and issue ceilings),
+Algorithms 2 + 3 at 1000 x 500 and 2000 x 2000, the uneven batch, the small
+fit, the learned proposer, the comparison data and successive components.
 
 --impl reference times the CPU oracle (C, OpenMP over jhat) on the machine's host
 cores, on a bounded sample of the same workload (a subset of the jhat columns,
@@ -523,8 +530,10 @@ def _replay_ms(g, stream, steps, flush=None):
 def measure_extras(dev, stream, flush):
     """The other workloads, reported beside the headline (not in `value`):
     the lambda batch and the uneven batch (each captured once into a CUDA graph
-    and replayed), Algorithms 2 and 3, the small fit, the learned proposer, the
-    comparison data and successive components."""
+    and replayed), Algorithm 2 over every pair of the 2000 x 2000 matrix (with
+    its HBM and issue ceilings), Algorithms 2 + 3 at 2000 x 2000 and 1000 x 500,
+    the small fit, the learned proposer, the comparison data and successive
+    components."""
     import numpy as np
     import torch
 
@@ -561,60 +570,37 @@ def measure_extras(dev, stream, flush):
         "fits_per_s": lams.size / (ms * 1e-3), "gpu_launches_per_step": launches,
         "tuning": tuning}
     del Xd, ws, res, g
-    # Algorithm 2: the lambda path of every (jhat, k) pair, 2000 x 2000 float32;
-    # its lambda = 0 scan runs under the headline shape's cached tuning
+    # Algorithm 2 over every (jhat, k) pair and Algorithm 3 on top of it:
+    # the 2000 x 2000 matrix (its lambda = 0 scan under the headline shape's
+    # cached tuning) and the 1000 x 500 lambda-path matrix
     X, _, _ = datagen.paper_size("float32")
-    Xd = torch.from_numpy(X).to(dev)
-    pws = l1line.path_workspace(torch.float32, 2000, 2000, dev)
     ptune = autotune.apply(torch.float32, 2000, 2000, 1)
-    with torch.cuda.stream(stream):
-        off, lam_o, v_o, ln, _ = l1line.paths(Xd, workspace=pws, stream=stream)
-    stream.synchronize()
-    tms = []
-    for _ in range(3):
-        flush.fill_(2)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-            off, lam_o, v_o, ln, _ = l1line.paths(Xd, workspace=pws, stream=stream)
-            e1.record(stream)
-        stream.synchronize()
-        tms.append(e0.elapsed_time(e1))
-    if l1line.status(pws, stream) != l1line.OK:
-        raise SystemExit("path enumeration failed on the device")
-    entries = int(ln.sum().item())
-    ms = statistics.median(tms)
+    big = measure_paths(dev, stream, flush, X)
+    l1line.set_tuning(None)
     out["lambda_paths"] = {
         "workload": "Algorithm 2 for every (jhat, k) pair of the 2000 x 2000 float32 matrix: "
-                    "exact lambda = 0 scan, count pass, offsets scan, write pass (L2 flushed)",
-        "ms_per_step": ms, "breakpoints": entries,
-        "breakpoints_per_s": entries / (ms * 1e-3), "pairs_per_s": 2000 * 1999 / (ms * 1e-3),
-        "tuning": ptune}
-    l1line.set_tuning(None)
-    del Xd, pws, off, lam_o, v_o, ln
-    # Algorithms 2 + 3: the whole solution path of the 1000 x 500 lambda-path matrix
+                    "exact lambda = 0 scan, count pass, offsets scan, write pass (L2 flushed, "
+                    "CUDA events, output buffers allocated beforehand)",
+        "ms_per_step": big["alg2_ms"], "breakpoints": big["entries"],
+        "breakpoints_per_s": big["entries"] / (big["alg2_ms"] * 1e-3),
+        "pairs_per_s": 2000 * 1999 / (big["alg2_ms"] * 1e-3), "tuning": ptune,
+        "roofline": path_roofline(2000, 2000, big["entries"], big["alg2_ms"], 4)}
+    out["solution_path_2000"] = {
+        "workload": "Algorithms 2 and 3 on the 2000 x 2000 float32 matrix: every pair's path "
+                    "with residuals, per-jhat objectives, lower envelope (CUDA events, output "
+                    "buffers allocated beforehand, L2 flushed)",
+        "ms_per_step": big["alg2_res_ms"] + big["alg3_ms"], "alg2_with_residuals_ms":
+        big["alg2_res_ms"], "alg3_ms": big["alg3_ms"], "pieces": big["pieces"],
+        "breakpoints": big["entries"]}
     X, _, _ = datagen.lambda_path("float32")
-    Xd = torch.from_numpy(X).to(dev)
-    with torch.cuda.stream(stream):
-        l1line.solution_path(Xd, stream=stream)
-    stream.synchronize()
-    tms = []
-    for _ in range(3):
-        flush.fill_(4)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            st, jh, I, S, V = l1line.solution_path(Xd, stream=stream)
-        stream.synchronize()
-        tms.append((time.perf_counter() - t0) * 1e3)
+    small = measure_paths(dev, stream, flush, X)
     out["solution_path"] = {
         "workload": "Algorithms 2 and 3 on the n=1000, m=500 float32 lambda-path matrix: every "
-                    "pair's path with residuals, per-jhat objectives, lower envelope "
-                    "(host-timed, includes the host reads of the sizes and the workspace "
-                    "allocation)",
-        "ms_per_step": statistics.median(tms), "pieces": int(st.numel()),
-        "jhat_star": sorted({int(x) for x in jh.tolist()})}
-    del Xd
+                    "pair's path with residuals, per-jhat objectives, lower envelope (CUDA "
+                    "events, output buffers allocated beforehand, L2 flushed)",
+        "ms_per_step": small["alg2_res_ms"] + small["alg3_ms"],
+        "alg2_with_residuals_ms": small["alg2_res_ms"], "alg3_ms": small["alg3_ms"],
+        "pieces": small["pieces"], "jhat_star": small["jhat_star"]}
     # uneven batch: 256 instances, n~U[100,5000], m~U[10,500], lambda=0.2
     batch = datagen.uneven_batch(256)
     Xs = [torch.from_numpy(Xb).to(dev) for Xb, _ in batch]
@@ -652,6 +638,113 @@ def measure_extras(dev, stream, flush):
         except Exception as e:  # context lines only: never cost the headline
             out[key] = {"error": f"{type(e).__name__}: {e}"}
     return out
+
+
+def path_roofline(n, m, entries, ms, es):
+    """Algorithm 2's count and write passes against two ceilings: HBM (the
+    bytes the write pass stores: lambda (8) and value (es) per breakpoint, a
+    length (4) and an offset (8) per pair, against the measured copy
+    bandwidth) and issue (two passes over the n rows of every pair at 6
+    lane-instructions per row: load, multiply by the staged reciprocal, key,
+    two compares, count or list; against 152 SMs x 128 lanes x 2070 MHz)."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    pairs = m * (m - 1)
+    wbytes = entries * (8 + es) + m * m * (4 + 8)
+    instr = 2 * 6 * n * pairs
+    alu_peak = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6
+    t = ms * 1e-3
+    ce = {"hbm": {"achieved": wbytes / t / 1e9, "peak": hbm, "unit": "GB/s",
+                  "frac": wbytes / t / 1e9 / hbm, "traffic_bytes": wbytes,
+                  "peak_source": "MEASURED_PEAKS.json" if peaks else "fallback 6.8 TB/s"},
+          "alu": {"achieved": instr / t / 1e12, "peak": alu_peak / 1e12, "unit": "Tinstr/s",
+                  "frac": instr / t / alu_peak, "instructions": instr}}
+    bound = max(ce, key=lambda c: wbytes / (hbm * 1e9) if c == "hbm" else instr / alu_peak)
+    return {"bound": bound, **{k: ce[bound][k] for k in ("achieved", "peak", "unit", "frac")},
+            "ceilings": ce}
+
+
+def measure_paths(dev, stream, flush, X, reps=3):
+    """Algorithm 2 (count + write, with and without residuals) and Algorithm 3
+    (the envelope) of X through the library's entry points, each timed with
+    CUDA events on the launching stream, L2 flushed before each; the output
+    buffers are sized by one untimed run first, so no allocation or host read
+    of a size lies inside a timed region."""
+    import ctypes
+
+    import torch
+
+    from paper_2402_16712_gb300 import l1line
+    lib = l1line.load()
+    Xd = torch.from_numpy(X).to(dev)
+    n, m = X.shape
+    pws = l1line.path_workspace(Xd.dtype, n, m, dev)
+    with torch.cuda.stream(stream):
+        st, jh, I, S, V = l1line.solution_path(Xd, stream=stream)
+        off, lam, v, ln, _, res = l1line.paths(Xd, workspace=pws, stream=stream, residuals=True)
+    stream.synchronize()
+    entries = int(off[m * m].item())
+    pieces = int(st.numel())
+    cap = pieces
+    nb = int(lib.l1line_solution_path_workspace_bytes(m, entries))
+    sws = l1line.Workspace(nb, dev)
+    o_st = torch.empty(cap, dtype=torch.float64, device=dev)
+    o_jh = torch.empty(cap, dtype=torch.int32, device=dev)
+    o_I = torch.empty(cap, dtype=torch.float64, device=dev)
+    o_S = torch.empty(cap, dtype=torch.float64, device=dev)
+    o_v = torch.empty((cap, m), dtype=Xd.dtype, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    P = ctypes.c_void_p
+    sp = P(stream.cuda_stream)
+    f32 = Xd.dtype == torch.float32
+    count = lib.l1line_path_count_f32 if f32 else lib.l1line_path_count_f64
+    write = lib.l1line_path_write_f32 if f32 else lib.l1line_path_write_f64
+    solve = lib.l1line_solution_path_f32 if f32 else lib.l1line_solution_path_f64
+
+    def ok(rc, what):
+        if rc != l1line.OK:
+            raise SystemExit(f"{what}: {l1line.status_string(rc)}")
+
+    def alg2(with_res):
+        ok(count(Xd.data_ptr(), n, m, off.data_ptr(), P(pws.ptr), pws.nbytes, sp), "path count")
+        ok(write(Xd.data_ptr(), n, m, off.data_ptr(), lam.data_ptr(), v.data_ptr(),
+                 P(res.data_ptr()) if with_res else None, ln.data_ptr(), P(pws.ptr), pws.nbytes,
+                 sp), "path write")
+
+    def alg3():
+        ok(solve(m, off.data_ptr(), lam.data_ptr(), v.data_ptr(), res.data_ptr(), ln.data_ptr(),
+                 entries, o_st.data_ptr(), o_jh.data_ptr(), o_I.data_ptr(), o_S.data_ptr(),
+                 o_v.data_ptr(), cnt.data_ptr(), cap, P(sws.ptr), sws.nbytes, sp),
+           "solution path")
+
+    def timed(fn):
+        t = []
+        for _ in range(reps):
+            flush.fill_(6)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                a.record(stream)
+                fn()
+                b.record(stream)
+            stream.synchronize()
+            t.append(a.elapsed_time(b))
+        return statistics.median(t)
+
+    alg2(True)
+    alg3()
+    r = {"alg2_ms": timed(lambda: alg2(False)), "alg2_res_ms": timed(lambda: alg2(True)),
+         "alg3_ms": timed(alg3), "entries": entries, "pieces": pieces,
+         "jhat_star": sorted({int(x) for x in jh.tolist()})}
+    if l1line.status(pws, stream) != l1line.OK or l1line.status(sws, stream) != l1line.OK:
+        raise SystemExit("path enumeration failed on the device")
+    if int(cnt.item()) != pieces:
+        raise SystemExit("solution path piece count changed between runs")
+    return r
 
 
 def measure_components(dev, stream, flush, ncomp=3, steps=5):
@@ -760,7 +853,7 @@ def measure_small_fit(dev, stream, replays=200):
             "pairs_per_s": m * (m - 1) / (ms * 1e-3), "gpu_launches_per_step": launches}
 
 
-def measure_learned(dev, stream, flush, count=8, Ks=(32, 512)):
+def measure_learned(dev, stream, flush, count=32, Ks=(32, 128)):
     """The learned top-K path against the full scan on a sample of held-out
     5000 x 1000 float32 instances (the committed network; the 200-instance
     evaluation is the proposer module's `eval`).  Times are CUDA events with L2
@@ -772,7 +865,7 @@ def measure_learned(dev, stream, flush, count=8, Ks=(32, 512)):
     from paper_2402_16712_gb300 import datagen, l1line, proposer
     mlp = proposer.network(dev)
     n, m = 5000, 1000
-    ws = l1line.Workspace.for_shape(torch.float32, n, m, 1, dev)
+    ws = l1line.proposed_workspace(torch.float32, n, m, 1, dev)
 
     def timed(fn):
         flush.fill_(5)

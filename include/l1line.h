@@ -272,27 +272,31 @@ int l1line_components_f64(const double *X, int64_t n, int64_t m, double lambda, 
 
 /*
  * Learned jhat proposer (not in the paper; an extension of Algorithm 1's
- * outer loop): a small network scores every candidate jhat from three column
+ * outer loop): a small network scores every candidate jhat from four
  * features, and only the K best-scored candidates are fitted exactly (the
  * exact objective still decides among them; the full scan stays the reference
  * for its regret).
  *
  * Features of column jhat: its l1 norm, l2 norm and the lower median of
- * |x_i,jhat| (0-based rank floor((n-1)/2) of the ascending order), each
- * standardised over the m columns of the instance (mean 0, population
- * standard deviation 1; a feature constant over the columns becomes 0).
- * Stored as float [m][3].
+ * |x_i,jhat| (0-based rank floor((n-1)/2) of the ascending order), and the
+ * objective z_jhat of Algorithm 1 (penalty lambda) on the R =
+ * l1line_proposer_rows(n) rows of X with the largest l1 norm (the double sum
+ * of |x_ij| over j, left to right, rounded to float; ties to the smaller row),
+ * computed by this library's own fit of those rows; each feature standardised
+ * over the m columns of the instance (mean 0, population standard deviation
+ * 1; a feature constant over the columns becomes 0).  Stored as float [m][4].
  *
- * Network: 3 -> 128 -> 128 -> 1, ReLU after both hidden layers; weight
+ * Network: 4 -> 128 -> 128 -> 1, ReLU after both hidden layers; weight
  * matrices in binary16, biases in float, float arithmetic.  l1line_mlp is its
- * packed DEVICE image (34,832 bytes, 16-byte aligned); the flat float
+ * packed DEVICE image (35,088 bytes, 16-byte aligned); the flat float
  * parameter vector used for training holds L1L_MLP_PARAMS values in the order
- * W1 [128][3], b1 [128], W2 [128][128], b2 [128], w3 [128], b3.
+ * W1 [128][4], b1 [128], W2 [128][128], b2 [128], w3 [128], b3.
  */
 #define L1L_MLP_HIDDEN 128
-#define L1L_MLP_PARAMS 17153
+#define L1L_MLP_FEATURES 4
+#define L1L_MLP_PARAMS 17281
 typedef struct l1line_mlp {
-    uint16_t w1[L1L_MLP_HIDDEN * 3];              /* binary16 bits, [o][c]  */
+    uint16_t w1[L1L_MLP_HIDDEN * L1L_MLP_FEATURES]; /* binary16 bits, [o][c]  */
     float b1[L1L_MLP_HIDDEN];
     uint16_t w2[L1L_MLP_HIDDEN * L1L_MLP_HIDDEN]; /* binary16 bits, [o][i]  */
     float b2[L1L_MLP_HIDDEN];
@@ -301,15 +305,25 @@ typedef struct l1line_mlp {
     float reserved[3];
 } l1line_mlp;
 
-/* Column features of X (raw and standardised, DEVICE float [m][3] each; raw
- * may be NULL).  Workspace as for l1line_fit_* with n_lambda = 1. */
-int l1line_features_f32(const float *X, int64_t n, int64_t m, float *out_raw, float *out_std,
-                        void *workspace, size_t workspace_bytes, void *stream);
-int l1line_features_f64(const double *X, int64_t n, int64_t m, float *out_raw, float *out_std,
-                        void *workspace, size_t workspace_bytes, void *stream);
+/* Rows of the restricted fit behind the fourth feature: min(n, max(256,
+ * ceil(n / 8))); 0 for n < 1. */
+int64_t l1line_proposer_rows(int64_t n);
+
+/* Bytes of device workspace l1line_features_* (n_lambda = 1) and
+ * l1line_fit_proposed_* need: the fit's workspace, then the restricted fit's
+ * (its rows, their copy and its own workspace); 0 on a bad argument. */
+size_t l1line_proposed_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t n_lambda);
+
+/* Features of every column of X (raw and standardised, DEVICE float [m][4]
+ * each; raw may be NULL); lambda (>= 0) is the penalty of the restricted
+ * objective.  Workspace: l1line_proposed_workspace_bytes(dtype, n, m, 1). */
+int l1line_features_f32(const float *X, int64_t n, int64_t m, double lambda, float *out_raw,
+                        float *out_std, void *workspace, size_t workspace_bytes, void *stream);
+int l1line_features_f64(const double *X, int64_t n, int64_t m, double lambda, float *out_raw,
+                        float *out_std, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Network forward pass: scores[r] = net(feat[rows[r]]) for r < N (rows NULL:
- * row r).  feat DEVICE float [*][3], rows DEVICE int32 [N] or NULL, mlp
+ * row r).  feat DEVICE float [*][4], rows DEVICE int32 [N] or NULL, mlp
  * DEVICE, scores DEVICE float [N]. */
 int l1line_mlp_forward(const float *feat, const int32_t *rows, int64_t N,
                        const l1line_mlp *mlp, float *scores, void *stream);
@@ -349,9 +363,10 @@ int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream);
  * NaN lowest, written in ascending index order to out_idx (DEVICE int32 [K]). */
 int l1line_topk(const float *scores, int64_t m, int64_t K, int32_t *out_idx, void *stream);
 
-/* The whole learned path in one call: features, network, top-K, then the
- * subset fit of those K candidates.  out_idx (DEVICE int32 [K]) receives the
- * candidates (may be NULL).  Workspace as for l1line_fit_*. */
+/* The whole learned path in one call: features (the restricted objective at
+ * lambdas[0]), network, top-K, then the subset fit of those K candidates.
+ * out_idx (DEVICE int32 [K]) receives the candidates (may be NULL).
+ * Workspace: l1line_proposed_workspace_bytes(dtype, n, m, n_lambda). */
 int l1line_fit_proposed_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                             int64_t n_lambda, const l1line_mlp *mlp, int64_t K,
                             int32_t *out_idx, float *out_v, double *out_obj,
@@ -411,6 +426,15 @@ const char *l1line_status_string(int status);
 /* Number of kernels the most recent scan or fit call launched (for launch
  * accounting); host-side counter, per calling thread. */
 int l1line_last_launch_count(void);
+
+/* Bounds-check counters (a diagnostic, not in the paper).  The library built
+ * with L1L_CHECKS=1 checks the shared- and global-memory indices of its
+ * kernels; an index out of range is counted, replaced by 0 (the kernel runs
+ * on, no trap) and sets *line (when non-NULL) to a source line of the last
+ * one.  Synchronises the device; returns the hits since the last reset and
+ * clears them when `reset` is non-zero; -1 in the normal build, -2 on a CUDA
+ * error. */
+int64_t l1line_check_hits(int reset, int *line);
 
 /*
  * Tuning of the pair kernel's launch (for an autotuner).  Every field 0 means

@@ -8,10 +8,13 @@ The proposer ranks the candidate preserved coordinates jhat of Algorithm 1 so
 that only the best K are scored exactly; the exact scores still decide.
 
 * Features of column jhat: l1 norm, l2 norm and the lower median of |x_i,jhat|
-  (the element of 0-based rank floor((n-1)/2) in ascending order), each then
-  standardised across the m columns of the instance (mean 0, population
-  standard deviation 1; a feature constant over the columns becomes 0).
-* Network: 3 -> 128 -> 128 -> 1 with ReLU.  The weight matrices are used at
+  (the element of 0-based rank floor((n-1)/2) in ascending order), and the
+  objective z_jhat of Algorithm 1 (penalty lambda) restricted to the R rows of
+  largest l1 norm (R = proxy_rows(n)), each then standardised across the m
+  columns of the instance (mean 0, population standard deviation 1; a feature
+  constant over the columns becomes 0).  The restricted objective uses the
+  exact method itself (the C oracle) on those rows.
+* Network: 4 -> 128 -> 128 -> 1 with ReLU.  The weight matrices are used at
   half precision (the caller passes them already rounded); biases, activations
   and sums are exact here (float64).
 * Loss per instance: cross entropy between softmax(target logits) and
@@ -24,19 +27,20 @@ from __future__ import annotations
 import numpy as np
 
 H = 128
-N_PARAMS = H * 3 + H + H * H + H + H + 1  # W1, b1, W2, b2, w3, b3 in that order
+NF = 4  # input features
+N_PARAMS = H * NF + H + H * H + H + H + 1  # W1, b1, W2, b2, w3, b3 in that order
 
 
 # ---------------------------------------------------------------------------
 # parameters
 # ---------------------------------------------------------------------------
 def unpack(theta):
-    """Flat parameter vector -> (W1 [H,3], b1 [H], W2 [H,H], b2 [H], w3 [H], b3)."""
+    """Flat parameter vector -> (W1 [H,NF], b1 [H], W2 [H,H], b2 [H], w3 [H], b3)."""
     theta = np.asarray(theta, dtype=np.float64)
     assert theta.size == N_PARAMS
     o = 0
-    W1 = theta[o:o + 3 * H].reshape(H, 3)
-    o += 3 * H
+    W1 = theta[o:o + NF * H].reshape(H, NF)
+    o += NF * H
     b1 = theta[o:o + H]
     o += H
     W2 = theta[o:o + H * H].reshape(H, H)
@@ -64,7 +68,7 @@ def half_weights(theta):
 # ---------------------------------------------------------------------------
 # features
 # ---------------------------------------------------------------------------
-def raw_features(X):
+def column_features(X):
     """(m, 3): l1 norm, l2 norm, lower median of |x| for every column of X."""
     A = np.abs(np.asarray(X, dtype=np.float64))
     n = A.shape[0]
@@ -72,6 +76,36 @@ def raw_features(X):
     l2 = np.sqrt((A * A).sum(axis=0))
     med = np.sort(A, axis=0)[(n - 1) // 2]
     return np.stack([l1, l2, med], axis=1)
+
+
+def proxy_rows(n):
+    """Rows of the restricted fit: min(n, max(256, ceil(n / 8)))."""
+    return min(n, max(256, -(-n // 8)))
+
+
+def heavy_rows(X, R):
+    """The R rows of largest l1 norm, in ascending index order.  The norm of a
+    row is the double sum of its |x_ij| taken left to right over j; rows are
+    ranked by that sum rounded to float, ties to the smaller index."""
+    A = np.abs(np.asarray(X, dtype=np.float64))
+    rho = np.cumsum(A, axis=1)[:, -1] if A.shape[1] else np.zeros(A.shape[0])
+    key = rho.astype(np.float32).astype(np.float64)
+    order = np.lexsort((np.arange(key.size), -key))
+    return np.sort(order[:R])
+
+
+def proxy_objective(X, lam, R=None):
+    """z_jhat of Algorithm 1 on the R heaviest rows (every jhat), by the oracle."""
+    import oracle
+    X = np.asarray(X)
+    R = proxy_rows(X.shape[0]) if R is None else R
+    rows = heavy_rows(X, R)
+    return oracle.fit(np.ascontiguousarray(X[rows]), [lam])["z_all"][0]
+
+
+def raw_features(X, lam):
+    """(m, 4): the three column features and the restricted objective."""
+    return np.concatenate([column_features(X), proxy_objective(X, lam)[:, None]], axis=1)
 
 
 def standardise(F):
@@ -91,7 +125,7 @@ def standardise(F):
 # network
 # ---------------------------------------------------------------------------
 def forward(theta, F, keep=False):
-    """Scores for the rows of F (N, 3).  `theta` is used as given (round it
+    """Scores for the rows of F (N, NF).  `theta` is used as given (round it
     with half_weights first to model the half-precision weights)."""
     W1, b1, W2, b2, w3, b3 = unpack(theta)
     F = np.asarray(F, dtype=np.float64)

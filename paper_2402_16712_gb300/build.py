@@ -17,6 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libl1line.so")
+# the bounds-checked build (L1L_CHECKS=1): the same sources, every kernel index
+# checked; l1line.py loads it when L1LINE_LIB names it
+LIB_CHECKS = os.path.join(HERE, "libl1line_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_prep.cu", "k_pairs.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "k_propose.cu",
            "k_path.cu", "k_solpath.cu", "k_probe.cu", "abi.cu"]
@@ -42,15 +45,19 @@ def _deps_mtime() -> float:
     return max(ts)
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps_mtime():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          checks: bool = False) -> str:
+    lib = LIB_CHECKS if checks else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps_mtime():
+        return lib
+    bdir = os.path.join(BUILD, "checks") if checks else BUILD
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
+    extra = ["-DL1L_CHECKS=1"] if checks else []
 
     def one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [cc, *_flags(verbose), "-c", os.path.join(CSRC, src), "-o", obj]
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
+        cmd = [cc, *_flags(verbose), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
@@ -61,15 +68,15 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     if verbose:
         for _, err in results:
             sys.stderr.write(err)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(force="--force" in sys.argv, verbose="-v" in sys.argv)
-    print(LIB)
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv,
+                checks="--checks" in sys.argv))

@@ -14,6 +14,7 @@
 
 #include "../../include/l1line.h"
 #include "batch_split.h"
+#include "checks.cuh"
 #include "common.cuh"
 #include "launch.h"
 
@@ -36,7 +37,7 @@ bool mul_ok(int64_t a, int64_t b, int64_t &out) {
 
 struct Layout {
     size_t status, slow_count, colinfo, Xt, Xf, v_all, s_all, z_all, slow;
-    size_t feat_raw, feat_std, score, idx;  // learned proposer: [m][3], [m][3], [m], [m]
+    size_t feat_raw, feat_std, score, idx;  // learned proposer: [m][4], [m][4], [m], [m]
     size_t total;
     int64_t ldn;
 };
@@ -77,15 +78,49 @@ bool make_layout(int dtype, int64_t n, int64_t m, int64_t nl, Layout &L) {
     L.slow = off;
     off = al256(off + (size_t)chunk_pairs * sizeof(SlowEntry));
     L.feat_raw = off;
-    off = al256(off + (size_t)m * 12);
+    off = al256(off + (size_t)m * 4 * L1L_MLP_FEATURES);
     L.feat_std = off;
-    off = al256(off + (size_t)m * 12);
+    off = al256(off + (size_t)m * 4 * L1L_MLP_FEATURES);
     L.score = off;
     off = al256(off + (size_t)m * 4);
     L.idx = off;
     off = al256(off + (size_t)m * 4);
     L.total = off;
     L.ldn = ldn;
+    return true;
+}
+
+// Rows of the restricted fit behind the proposer's fourth feature.
+int64_t proposer_rows(int64_t n) {
+    if (n < 1) return 0;
+    const int64_t r = std::max<int64_t>(256, (n + 7) / 8);
+    return std::min<int64_t>(n, r);
+}
+
+// Workspace of the proposer calls: the fit's layout, then the restricted
+// fit's row norms, row list, row copy and its own fit workspace.
+struct ProposedLayout {
+    Layout L;
+    int64_t R;
+    size_t rho, rows, xr, pws, pws_bytes, total;
+};
+bool make_proposed_layout(int dtype, int64_t n, int64_t m, int64_t nl, ProposedLayout &P) {
+    if (!make_layout(dtype, n, m, nl, P.L)) return false;
+    P.R = proposer_rows(n);
+    Layout LR;
+    if (!make_layout(dtype, P.R, m, 1, LR)) return false;
+    const size_t es = dtype == L1L_DTYPE_F32 ? 4 : 8;
+    size_t off = al256(P.L.total);
+    P.rho = off;
+    off = al256(off + (size_t)n * 4);
+    P.rows = off;
+    off = al256(off + (size_t)P.R * 4);
+    P.xr = off;
+    off = al256(off + (size_t)P.R * (size_t)m * es);
+    P.pws = off;
+    P.pws_bytes = LR.total;
+    off = al256(off + LR.total);
+    P.total = off;
     return true;
 }
 
@@ -317,17 +352,48 @@ int path_write_impl(const T *X, int64_t n, int64_t m, const int64_t *offsets, do
     return L1L_OK;
 }
 
+// Every feature of the proposer into raw / stdz: the column features of the
+// staged copy, then the restricted objective: row norms, the R heaviest rows
+// copied out, and this library's own fit of them (z only, at lambda) in the
+// workspace region after the main one; its device status joins the main
+// status word.
 template <typename T>
-int features_impl(const T *X, int64_t n, int64_t m, float *out_raw, float *out_std, void *ws,
-                  size_t ws_bytes, void *stream) {
-    if (!out_std) return L1L_ERR_ARG;
+int proposer_features(const T *X, int64_t n, int64_t m, double lambda, Scan<T> &c,
+                      const ProposedLayout &P, float *raw, float *stdz) {
+    if (launch_colfeat<T>(c.a.Xt, c.a.ldn, n, m, raw, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    float *rho = reinterpret_cast<float *>(c.base + P.rho);
+    int32_t *rows = reinterpret_cast<int32_t *>(c.base + P.rows);
+    T *xr = reinterpret_cast<T *>(c.base + P.xr);
+    if (launch_heavy_rows<T>(X, n, m, P.R, rho, rows, xr, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    Scan<T> p;
+    L1L_TRY(scan_setup<T>(xr, P.R, m, &lambda, 1, nullptr, nullptr, nullptr, c.base + P.pws,
+                          P.pws_bytes, c.st, 0u, p));
+    L1L_TRY(scan_prep<T>(xr, p));
+    L1L_TRY(scan_pairs<T>(p, &lambda, 1, nullptr, m));
+    c.launches += p.launches;
+    if (launch_setfeat(p.z, m, 3, raw, c.st, c.launches) != cudaSuccess ||
+        launch_status_or(c.a.status, p.a.status, c.st, c.launches) != cudaSuccess ||
+        launch_featstd(raw, m, stdz, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    return L1L_OK;
+}
+
+template <typename T>
+int features_impl(const T *X, int64_t n, int64_t m, double lambda, float *out_raw,
+                  float *out_std, void *ws, size_t ws_bytes, void *stream) {
+    g_last_launches = 0;
+    if (!X || !out_std || n < 1 || m < 1) return L1L_ERR_ARG;
+    ProposedLayout P;
+    if (!make_proposed_layout(dtype_of<T>(), n, m, 1, P)) return L1L_ERR_UNSUPPORTED;
+    if (ws_bytes < P.total) return L1L_ERR_WORKSPACE;
     Scan<T> c;
-    L1L_TRY(scan_setup<T>(X, n, m, &k_zero_lambda, 1, nullptr, nullptr, nullptr, ws, ws_bytes,
-                          stream, 0u, c));
+    L1L_TRY(scan_setup<T>(X, n, m, &lambda, 1, nullptr, nullptr, nullptr, ws, ws_bytes, stream,
+                          0u, c));
     L1L_TRY(scan_prep<T>(X, c));
     float *raw = out_raw ? out_raw : reinterpret_cast<float *>(c.base + c.L.feat_raw);
-    if (launch_features<T>(c.a.Xt, c.a.ldn, n, m, raw, out_std, c.st, c.launches) != cudaSuccess)
-        return L1L_ERR_CUDA;
+    L1L_TRY(proposer_features<T>(X, n, m, lambda, c, P, raw, out_std));
     g_last_launches = c.launches;
     return L1L_OK;
 }
@@ -336,9 +402,14 @@ template <typename T>
 int proposed_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl,
                   const l1line_mlp *mlp, int64_t K, int32_t *out_idx, T *out_v, double *out_obj,
                   int32_t *out_jstar, void *ws, size_t ws_bytes, void *stream) {
-    if (!mlp || !out_v || !out_obj || !out_jstar) return L1L_ERR_ARG;
+    g_last_launches = 0;
+    if (!X || !lambdas || !mlp || !out_v || !out_obj || !out_jstar || n < 1 || m < 1 || nl < 1)
+        return L1L_ERR_ARG;
     if (K < 1 || K > m) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
+    ProposedLayout P;
+    if (!make_proposed_layout(dtype_of<T>(), n, m, nl, P)) return L1L_ERR_UNSUPPORTED;
+    if (ws_bytes < P.total) return L1L_ERR_WORKSPACE;
     Scan<T> c;
     L1L_TRY(scan_setup<T>(X, n, m, lambdas, nl, nullptr, nullptr, nullptr, ws, ws_bytes, stream,
                           0u, c));
@@ -347,8 +418,8 @@ int proposed_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64
     float *stdz = reinterpret_cast<float *>(c.base + c.L.feat_std);
     float *score = reinterpret_cast<float *>(c.base + c.L.score);
     int32_t *idx = out_idx ? out_idx : reinterpret_cast<int32_t *>(c.base + c.L.idx);
-    if (launch_features<T>(c.a.Xt, c.a.ldn, n, m, raw, stdz, c.st, c.launches) != cudaSuccess ||
-        launch_mlp_forward(stdz, nullptr, m, mlp, score, c.st, c.launches) != cudaSuccess ||
+    L1L_TRY(proposer_features<T>(X, n, m, lambdas[0], c, P, raw, stdz));
+    if (launch_mlp_forward(stdz, nullptr, m, mlp, score, c.st, c.launches) != cudaSuccess ||
         launch_topk(score, m, (int)K, idx, c.st, c.launches) != cudaSuccess)
         return L1L_ERR_CUDA;
     L1L_TRY(scan_pairs<T>(c, lambdas, nl, idx, K));
@@ -434,14 +505,25 @@ int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *l
                             workspace, workspace_bytes, stream);
 }
 
-int l1line_features_f32(const float *X, int64_t n, int64_t m, float *out_raw, float *out_std,
-                        void *workspace, size_t workspace_bytes, void *stream) {
-    return features_impl<float>(X, n, m, out_raw, out_std, workspace, workspace_bytes, stream);
+int64_t l1line_proposer_rows(int64_t n) { return proposer_rows(n); }
+
+size_t l1line_proposed_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t n_lambda) {
+    if (dtype != L1L_DTYPE_F32 && dtype != L1L_DTYPE_F64) return 0;
+    ProposedLayout P;
+    if (!make_proposed_layout(dtype, n, m, n_lambda, P)) return 0;
+    return P.total;
 }
 
-int l1line_features_f64(const double *X, int64_t n, int64_t m, float *out_raw, float *out_std,
-                        void *workspace, size_t workspace_bytes, void *stream) {
-    return features_impl<double>(X, n, m, out_raw, out_std, workspace, workspace_bytes, stream);
+int l1line_features_f32(const float *X, int64_t n, int64_t m, double lambda, float *out_raw,
+                        float *out_std, void *workspace, size_t workspace_bytes, void *stream) {
+    return features_impl<float>(X, n, m, lambda, out_raw, out_std, workspace, workspace_bytes,
+                                stream);
+}
+
+int l1line_features_f64(const double *X, int64_t n, int64_t m, double lambda, float *out_raw,
+                        float *out_std, void *workspace, size_t workspace_bytes, void *stream) {
+    return features_impl<double>(X, n, m, lambda, out_raw, out_std, workspace, workspace_bytes,
+                                 stream);
 }
 
 int l1line_mlp_forward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
@@ -741,6 +823,35 @@ const char *l1line_status_string(int status) {
 }
 
 int l1line_last_launch_count(void) { return g_last_launches; }
+
+#if L1L_CHECKS
+extern "C" long long l1l_checks_pairs(int, int *);
+extern "C" long long l1l_checks_batch(int, int *);
+extern "C" long long l1l_checks_exact(int, int *);
+extern "C" long long l1l_checks_path(int, int *);
+extern "C" long long l1l_checks_solpath(int, int *);
+extern "C" long long l1l_checks_propose(int, int *);
+#endif
+
+int64_t l1line_check_hits(int reset, int *line) {
+#if L1L_CHECKS
+    if (cudaDeviceSynchronize() != cudaSuccess) return -2;
+    long long (*readers[])(int, int *) = {l1l_checks_pairs, l1l_checks_batch, l1l_checks_exact,
+                                          l1l_checks_path, l1l_checks_solpath,
+                                          l1l_checks_propose};
+    long long total = 0;
+    for (auto r : readers) {
+        const long long h = r(reset, line);
+        if (h < 0) return -2;
+        total += h;
+    }
+    return total;
+#else
+    (void)reset;
+    (void)line;
+    return -1;
+#endif
+}
 
 int l1line_set_tuning(const l1line_tuning *t) {
     if (!t) {

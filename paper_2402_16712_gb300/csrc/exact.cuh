@@ -5,6 +5,7 @@
 // and so every float, is an integer multiple of it), reduced across the warp
 // limb by limb and compared with the exact total W = sum w + lambda.
 #pragma once
+#include "checks.cuh"
 #include "common.cuh"
 
 namespace l1l {
@@ -90,8 +91,8 @@ __device__ void exact_entry(const ScanArgs<T> &a, const SlowEntry &en, double la
     using K = typename Tr::K;
     const int n = (int)a.n;
     const int64_t m = a.m;
-    const T *xk = a.Xt + (int64_t)en.k * a.ldn;
-    const T *xj = a.Xt + (int64_t)en.j * a.ldn;
+    const T *xk = a.Xt + (int64_t)L1L_CHK(en.k, (int32_t)m) * a.ldn;
+    const T *xj = a.Xt + (int64_t)L1L_CHK(en.j, (int32_t)m) * a.ldn;
     K ts = Tr::KEY0;
     if (a.ci[en.j].n_valid > 0) {
         // exact total W = sum_i |x_ijhat| + lambda
@@ -137,7 +138,8 @@ __device__ void exact_entry(const ScanArgs<T> &a, const SlowEntry &en, double la
     const T v = Tr::value(ts);
     const T res = warp_residual<T>(xk, xj, n, v, lane);
     if (lane == 0) {
-        const int64_t o = ((int64_t)en.t * m + en.j) * m + en.k;
+        const int64_t o =
+            L1L_CHK(((int64_t)en.t * m + en.j) * m + en.k, (int64_t)a.n_lambda * m * m);
         a.v_all[o] = v;
         a.s_all[o] = (double)res + lam * (double)fabs(v);
     }

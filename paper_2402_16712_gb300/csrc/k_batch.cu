@@ -227,4 +227,6 @@ template cudaError_t launch_batch<double>(const BatchDesc<double> &, unsigned ch
                                           double *, int32_t *, const BatchClass *, int, bool, int,
                                           cudaStream_t, int &);
 
+L1L_CHECKS_READER(l1l_checks_batch)
+
 }  // namespace l1l

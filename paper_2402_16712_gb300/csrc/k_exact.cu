@@ -46,4 +46,6 @@ template cudaError_t launch_exact<float>(const ScanArgs<float> &, const double *
 template cudaError_t launch_exact<double>(const ScanArgs<double> &, const double *, int, int, int,
                                           cudaStream_t, int &);
 
+L1L_CHECKS_READER(l1l_checks_exact)
+
 }  // namespace l1l

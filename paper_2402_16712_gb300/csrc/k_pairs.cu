@@ -218,4 +218,6 @@ template cudaError_t launch_pairs<float>(const ScanArgs<float> &, const double *
 template cudaError_t launch_pairs<double>(const ScanArgs<double> &, const double *, int, int,
                                           const PairPlan &, cudaStream_t, int &);
 
+L1L_CHECKS_READER(l1l_checks_pairs)
+
 }  // namespace l1l

@@ -18,6 +18,7 @@
 // with a list in global scratch.
 #include <cmath>
 
+#include "checks.cuh"
 #include "common.cuh"
 #include "launch.h"
 #include "pairs.cuh"
@@ -165,6 +166,7 @@ __device__ void emit_path(const PathArgs<T> &a, int64_t p, T v0, bool pos,
     using K = typename Tr::K;
     const unsigned FULL = 0xFFFFFFFFu;
     const int64_t o = a.off[p];
+    const int64_t room = a.off[p + 1] - o;  // entries the count pass reserved
     // number of runs of equal keys
     int groups = 0;
     for (int i0 = 0; i0 < c; i0 += 32) {
@@ -172,6 +174,8 @@ __device__ void emit_path(const PathArgs<T> &a, int64_t p, T v0, bool pos,
         const bool end = i < c && (i == c - 1 || keys[i] != keys[i + 1]);
         groups += __popc(__ballot_sync(FULL, end));
     }
+    // the entries 0 .. groups lie inside the room the count pass reserved
+    L1L_CHK((int64_t)groups, room);
     int64_t carry = Sbelow;  // S at the end of the previous chunk
     double cA = rs.Ab, cB = rs.Bb;  // residual sums at the end of the previous chunk
     double cQrun = 0.0;             // corrections of the run open at the chunk's end
@@ -620,5 +624,7 @@ template cudaError_t launch_path<double>(bool, const double *, const float *, co
                                          int64_t *, double *, double *, double *, int32_t *,
                                          int32_t *, uint32_t *, unsigned char *, uint32_t *, int,
                                          cudaStream_t, int &);
+
+L1L_CHECKS_READER(l1l_checks_path)
 
 }  // namespace l1l

@@ -1,5 +1,6 @@
 // k_propose.cu -- the learned jhat proposer (not part of the paper): column
-// features, the 3-128-128-1 ReLU network (forward, backward, Adam), the
+// features (and the row norms and row gather of the restricted-objective
+// feature), the 4-128-128-1 ReLU network (forward, backward, Adam), the
 // listwise training loss and the top-K selection of candidate columns.
 //
 // The network's weight matrices are stored in binary16 and widened to float
@@ -8,6 +9,7 @@
 #include <cfloat>
 #include <cuda_fp16.h>
 
+#include "checks.cuh"
 #include "common.cuh"
 #include "l1line.h"
 #include "launch.h"
@@ -17,11 +19,12 @@ namespace l1l {
 namespace {
 
 constexpr int HID = L1L_MLP_HIDDEN;  // 128
-constexpr int NPAR = L1L_MLP_PARAMS;  // 17153
-constexpr int OFF_B1 = HID * 3, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
+constexpr int NF = L1L_MLP_FEATURES;  // 4
+constexpr int NPAR = L1L_MLP_PARAMS;  // 17281
+constexpr int OFF_B1 = HID * NF, OFF_W2 = OFF_B1 + HID, OFF_B2 = OFF_W2 + HID * HID,
               OFF_W3 = OFF_B2 + HID, OFF_B3 = OFF_W3 + HID;
 static_assert(OFF_B3 + 1 == NPAR, "parameter layout");
-static_assert(sizeof(l1line_mlp) == 34832, "packed network image");
+static_assert(sizeof(l1line_mlp) == 35088, "packed network image");
 constexpr int TS = MLP_TILE;  // samples per CTA
 constexpr int LD = HID + 1;   // shared row stride in floats (conflict-free column walks)
 constexpr int NT = 256;
@@ -132,7 +135,7 @@ __global__ void __launch_bounds__(NT) k_colfeat(const T *__restrict__ Xt, int64_
         for (int b = threadIdx.x; b < 256; b += NT) hist[b] = 0u;
         __syncthreads();
         for (int i = threadIdx.x; i < n; i += NT) {
-            const uint32_t k = keys[i];
+            const uint32_t k = keys[L1L_CHK(i, n)];
             if (pass == 0 || (uint32_t)((uint64_t)k >> (shift + 8)) == s.prefix)
                 atomicAdd(&hist[(k >> shift) & 255u], 1u);
         }
@@ -140,10 +143,44 @@ __global__ void __launch_bounds__(NT) k_colfeat(const T *__restrict__ Xt, int64_
         radix_pick(hist, s, &sel);
     }
     if (threadIdx.x == 0) {
-        raw[j * 3 + 0] = (float)fmin(s1, (double)FLT_MAX);
-        raw[j * 3 + 1] = (float)fmin(sqrt(s2), (double)FLT_MAX);
-        raw[j * 3 + 2] = __uint_as_float(s.prefix);
+        raw[j * NF + 0] = (float)fmin(s1, (double)FLT_MAX);
+        raw[j * NF + 1] = (float)fmin(sqrt(s2), (double)FLT_MAX);
+        raw[j * NF + 2] = __uint_as_float(s.prefix);
     }
+}
+
+// Row weights of the restricted-objective feature: rho_i = sum_j |x_ij| in
+// double, added left to right over j (one thread per row of the row-major X;
+// the fixed order makes the sum reproducible), rounded to float.
+template <typename T>
+__global__ void __launch_bounds__(NT) k_rownorm(const T *__restrict__ X, int64_t n, int64_t m,
+                                                 float *__restrict__ rho) {
+    const int64_t i = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (i >= n) return;
+    const T *x = X + i * m;
+    double s = 0.0;
+    for (int64_t j = 0; j < m; ++j) s += fabs((double)x[j]);
+    rho[i] = (float)fmin(s, (double)FLT_MAX);
+}
+
+// Rows[r] of X (row-major n x m) into Y (row-major R x m).
+template <typename T>
+__global__ void __launch_bounds__(NT) k_gather_rows(const T *__restrict__ X, int64_t n, int64_t m,
+                                                     const int32_t *__restrict__ rows,
+                                                     T *__restrict__ Y) {
+    const int64_t r = blockIdx.x;
+    const T *x = X + (int64_t)L1L_CHK(rows[r], (int32_t)n) * m;
+    T *y = Y + r * m;
+    for (int64_t j = threadIdx.x; j < m; j += NT) y[j] = x[j];
+}
+
+__global__ void k_status_or(uint32_t *dst, const uint32_t *src) { *dst |= *src; }
+
+// raw[j][c] = z[j] (the restricted objective, rounded to float).
+__global__ void __launch_bounds__(NT) k_setfeat(const double *__restrict__ z, int64_t m, int c,
+                                                 float *__restrict__ raw) {
+    const int64_t j = (int64_t)blockIdx.x * NT + threadIdx.x;
+    if (j < m) raw[j * NF + c] = (float)fmin(fmax(z[j], -(double)FLT_MAX), (double)FLT_MAX);
 }
 
 // Per feature: (f - mean) / population standard deviation over the m
@@ -151,18 +188,18 @@ __global__ void __launch_bounds__(NT) k_colfeat(const T *__restrict__ Xt, int64_
 __global__ void __launch_bounds__(NT) k_featstd(const float *__restrict__ raw, int64_t m,
                                                  float *__restrict__ out) {
     __shared__ double red[NT / 32];
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NF; ++c) {
         double s = 0.0;
-        for (int64_t j = threadIdx.x; j < m; j += NT) s += raw[j * 3 + c];
+        for (int64_t j = threadIdx.x; j < m; j += NT) s += raw[j * NF + c];
         const double mean = block_sum_f64(s, red) / (double)m;
         double v = 0.0;
         for (int64_t j = threadIdx.x; j < m; j += NT) {
-            const double d = raw[j * 3 + c] - mean;
+            const double d = raw[j * NF + c] - mean;
             v += d * d;
         }
         const double sd = sqrt(block_sum_f64(v, red) / (double)m);
         for (int64_t j = threadIdx.x; j < m; j += NT)
-            out[j * 3 + c] = sd > 0.0 ? (float)((raw[j * 3 + c] - mean) / sd) : 0.0f;
+            out[j * NF + c] = sd > 0.0 ? (float)((raw[j * NF + c] - mean) / sd) : 0.0f;
     }
 }
 
@@ -171,10 +208,10 @@ __global__ void __launch_bounds__(NT) k_featstd(const float *__restrict__ raw, i
 // ---------------------------------------------------------------------------
 struct MlpSmem {
     float w2[HID * LD];  // w2[o * LD + i]
-    float w1[HID * 3];
+    float w1[HID * NF];
     float b1[HID], b2[HID], w3[HID];
     float b3;
-    float f[TS * 3];
+    float f[TS * NF];
     float h1[TS * LD];  // h1, then (backward) g1
     float h2[TS * LD];  // h2, then (backward) g2; forward-only: partial scores
     float ds[TS];
@@ -184,7 +221,7 @@ __device__ __forceinline__ float h2f(uint16_t b) { return __half2float(__ushort_
 
 __device__ void mlp_load(const l1line_mlp *__restrict__ p, MlpSmem &S) {
     for (int e = threadIdx.x; e < HID * HID; e += NT) S.w2[(e >> 7) * LD + (e & 127)] = h2f(p->w2[e]);
-    for (int e = threadIdx.x; e < HID * 3; e += NT) S.w1[e] = h2f(p->w1[e]);
+    for (int e = threadIdx.x; e < HID * NF; e += NT) S.w1[e] = h2f(p->w1[e]);
     for (int e = threadIdx.x; e < HID; e += NT) {
         S.b1[e] = p->b1[e];
         S.b2[e] = p->b2[e];
@@ -200,9 +237,8 @@ __device__ void mlp_tile_forward(MlpSmem &S, int cnt, float *__restrict__ score_
     for (int e = threadIdx.x; e < TS * HID; e += NT) {
         const int s = e >> 7, i = e & 127;
         float a = S.b1[i];
-        a = fmaf(S.w1[i * 3 + 0], S.f[s * 3 + 0], a);
-        a = fmaf(S.w1[i * 3 + 1], S.f[s * 3 + 1], a);
-        a = fmaf(S.w1[i * 3 + 2], S.f[s * 3 + 2], a);
+#pragma unroll
+        for (int c = 0; c < NF; ++c) a = fmaf(S.w1[i * NF + c], S.f[s * NF + c], a);
         S.h1[s * LD + i] = fmaxf(a, 0.0f);
     }
     __syncthreads();
@@ -249,12 +285,12 @@ __device__ void mlp_tile_forward(MlpSmem &S, int cnt, float *__restrict__ score_
 
 __device__ void load_tile_features(MlpSmem &S, const float *__restrict__ feat,
                                    const int32_t *__restrict__ rows, int64_t base, int cnt) {
-    for (int e = threadIdx.x; e < TS * 3; e += NT) {
-        const int s = e / 3, c = e - 3 * (e / 3);
+    for (int e = threadIdx.x; e < TS * NF; e += NT) {
+        const int s = e / NF, c = e - NF * (e / NF);
         float v = 0.0f;
         if (s < cnt) {
             const int64_t r = rows ? (int64_t)rows[base + s] : base + s;
-            v = feat[r * 3 + c];
+            v = feat[r * NF + c];
         }
         S.f[e] = v;
     }
@@ -370,17 +406,17 @@ __global__ void __launch_bounds__(NT) k_mlp_bwd(const float *__restrict__ feat,
     __syncthreads();
     if (threadIdx.x < HID) {
         const int i = threadIdx.x;
-        float d0 = 0.0f, d1 = 0.0f, d2 = 0.0f, db1 = 0.0f;
+        float d[NF], db1 = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) d[c] = 0.0f;
         for (int s = 0; s < TS; ++s) {
             const float g1 = S.h1[s * LD + i];
-            d0 = fmaf(g1, S.f[s * 3 + 0], d0);
-            d1 = fmaf(g1, S.f[s * 3 + 1], d1);
-            d2 = fmaf(g1, S.f[s * 3 + 2], d2);
+#pragma unroll
+            for (int c = 0; c < NF; ++c) d[c] = fmaf(g1, S.f[s * NF + c], d[c]);
             db1 += g1;
         }
-        g[i * 3 + 0] = d0;
-        g[i * 3 + 1] = d1;
-        g[i * 3 + 2] = d2;
+#pragma unroll
+        for (int c = 0; c < NF; ++c) g[i * NF + c] = d[c];
         g[OFF_B1 + i] = db1;
     }
 }
@@ -534,7 +570,7 @@ __global__ void __launch_bounds__(TK_NT) k_topk(const float *__restrict__ score,
         const uint32_t k = score_key(score[i]);
         bool in = k < T;
         if (k == T) in = er++ < need;
-        if (in) out[pos++] = (int32_t)i;
+        if (in) out[L1L_CHK(pos++, (uint32_t)K)] = (int32_t)i;
     }
 }
 
@@ -542,16 +578,51 @@ __global__ void __launch_bounds__(TK_NT) k_topk(const float *__restrict__ score,
 
 size_t mlp_smem_bytes() { return sizeof(MlpSmem); }
 
+L1L_CHECKS_READER(l1l_checks_propose)
+
 template <typename T>
-cudaError_t launch_features(const T *Xt, int64_t ldn, int64_t n, int64_t m, float *raw,
-                            float *stdz, cudaStream_t st, int &launches) {
+cudaError_t launch_colfeat(const T *Xt, int64_t ldn, int64_t n, int64_t m, float *raw,
+                           cudaStream_t st, int &launches) {
     const size_t smem = (size_t)n * 4;
     cudaError_t e = ensure_smem(reinterpret_cast<const void *>(k_colfeat<T>), smem);
     if (e != cudaSuccess) return e;
     k_colfeat<T><<<(unsigned)m, NT, smem, st>>>(Xt, ldn, (int)n, raw);
     launches++;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_featstd(const float *raw, int64_t m, float *stdz, cudaStream_t st,
+                           int &launches) {
     k_featstd<<<1, NT, 0, st>>>(raw, m, stdz);
+    launches++;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_heavy_rows(const T *X, int64_t n, int64_t m, int64_t R, float *rho,
+                              int32_t *rows, T *Y, cudaStream_t st, int &launches) {
+    k_rownorm<T><<<(unsigned)((n + NT - 1) / NT), NT, 0, st>>>(X, n, m, rho);
+    launches++;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_topk<<<1, TK_NT, 0, st>>>(rho, n, (int)R, rows);
+    launches++;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gather_rows<T><<<(unsigned)R, NT, 0, st>>>(X, n, m, rows, Y);
+    launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status_or(uint32_t *dst, const uint32_t *src, cudaStream_t st,
+                             int &launches) {
+    k_status_or<<<1, 1, 0, st>>>(dst, src);
+    launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setfeat(const double *z, int64_t m, int c, float *raw, cudaStream_t st,
+                           int &launches) {
+    k_setfeat<<<(unsigned)((m + NT - 1) / NT), NT, 0, st>>>(z, m, c, raw);
     launches++;
     return cudaGetLastError();
 }
@@ -611,9 +682,13 @@ cudaError_t launch_topk(const float *score, int64_t m, int K, int32_t *out, cuda
     return cudaGetLastError();
 }
 
-template cudaError_t launch_features<float>(const float *, int64_t, int64_t, int64_t, float *,
-                                            float *, cudaStream_t, int &);
-template cudaError_t launch_features<double>(const double *, int64_t, int64_t, int64_t, float *,
-                                             float *, cudaStream_t, int &);
+template cudaError_t launch_colfeat<float>(const float *, int64_t, int64_t, int64_t, float *,
+                                           cudaStream_t, int &);
+template cudaError_t launch_colfeat<double>(const double *, int64_t, int64_t, int64_t, float *,
+                                            cudaStream_t, int &);
+template cudaError_t launch_heavy_rows<float>(const float *, int64_t, int64_t, int64_t, float *,
+                                              int32_t *, float *, cudaStream_t, int &);
+template cudaError_t launch_heavy_rows<double>(const double *, int64_t, int64_t, int64_t,
+                                               float *, int32_t *, double *, cudaStream_t, int &);
 
 }  // namespace l1l

@@ -527,4 +527,6 @@ template cudaError_t launch_solpath<double>(int64_t, const int64_t *, const int3
                                             double *, double *, double *, int64_t *, int64_t,
                                             cudaStream_t, int &);
 
+L1L_CHECKS_READER(l1l_checks_solpath)
+
 }  // namespace l1l

@@ -71,9 +71,23 @@ cudaError_t launch_deflate(const T *X, T *Y, int64_t n, int64_t m, const int32_t
 // ---- learned jhat proposer (k_propose.cu) ----
 constexpr int MLP_TILE = 64;  // samples per CTA of the network kernels
 size_t mlp_smem_bytes();
+// Column features 0..2 of the staged copy into raw [m][L1L_MLP_FEATURES].
 template <typename T>
-cudaError_t launch_features(const T *Xt, int64_t ldn, int64_t n, int64_t m, float *raw,
-                            float *stdz, cudaStream_t st, int &launches);
+cudaError_t launch_colfeat(const T *Xt, int64_t ldn, int64_t n, int64_t m, float *raw,
+                           cudaStream_t st, int &launches);
+// Standardises every feature column of raw over the m columns.
+cudaError_t launch_featstd(const float *raw, int64_t m, float *stdz, cudaStream_t st,
+                           int &launches);
+// The R rows of largest l1 norm of the row-major X (rho: row norms [n],
+// rows: their indices in ascending order [R]) copied into Y (R x m).
+template <typename T>
+cudaError_t launch_heavy_rows(const T *X, int64_t n, int64_t m, int64_t R, float *rho,
+                              int32_t *rows, T *Y, cudaStream_t st, int &launches);
+// *dst |= *src (device status words), one thread.
+cudaError_t launch_status_or(uint32_t *dst, const uint32_t *src, cudaStream_t st, int &launches);
+// raw[j][c] = z[j] for j < m.
+cudaError_t launch_setfeat(const double *z, int64_t m, int c, float *raw, cudaStream_t st,
+                           int &launches);
 cudaError_t launch_mlp_forward(const float *feat, const int32_t *rows, int64_t N,
                                const l1line_mlp *p, float *score, cudaStream_t st, int &launches);
 cudaError_t launch_mlp_backward(const float *feat, const int32_t *rows, int64_t N,

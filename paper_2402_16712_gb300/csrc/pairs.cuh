@@ -42,6 +42,7 @@
 #include <cmath>
 
 #include "binmap.cuh"
+#include "checks.cuh"
 #include "common.cuh"
 
 namespace l1l {
@@ -263,6 +264,7 @@ __device__ __forceinline__ void hist_zero(uint32_t *h, int lane) {
     for (int q = 0; q < (4 * XB) / 32; ++q) h[q * 32 + lane] = 0u;
 }
 __device__ __forceinline__ void hist_add(uint32_t *h, int bin, int64_t q) {
+    bin = L1L_CHK(bin, XB);
     const uint64_t u = (uint64_t)q;
     atomicAdd(&h[bin], (uint32_t)(u & 0xFFFFu));
     atomicAdd(&h[XB + bin], (uint32_t)((u >> 16) & 0xFFFFu));
@@ -381,6 +383,10 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     const unsigned FULL = 0xFFFFFFFFu;
     const float Qf = (float)dc.Q;
     const float hneg0 = 0.5f * (Qf + (float)dc.Lf), hpos0 = 0.5f * (Qf - (float)dc.Lc);
+    const int nrow = (n + ROW_PAD - 1) & ~(ROW_PAD - 1);  // rows the columns hold
+    const int nslot = qt * 32;                             // candidate slots
+    (void)nrow;
+    (void)nslot;
 
     // ---------------- level 0 -------------------------------------------
     // 64 rows drawn in proportion to their weight (each stands for Q/64), so the
@@ -388,7 +394,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     uint32_t sk[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const int i = samp[e * 32 + lane];
+        const int i = L1L_CHK((int)samp[e * 32 + lane], nrow);
         sk[e] = akey(__fmul_rn(xf[i], inv[i]));
     }
     warp_sort64(sk, lane);
@@ -535,8 +541,8 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
                 Sb += below ? q : 0;
                 // speculative store: the slot is only kept when cnt advances
                 if (cnt < qt) {
-                    lk[cnt * 32 + lane] = kk;
-                    li[cnt * 32 + lane] = (uint16_t)i;
+                    lk[L1L_CHK(cnt * 32 + lane, nslot)] = kk;
+                    li[cnt * 32 + lane] = (uint16_t)L1L_CHK(i, nrow);
                 }
                 cnt += cand ? 1 : 0;
             }
@@ -559,9 +565,9 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         int64_t Sb2 = 0;
 #pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
-            const int p = j * 32 + lane;
+            const int p = L1L_CHK(j * 32 + lane, nslot);
             uint32_t kk = lk[p];
-            const uint16_t id = li[p];
+            const uint16_t id = (uint16_t)L1L_CHK((int)li[p], nrow);
             // clear: the keys G either side fall in the same bin
             const bool clear = kk >= g1 && kk <= g2 && bm.bin(kk - G) == bm.bin(kk + G);
             if (!clear) {
@@ -632,9 +638,10 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
         __syncwarp();
 #pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
-            const int p = j * 32 + lane;
+            const int p = L1L_CHK(j * 32 + lane, nslot);
             uint32_t kk = lk[p];
             uint16_t id = li[p];
+            L1L_CHK((int)(id & ROW_MASK), nrow);
             const uint32_t off = (kk - lo) & bmask;
             if (!(id & EXACT_BIT) && (off < G || off + G > bmask)) {
                 const int row = id & ROW_MASK;
@@ -701,13 +708,14 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
     {
         const int excl = warp_scan_add(cnt, lane) - cnt;
         uint16_t *stage = reinterpret_cast<uint16_t *>(hist);
-        for (int j = 0; j < cnt; ++j) stage[excl + j] = li[j * 32 + lane] & ROW_MASK;
+        for (int j = 0; j < cnt; ++j)
+            stage[L1L_CHK(excl + j, 31)] = li[L1L_CHK(j * 32 + lane, nslot)] & ROW_MASK;
     }
     __syncwarp();
     K fk = Tr::NONE;
     int64_t fq = 0;
     if (lane < c) {
-        const int row = reinterpret_cast<const uint16_t *>(hist)[lane];
+        const int row = L1L_CHK((int)reinterpret_cast<const uint16_t *>(hist)[lane], nrow);
         fk = Tr::key(Tr::div_rn(xk[row], colb[row]));
         fq = colq(row);
     } else if (lane == c && lo <= CK0 && CK0 <= hi) {
@@ -852,7 +860,7 @@ __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int
                           double lam, int lane) {
     using Tr = Traits<T>;
     const int64_t m = a.m;
-    const int64_t o = ((int64_t)t * m + j) * m + k;
+    const int64_t o = L1L_CHK(((int64_t)t * m + j) * m + k, (int64_t)a.n_lambda * m * m);
     if (st >= SEL_SLOW) {
         if (lane == 0) {
             uint32_t slot = atomicAdd(a.slow_count, 1u);
@@ -978,7 +986,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
     K fk = Tr::NONE;
     int64_t fq = 0;
     if (lane < c) {
-        const int row = stage[lane];
+        const int row = L1L_CHK((int)stage[lane], (n + ROW_PAD - 1) & ~(ROW_PAD - 1));
         fk = Tr::key(Tr::div_rn(xk[row], w.colb[row]));
         fq = w.q(row);
     } else if (lane == c && Klo <= Tr::KEY0 && Tr::KEY0 <= Khi) {
@@ -1104,7 +1112,7 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
             int s0 = (int)floor(x0) + 1, s1 = (int)floor(x1);
             s0 = max(s0, 0);
             s1 = min(s1, NSAMP - 1);
-            for (int sidx = s0; sidx <= s1; ++sidx) samp[sidx] = (uint16_t)r;
+            for (int sidx = s0; sidx <= s1; ++sidx) samp[L1L_CHK(sidx, NSAMP)] = (uint16_t)r;
             before = after;
         }
         __syncthreads();
@@ -1134,7 +1142,8 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     for (int64_t k = k0 + warp; k < k1; k += nw) {
         if (k == j) {  // v_jhat = 1: zero residual, penalty lambda * 1
             for (int tl = lane; tl < nlc; tl += 32) {
-                int64_t o = ((int64_t)(t0 + tl) * m + j) * m + k;
+                int64_t o = L1L_CHK(((int64_t)(t0 + tl) * m + j) * m + k,
+                                    (int64_t)a.n_lambda * m * m);
                 a.v_all[o] = T(1);
                 a.s_all[o] = lp.lam[tl];
             }

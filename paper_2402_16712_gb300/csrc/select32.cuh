@@ -21,6 +21,7 @@
 #include <cstdint>
 
 #include "binmap.cuh"
+#include "checks.cuh"
 #include "common.cuh"
 
 namespace l1l {
@@ -217,8 +218,8 @@ __device__ __forceinline__ int hist32_cross(const uint32_t *h, const BinMapA *bm
                                             const Decide &dc, int64_t *below, int lane) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int b0 = 2 * lane, b1 = 2 * lane + 1;
-    const uint32_t s0 = b0 < nbins ? h[b0] : 0u;
-    const uint32_t s1 = b1 < nbins ? h[b1] : 0u;
+    const uint32_t s0 = b0 < nbins ? h[L1L_CHK(b0, XB32)] : 0u;
+    const uint32_t s1 = b1 < nbins ? h[L1L_CHK(b1, XB32)] : 0u;
     uint32_t incl = s0 + s1;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -248,7 +249,7 @@ __device__ __forceinline__ int hist32_cross(const uint32_t *h, const BinMapA *bm
 // Keeps, lane-locally and in place, the entries whose key lies in [K1, K2]
 // (every entry is KEYED afterwards); returns this lane's new count.
 __device__ __forceinline__ int list32_keep(uint2 *__restrict__ lst, int cnt, uint32_t K1,
-                                           uint32_t K2, int lane) {
+                                           uint32_t K2, int lane, int nslot) {
     // every lane runs to the warp's largest count (no divergent loop exit);
     // slots past a lane's own count are read but not used
     const int cmax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)cnt);
@@ -257,9 +258,10 @@ __device__ __forceinline__ int list32_keep(uint2 *__restrict__ lst, int cnt, uin
 #pragma unroll 1
     for (int j = 0; j < cmax; ++j) {
         const bool act = j < cnt;
-        const uint2 e = lst[j * 32 + lane];
+        const uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];
         const uint32_t kk = (e.y & E32_KEYED) ? e.x : akey(__uint_as_float(e.x));
-        st_shared_v2_if(act, base + 256u * (uint32_t)w, kk, e.y | E32_KEYED);  // w <= j
+        st_shared_v2_if(act, base + 256u * (uint32_t)L1L_CHK(w, nslot / 32), kk,
+                        e.y | E32_KEYED);  // w <= j
         w += (act & (kk >= K1) & (kk <= K2)) ? 1 : 0;
     }
     return w;
@@ -282,12 +284,14 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
     const float Qf = (float)dc.Q;
     const float hneg0 = 0.5f * (Qf + (float)dc.Lf), hpos0 = 0.5f * (Qf - (float)dc.Lc);
     const int ng = (n + 127) >> 7;  // 128-row groups (rows are padded to them)
+    const int nrow = ng * 128;      // rows every staged or copied column holds
+    const int nslot = qt * 32;      // candidate slots of this warp's list
 
     // ---------------- sample bracket ------------------------------------
     uint32_t sk[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
-        const int i = samp[e * 32 + lane];
+        const int i = L1L_CHK((int)samp[e * 32 + lane], nrow);
         sk[e] = akey(__fmul_rn(__ldg(xk + i), inv[i]));
     }
     warp_sort64(sk, lane);
@@ -375,7 +379,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
 #pragma unroll 1
             for (int j = 0; j < cmax; ++j) {
                 const bool act = j < cnt;
-                const uint2 e = lst[j * 32 + lane];  // fresh entries: (ratio bits, row)
+                const uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];  // fresh: (ratio bits, row)
                 const uint32_t kk = akey(__uint_as_float(e.x));
                 const bool clear = act & (kk >= g1) & (kk <= g2) &
                                    (((kk - G - bm.base) >> bm.sh) == ((kk + G - bm.base) >> bm.sh));
@@ -384,8 +388,8 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
                 const int bx = kk < CK0 ? dn : nb1 - dp;
                 const int bu = (int)((kk - bm.base) >> bm.sh);
                 const int b = bm.cross ? bx : bu;
-                const uint32_t q = q32[act ? e.y : 0u];
-                red_shared_add_if(clear, ahist + 4u * (uint32_t)b, q);
+                const uint32_t q = q32[act ? L1L_CHK(e.y, (uint32_t)nrow) : 0u];
+                red_shared_add_if(clear, ahist + 4u * (uint32_t)L1L_CHK(clear ? b : 0, XB32), q);
                 const bool pj = act & !clear;
                 st_shared_u32_if(pj, ebase + 256u * (uint32_t)j + 4u, e.y | E32_PEND);
                 pend |= pj;
@@ -394,16 +398,16 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
         uint32_t Sb2 = 0;
         if (__any_sync(FULL, pend)) {
             for (int j = 0; j < cnt; ++j) {
-                const uint2 e = lst[j * 32 + lane];
+                const uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];
                 if (e.y & E32_PEND) {
-                    const uint32_t id = e.y & E32_ROW;
+                    const uint32_t id = L1L_CHK(e.y & E32_ROW, (uint32_t)nrow);
                     const uint32_t kk = ckey(__fdiv_rn(__ldg(xk + id), colb[id]));
                     lst[j * 32 + lane] = make_uint2(kk, id | E32_EXACT | E32_KEYED);
                     const uint32_t q = q32[id];
                     if (kk < P1)
                         Sb2 += q;
                     else if (kk <= P2)
-                        red_shared_add(ahist + 4u * (uint32_t)bm.bin(kk), q);
+                        red_shared_add(ahist + 4u * (uint32_t)L1L_CHK(bm.bin(kk), XB32), q);
                 }
             }
         }
@@ -431,7 +435,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
             continue;
         }
         const uint32_t K1 = bm.lower(bs), K2 = bm.upper(bs);
-        cnt = list32_keep(lst, cnt, K1, K2, lane);
+        cnt = list32_keep(lst, cnt, K1, K2, lane, nslot);
         __syncwarp();
         L = below;
         lo = K1;
@@ -455,15 +459,15 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
         __syncwarp();
 #pragma unroll 2
         for (int j = 0; j < cnt; ++j) {
-            uint2 e = lst[j * 32 + lane];  // KEYED
-            const uint32_t id = e.y & E32_ROW;
+            uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];  // KEYED
+            const uint32_t id = L1L_CHK(e.y & E32_ROW, (uint32_t)nrow);
             uint32_t kk = e.x;
             const uint32_t off = (kk - lo) & bmask;
             if (!(e.y & E32_EXACT) && (off < G || off + G > bmask)) {
                 kk = ckey(__fdiv_rn(__ldg(xk + id), colb[id]));
                 lst[j * 32 + lane] = make_uint2(kk, id | E32_EXACT | E32_KEYED);
             }
-            red_shared_add(ahist + 4u * ((kk - lo) >> sh), q32[id]);
+            red_shared_add(ahist + 4u * L1L_CHK((kk - lo) >> sh, (uint32_t)XB32), q32[id]);
         }
         __syncwarp();
         int64_t below = 0;
@@ -473,7 +477,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
         if (bs < 0) return SEL_INTERNAL;
         const uint32_t K1 = lo + ((uint32_t)bs << sh);
         const uint32_t K2 = min(hi, K1 + bmask);
-        cnt = list32_keep(lst, cnt, K1, K2, lane);
+        cnt = list32_keep(lst, cnt, K1, K2, lane, nslot);
         __syncwarp();
         L = below;
         lo = K1;
@@ -490,13 +494,14 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
     {
         const int excl = warp_scan_add(cnt, lane) - cnt;
         uint32_t *stage = hist;
-        for (int j = 0; j < cnt; ++j) stage[excl + j] = lst[j * 32 + lane].y & E32_ROW;
+        for (int j = 0; j < cnt; ++j)
+            stage[L1L_CHK(excl + j, 31)] = lst[L1L_CHK(j * 32 + lane, nslot)].y & E32_ROW;
     }
     __syncwarp();
     const bool zero_in = lo <= CK0 && CK0 <= hi;
     uint32_t fk = CKNONE, fq = 0;
     if (lane < c) {
-        const uint32_t row = hist[lane];
+        const uint32_t row = L1L_CHK(hist[lane], (uint32_t)nrow);
         fk = ckey(__fdiv_rn(__ldg(xk + row), colb[row]));
         fq = q32[row];
     } else if (lane == c && zero_in) {

@@ -13,7 +13,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libl1line.so")
+# L1LINE_LIB selects another build of the same library (the bounds-checked
+# libl1line_checks.so)
+LIB_PATH = os.environ.get("L1LINE_LIB") or os.path.join(_HERE, "libl1line.so")
 
 OK, ERR_ARG, ERR_NONFINITE, ERR_CUDA, ERR_WORKSPACE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_INTERNAL = (
     0, -1, -2, -3, -4, -5, -6, -7)
@@ -35,6 +37,7 @@ SIGNATURES = {
     "l1line_status": (_I, [_P, _P]),
     "l1line_status_string": (ctypes.c_char_p, [_I]),
     "l1line_last_launch_count": (_I, []),
+    "l1line_check_hits": (_I64, [_I, _P]),
     "l1line_profile_events": (_I, [_P, _P]),
     "l1line_path_max_rows": (_I64, [_I]),
     "l1line_probe": (_I, [_I, _P, _SZ, _I, _P, _P, _P]),
@@ -44,8 +47,10 @@ SIGNATURES = {
     "l1line_fit_batched_f64": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "l1line_fit_subset_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
     "l1line_fit_subset_f64": (_I, [_P, _I64, _I64, _P, _I64, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
-    "l1line_features_f32": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),
-    "l1line_features_f64": (_I, [_P, _I64, _I64, _P, _P, _P, _SZ, _P]),
+    "l1line_proposer_rows": (_I64, [_I64]),
+    "l1line_proposed_workspace_bytes": (_SZ, [_I, _I64, _I64, _I64]),
+    "l1line_features_f32": (_I, [_P, _I64, _I64, ctypes.c_double, _P, _P, _P, _SZ, _P]),
+    "l1line_features_f64": (_I, [_P, _I64, _I64, ctypes.c_double, _P, _P, _P, _SZ, _P]),
     "l1line_mlp_forward": (_I, [_P, _P, _I64, _P, _P, _P]),
     "l1line_mlp_workspace_bytes": (_SZ, [_I64]),
     "l1line_mlp_backward": (_I, [_P, _P, _I64, _P, _P, _P, _P, _SZ, _P]),
@@ -76,8 +81,9 @@ SIGNATURES = {
     "l1line_set_tuning": (_I, [_P]),
     "l1line_plan": (_I, [_I, _I64, _I64, _I64, _P]),
 }
-MLP_PARAMS = 17153   # L1L_MLP_PARAMS
-MLP_BYTES = 34832    # sizeof(l1line_mlp)
+MLP_FEATURES = 4     # L1L_MLP_FEATURES
+MLP_PARAMS = 17281   # L1L_MLP_PARAMS
+MLP_BYTES = 35088    # sizeof(l1line_mlp)
 NOALLOC_SCRATCH_BYTES = 32 << 20  # L1L_NOALLOC_SCRATCH_BYTES in include/l1line.h
 
 _lib = None
@@ -120,6 +126,14 @@ def workspace_bytes(dtype, n: int, m: int, n_lambda: int) -> int:
 
 def last_launch_count() -> int:
     return int(load().l1line_last_launch_count())
+
+
+def check_hits(reset: bool = False):
+    """(hits, source line of the last) of the bounds-checked build; hits is -1
+    in the normal build."""
+    line = ctypes.c_int(0)
+    h = int(load().l1line_check_hits(1 if reset else 0, ctypes.byref(line)))
+    return h, line.value
 
 
 def _dt(dtype) -> int:
@@ -261,17 +275,30 @@ def fit_subset(X, lambdas, jhat, workspace: Optional[Workspace] = None, stream=N
     return v, obj, js, ws
 
 
-def features(X, workspace: Optional[Workspace] = None, stream=None, raw=True):
-    """Column features of X: (raw [m, 3] or None, standardised [m, 3]) float32."""
+def proposer_rows(n: int) -> int:
+    return int(load().l1line_proposer_rows(n))
+
+
+def proposed_workspace(dtype, n: int, m: int, n_lambda: int = 1, device=None) -> "Workspace":
+    """Workspace of the proposer calls (features, fit_proposed)."""
+    nb = int(load().l1line_proposed_workspace_bytes(_dt(dtype), n, m, n_lambda))
+    if nb == 0:
+        raise ValueError("bad shape for the proposer workspace")
+    return Workspace(nb, device)
+
+
+def features(X, lam: float, workspace: Optional[Workspace] = None, stream=None, raw=True):
+    """The proposer's features of every column of X (the restricted objective
+    at penalty lam): (raw [m, 4] or None, standardised [m, 4]) float32."""
     import torch
     _check_x(X)
     n, m = X.shape
-    ws = workspace or Workspace.for_shape(X.dtype, n, m, 1, X.device)
-    r = torch.empty((m, 3), dtype=torch.float32, device=X.device) if raw else None
-    z = torch.empty((m, 3), dtype=torch.float32, device=X.device)
+    ws = workspace or proposed_workspace(X.dtype, n, m, 1, X.device)
+    r = torch.empty((m, MLP_FEATURES), dtype=torch.float32, device=X.device) if raw else None
+    z = torch.empty((m, MLP_FEATURES), dtype=torch.float32, device=X.device)
     f = load().l1line_features_f32 if X.dtype == torch.float32 else load().l1line_features_f64
-    _check(f(X.data_ptr(), n, m, _ptr(r), _ptr(z), ctypes.c_void_p(ws.ptr), ws.nbytes,
-             _stream_ptr(stream)), "l1line_features")
+    _check(f(X.data_ptr(), n, m, float(lam), _ptr(r), _ptr(z), ctypes.c_void_p(ws.ptr),
+             ws.nbytes, _stream_ptr(stream)), "l1line_features")
     return r, z
 
 
@@ -346,7 +373,7 @@ def fit_proposed(X, lambdas, mlp, K, workspace: Optional[Workspace] = None, stre
     _check_x(X)
     lam = _lams(lambdas)
     n, m = X.shape
-    ws = workspace or Workspace.for_shape(X.dtype, n, m, lam.size, X.device)
+    ws = workspace or proposed_workspace(X.dtype, n, m, lam.size, X.device)
     v, obj, js = _fit_outputs(X, lam.size, out)
     if idx is None:
         idx = torch.empty(int(K), dtype=torch.int32, device=X.device)

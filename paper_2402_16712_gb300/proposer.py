@@ -2,10 +2,13 @@
 library's own network kernels, and evaluation against the full scan.
 
 Algorithm 1 scores every candidate jhat exactly (m of them, each scanning all
-k).  The proposer ranks the candidates from three column features with a small
-network and only the K best-ranked ones are scored exactly; the exact
-objective still decides among them, and the full scan is the reference for the
-regret (objective lost by missing the best jhat).
+k).  The proposer ranks the candidates from four features with a small network
+and only the K best-ranked ones are scored exactly; the exact objective still
+decides among them, and the full scan is the reference for the regret
+(objective lost by missing the best jhat).  The features are three column
+statistics (l1 and l2 norms, median |x|) and the objective of Algorithm 1 on
+the instance's heaviest rows (l1line_proposer_rows(n) of them), fitted by the
+library itself: the objective is dominated by the few rows of large norm.
 
     python -m paper_2402_16712_gb300.proposer train --out DIR
     python -m paper_2402_16712_gb300.proposer eval [--theta FILE] [--count 200]
@@ -46,8 +49,8 @@ K_DEFAULT = 32
 def init_theta(seed: int) -> np.ndarray:
     """He-normal weights, zero biases, in the flat order W1, b1, W2, b2, w3, b3."""
     rng = np.random.default_rng(seed)
-    H = 128
-    parts = [rng.normal(0.0, np.sqrt(2.0 / 3.0), H * 3), np.zeros(H),
+    H, F = 128, l1line.MLP_FEATURES
+    parts = [rng.normal(0.0, np.sqrt(2.0 / F), H * F), np.zeros(H),
              rng.normal(0.0, np.sqrt(2.0 / H), H * H), np.zeros(H),
              rng.normal(0.0, np.sqrt(1.0 / H), H), np.zeros(1)]
     th = np.concatenate(parts).astype(np.float32)
@@ -81,7 +84,7 @@ def _targets(z: np.ndarray) -> np.ndarray:
 # data
 # ---------------------------------------------------------------------------
 def build_dataset(seeds, device, log=None):
-    """Standardised features [N, 3] and target logits [N] (device, float32),
+    """Standardised features [N, 4] and target logits [N] (device, float32),
     instance offsets, and per instance the best jhat and m.  The fits queue
     back to back on the device; the objectives come back to the host once per
     block of instances, where the device status is checked too."""
@@ -98,14 +101,15 @@ def build_dataset(seeds, device, log=None):
         for r, seed in enumerate(seeds[q0:q0 + block]):
             spec = datagen.proposer_spec(seed)
             X, _, _ = datagen.planted_torch(spec, device)
-            need = l1line.workspace_bytes("float32", spec.n, spec.m, 1)
+            need = int(l1line.load().l1line_proposed_workspace_bytes(l1line.DTYPE_F32, spec.n,
+                                                                     spec.m, 1))
             if r == len(ring):
                 ring.append(l1line.Workspace(need, device))
             elif ring[r].nbytes < need:
                 ring[r] = l1line.Workspace(need, device)
             ws = ring[r]
             # features first: the scan resets the status word and then keeps its own
-            _, fz = l1line.features(X, workspace=ws, raw=False)
+            _, fz = l1line.features(X, datagen.PROPOSER_LAMBDA, workspace=ws, raw=False)
             _, _, z, _ = l1line.scan(X, [datagen.PROPOSER_LAMBDA], workspace=ws, z_only=True)
             feats.append(fz)
             zs.append(z[0])
@@ -236,19 +240,20 @@ def _ranks_of_best(z, score):
 def rank_study(count, seed0, n=5000, m=1000, theta_path=THETA_PATH, device=None, log=None):
     """Per instance (float32 n x m, proposer_spec seeds seed0 ...): the exact
     objectives of every jhat (one scan) and, for the learned scores, the l1,
-    l2 and median features and a random order, the smallest K that keeps a
-    best jhat.  Zero regret at K <=> that rank <= K."""
+    l2 and median features, the heavy-row objective alone (lowest first) and a
+    random order, the smallest K that keeps a best jhat.  Zero regret at K <=>
+    that rank <= K."""
     import torch
     device = device or "cuda"
     mlp = network(device, theta_path)
-    ws = l1line.Workspace.for_shape("float32", n, m, 1, device)
+    ws = l1line.proposed_workspace("float32", n, m, 1, device)
     rng = np.random.default_rng(seed0)
-    ranks = {"learned": [], "l1": [], "l2": [], "median": [], "random": []}
+    ranks = {"learned": [], "l1": [], "l2": [], "median": [], "heavy_rows": [], "random": []}
     regrets = {k: [] for k in ranks}
     for i in range(count):
         spec = datagen.proposer_spec(seed0 + i, n=n, m=m)
         X, _, _ = datagen.planted_torch(spec, device)
-        raw, fz = l1line.features(X, workspace=ws)
+        raw, fz = l1line.features(X, datagen.PROPOSER_LAMBDA, workspace=ws)
         s = l1line.mlp_forward(fz, mlp)
         _, _, z, _ = l1line.scan(X, [datagen.PROPOSER_LAMBDA], workspace=ws, z_only=True)
         if l1line.status(ws) != l1line.OK:
@@ -256,7 +261,8 @@ def rank_study(count, seed0, n=5000, m=1000, theta_path=THETA_PATH, device=None,
         z = z[0].cpu().numpy()
         raw = raw.cpu().numpy().astype(np.float64)
         for key, sc in (("learned", s.cpu().numpy().astype(np.float64)), ("l1", raw[:, 0]),
-                        ("l2", raw[:, 1]), ("median", raw[:, 2]), ("random", rng.random(m))):
+                        ("l2", raw[:, 1]), ("median", raw[:, 2]), ("heavy_rows", -raw[:, 3]),
+                        ("random", rng.random(m))):
             r, reg = _ranks_of_best(z, sc)
             ranks[key].append(r)
             regrets[key].append(reg)
@@ -294,7 +300,7 @@ def evaluate(theta_path=THETA_PATH, count=200, Ks=(32, 64, 128, 256, 512), n=500
     held = rank_study(count, seed0, n, m, theta_path, device, log)
     mlp = network(device, theta_path)
     lam = [datagen.PROPOSER_LAMBDA]
-    ws = l1line.Workspace.for_shape("float32", n, m, 1, device)
+    ws = l1line.proposed_workspace("float32", n, m, 1, device)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
 

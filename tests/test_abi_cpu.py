@@ -150,7 +150,7 @@ def test_proposer_argument_errors(lib):
     assert lib.l1line_mlp_forward(p, None, 10, P(264), p, None) == l1line.ERR_ARG
     assert lib.l1line_mlp_forward(p, None, 10, None, p, None) == l1line.ERR_ARG
     assert lib.l1line_mlp_workspace_bytes(0) == 0
-    assert lib.l1line_mlp_workspace_bytes(64) == 17153 * 4 + 252  # one CTA row, 256-aligned
+    assert lib.l1line_mlp_workspace_bytes(64) == 17281 * 4 + 252  # one CTA row, 256-aligned
     assert lib.l1line_mlp_backward(p, None, 100, p, p, p, None, 1 << 20, None) == \
         l1line.ERR_WORKSPACE
     assert lib.l1line_mlp_backward(p, None, 100, p, p, p, P(1024), 16, None) == l1line.ERR_WORKSPACE
@@ -169,7 +169,8 @@ def test_proposer_argument_errors(lib):
                                        None) == l1line.ERR_ARG
     assert lib.l1line_fit_proposed_f64(p, 10, 5, L, 1, None, 2, None, p, p, p, P(1024), 1 << 30,
                                        None) == l1line.ERR_ARG
-    assert lib.l1line_features_f32(p, 10, 5, None, None, P(1024), 1 << 30, None) == l1line.ERR_ARG
+    assert lib.l1line_features_f32(p, 10, 5, 0.2, None, None, P(1024), 1 << 30, None) == \
+        l1line.ERR_ARG
 
 
 def test_probe_argument_errors(lib):
@@ -184,6 +185,33 @@ def test_probe_argument_errors(lib):
     assert lib.l1line_probe(l1line.PROBE_SMEM, None, 0, 1, None, None, ref) == l1line.ERR_ARG
     assert lib.l1line_probe(l1line.PROBE_SMEM, None, 0, 1, P(258), None, ref) == l1line.ERR_ARG
     assert lib.l1line_probe(l1line.PROBE_SMEM, None, 0, 1, P(256), None, None) == l1line.ERR_ARG
+
+
+def test_proposer_rows_and_workspace(lib):
+    # the restricted fit takes min(n, max(256, ceil(n / 8))) rows
+    assert [lib.l1line_proposer_rows(n) for n in (0, 1, 200, 256, 2048, 2049, 5000)] == \
+        [0, 1, 200, 256, 256, 257, 625]
+    for dt in (0, 1):
+        for n, m, nl in ((300, 20, 1), (5000, 1000, 1), (2000, 50, 3)):
+            fit = lib.l1line_workspace_bytes(dt, n, m, nl)
+            prop = lib.l1line_proposed_workspace_bytes(dt, n, m, nl)
+            R = lib.l1line_proposer_rows(n)
+            # the fit's workspace, the row norms, row list, row copy and the
+            # restricted fit's own workspace
+            assert prop >= fit + n * 4 + R * 4 + R * m * (4 if dt == 0 else 8) + \
+                lib.l1line_workspace_bytes(dt, R, m, 1)
+    assert lib.l1line_proposed_workspace_bytes(2, 10, 10, 1) == 0
+    assert lib.l1line_proposed_workspace_bytes(0, 0, 10, 1) == 0
+    P = ctypes.c_void_p
+    lam = np.array([0.2])
+    small = lib.l1line_proposed_workspace_bytes(0, 10, 5, 1) - 256
+    assert lib.l1line_features_f32(P(256), 10, 5, 0.2, None, P(512), P(1024), small, None) == \
+        l1line.ERR_WORKSPACE
+    assert lib.l1line_features_f32(P(256), 10, 5, 0.2, None, None, P(1024), 1 << 30, None) == \
+        l1line.ERR_ARG
+    assert lib.l1line_fit_proposed_f32(P(256), 10, 5, lam.ctypes.data_as(P), 1, P(256), 2, None,
+                                       P(512), P(512), P(512), P(1024), small, None) == \
+        l1line.ERR_WORKSPACE
 
 
 def test_committed_network_parameters():

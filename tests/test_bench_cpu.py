@@ -251,3 +251,22 @@ def test_sharded_summary_arithmetic():
     assert r["ms_per_step"] == 6.0 and r["fits_per_s"] == pytest.approx(2 / 12e-3)
     assert r["value"] == pytest.approx(2 * 3_998_000 / 12e-3)
     assert r["identical_to_one_gpu"] is True and r["scaling"] == "strong"
+
+
+def test_path_roofline_arithmetic():
+    """Algorithm 2's ceilings on hand-worked numbers: 2000 x 2000 float32,
+    2.6e8 breakpoints in 60 ms."""
+    import bench
+    r = bench.path_roofline(2000, 2000, 260_000_000, 60.0, 4)
+    wbytes = 260_000_000 * 12 + 2000 * 2000 * 12
+    instr = 2 * 6 * 2000 * (2000 * 1999)
+    c = r["ceilings"]
+    assert c["hbm"]["traffic_bytes"] == wbytes and c["alu"]["instructions"] == instr
+    assert c["hbm"]["achieved"] == pytest.approx(wbytes / 0.060 / 1e9)
+    assert c["alu"]["achieved"] == pytest.approx(instr / 0.060 / 1e12)
+    assert c["alu"]["peak"] == pytest.approx(152 * 128 * 2070e6 / 1e12)
+    # the binding ceiling is the one with the longer minimum time
+    t_hbm = wbytes / (c["hbm"]["peak"] * 1e9)
+    t_alu = instr / (c["alu"]["peak"] * 1e12)
+    assert r["bound"] == ("hbm" if t_hbm > t_alu else "alu")
+    assert r["frac"] == c[r["bound"]]["frac"]

@@ -4,9 +4,11 @@ the oracle restricted to the same candidate list.
 
 Bars:
   * features: l1 and l2 within 1e-6 relative of the float64 values (they are
-    float64 sums rounded once to float); the median exactly float(median);
-    the standardised features within 1e-5 of the reference standardisation of
-    the GPU's raw features.
+    float64 sums rounded once to float); the median exactly float(median); the
+    heavy-row objective within the fit's bar (1e-5 relative for float input,
+    float rounding for float64 input) of the oracle's objective on the same
+    rows; the standardised features within 1e-5 of the reference
+    standardisation of the GPU's raw features.
   * network forward, backward, loss and Adam: float arithmetic against float64
     with the same binary16 weights; bounds are stated per test.
   * top-K: exact indices.
@@ -42,8 +44,9 @@ def _dev(a, dtype=None):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-@pytest.mark.parametrize("shape", [(1, 5), (2, 3), (7, 40), (300, 33), (1001, 70)])
-def test_features_match_reference(dtype, shape):
+@pytest.mark.parametrize("shape,lam", [((1, 5), 0.2), ((2, 3), 0.0), ((7, 40), 0.2),
+                                       ((300, 33), 0.2), ((1001, 70), 0.2), ((2500, 48), 1.5)])
+def test_features_match_reference(dtype, shape, lam):
     n, m = shape
     rng = np.random.default_rng(n * 131 + m)
     X = rng.laplace(0.0, 1.0, size=(n, m)).astype(dtype)
@@ -51,11 +54,17 @@ def test_features_match_reference(dtype, shape):
     if m > 2:
         X[rng.random(n) < 0.3, 1] = 0.0  # many zeros
         X[:, 2] = np.where(rng.random(n) < 0.5, -2.5, 2.5).astype(dtype)  # constant |x|
-    raw, z = l1line.features(_dev(X))
+    X[rng.choice(n, max(1, n // 20), replace=False)] *= 40.0  # a few heavy rows
+    raw, z = l1line.features(_dev(X), lam)
     raw, z = raw.cpu().numpy(), z.cpu().numpy()
-    ref = P.raw_features(X)
+    ref = P.raw_features(X, lam)
+    assert l1line.proposer_rows(n) == P.proxy_rows(n)
     assert np.allclose(raw[:, :2], ref[:, :2], rtol=1e-6, atol=0)
     assert np.array_equal(raw[:, 2], ref[:, 2].astype(np.float32))
+    # the restricted objective: the same rows, then the fit's bar
+    rtol = 1e-5 if dtype == np.float32 else 1e-7
+    assert np.allclose(raw[:, 3], ref[:, 3], rtol=rtol, atol=0), \
+        np.abs(raw[:, 3] - ref[:, 3]).max()
     zr = P.standardise(raw.astype(np.float64))
     assert np.allclose(z, zr, rtol=0, atol=1e-5)
 
@@ -65,7 +74,7 @@ def test_network_forward_matches_reference():
     thd = _dev(th)
     mlp = l1line.mlp_pack(thd)
     rng = np.random.default_rng(2)
-    F = rng.normal(size=(200, 3)).astype(np.float32)
+    F = rng.normal(size=(200, 4)).astype(np.float32)
     rows = rng.integers(0, 200, size=131).astype(np.int32)  # ragged tile, gathered
     s = l1line.mlp_forward(_dev(F), mlp, rows=_dev(rows)).cpu().numpy()
     thh = P.half_weights(th.astype(np.float64))
@@ -75,8 +84,8 @@ def test_network_forward_matches_reference():
     assert np.abs(s - ref).max() <= 1e-5 * scale
     # the packed image holds the binary16 weights
     img = mlp.cpu().numpy()
-    w1 = img[:768].view(np.float16).astype(np.float64)
-    assert np.array_equal(w1, thh[:384])
+    w1 = img[:1024].view(np.float16).astype(np.float64)
+    assert np.array_equal(w1, thh[:512])
 
 
 def test_network_backward_matches_reference():
@@ -84,7 +93,7 @@ def test_network_backward_matches_reference():
     thd = _dev(th)
     mlp = l1line.mlp_pack(thd)
     rng = np.random.default_rng(4)
-    F = rng.normal(size=(300, 3)).astype(np.float32)
+    F = rng.normal(size=(300, 4)).astype(np.float32)
     rows = rng.permutation(300)[:197].astype(np.int32)
     ds = rng.normal(size=197).astype(np.float32)
     g = l1line.mlp_backward(_dev(F), mlp, _dev(ds), rows=_dev(rows)).cpu().numpy()
@@ -200,13 +209,13 @@ def test_proposed_fit_is_the_subset_fit_of_the_network_top_k(dtype):
     assert l1line.status(ws) == l1line.OK
     idx = idx.cpu().numpy()
     # stepwise: features -> network -> top-K through the separate entry points
-    _, z = l1line.features(_dev(X))
+    _, z = l1line.features(_dev(X), lams[0])
     s = l1line.mlp_forward(z, mlp)
     assert np.array_equal(idx, l1line.topk(s, K).cpu().numpy())
     # and the reference chain picks the same candidates (scores well separated
     # compared with the float error of the network)
     sr = P.forward(P.half_weights(_theta(12).astype(np.float64)),
-                   P.standardise(P.raw_features(X)))
+                   P.standardise(P.raw_features(X, lams[0])))
     gap = np.sort(sr)[::-1]
     if gap[K - 1] - gap[K] > 1e-3:
         assert np.array_equal(idx, P.topk(sr, K))
@@ -218,7 +227,7 @@ def test_training_steps_reduce_the_loss():
     # learn to prefer a large first feature
     rng = np.random.default_rng(13)
     nb, per = 32, 50
-    F = rng.normal(size=(nb * per, 3)).astype(np.float32)
+    F = rng.normal(size=(nb * per, 4)).astype(np.float32)
     u = (3.0 * F[:, 0] - F[:, 2]).astype(np.float32)
     offs = (np.arange(nb + 1) * per).astype(np.int64)
     th = (np.random.default_rng(14).normal(size=P.N_PARAMS) * 0.1).astype(np.float32)
@@ -243,20 +252,22 @@ def test_training_steps_reduce_the_loss():
 def test_trained_network_gain_over_the_method_without_it():
     """The committed network on held-out instances of the evaluation shape
     (float32 5000 x 1000, seeds never used in training): its top-32 holds the
-    exact best jhat far more often than a random top-32 and at least as often
-    as the column-l1 heuristic (one instance of slack), and the learned path
-    is much faster than the full scan, which it replaces."""
+    exact best jhat on strictly more instances than the column-l1 heuristic's
+    top-32, on at least 95% of them, far more often than a random top-32, and
+    the learned path is several times faster than the full scan, which it
+    replaces."""
     from paper_2402_16712_gb300 import proposer
-    count = 24
+    count = 40
     r = proposer.rank_study(count, datagen.PROPOSER_HELDOUT_SEED0)
     assert (r["regret"]["learned"][np.arange(count), r["learned"] - 1] == 0).all()
     learned = np.mean(r["learned"] <= 32)
+    assert learned > np.mean(r["l1"] <= 32), (learned, np.mean(r["l1"] <= 32))
+    assert learned >= 0.95, learned
     assert learned >= np.mean(r["random"] <= 32) + 0.3
-    assert learned >= np.mean(r["l1"] <= 32) - 1.0 / count
     X, _, _ = datagen.planted_torch(datagen.proposer_spec(datagen.PROPOSER_HELDOUT_SEED0, n=5000,
                                                           m=1000), "cuda")
     mlp = proposer.network()
-    ws = l1line.Workspace.for_shape("float32", 5000, 1000, 1)
+    ws = l1line.proposed_workspace("float32", 5000, 1000, 1)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     for _ in range(2):
         ev[0].record()
@@ -267,4 +278,4 @@ def test_trained_network_gain_over_the_method_without_it():
     torch.cuda.synchronize()
     assert l1line.status(ws) == l1line.OK
     t_full, t_prop = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
-    assert t_prop * 5 < t_full, (t_full, t_prop)
+    assert t_prop * 3 < t_full, (t_full, t_prop)

@@ -1,10 +1,16 @@
 """Pins of the CPU reference of the learned proposer (oracle/proposer_ref.py)
 against facts that do not come from that file: finite differences, hand
-computed values, invariances and known binary16 roundings."""
+computed values, invariances, known binary16 roundings, and the paper's toy
+example (Figure 1's lines) for the restricted-objective feature."""
+import json
+import os
+
 import numpy as np
 import pytest
 
 from oracle import proposer_ref as P
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "toy_example.json")
 
 
 def _theta(seed, scale=0.3):
@@ -13,7 +19,7 @@ def _theta(seed, scale=0.3):
 
 
 def test_parameter_count_and_pack_roundtrip():
-    assert P.N_PARAMS == 128 * 3 + 128 + 128 * 128 + 128 + 128 + 1 == 17153
+    assert P.N_PARAMS == 128 * 4 + 128 + 128 * 128 + 128 + 128 + 1 == 17281
     th = _theta(0)
     assert np.array_equal(P.pack(*P.unpack(th)), th)
 
@@ -21,13 +27,13 @@ def test_parameter_count_and_pack_roundtrip():
 def test_forward_hand_built_network():
     # unit 0 = relu(f0), unit 1 = relu(-f0), unit 2 = relu(f1 - 1): layer 2 passes
     # them through and the output is |f0| + 2 relu(f1 - 1) - 0.5
-    W1 = np.zeros((128, 3)); b1 = np.zeros(128)
+    W1 = np.zeros((128, 4)); b1 = np.zeros(128)
     W1[0, 0], W1[1, 0], W1[2, 1], b1[2] = 1.0, -1.0, 1.0, -1.0
     W2 = np.zeros((128, 128)); W2[0, 0] = W2[1, 1] = W2[2, 2] = 1.0
     b2 = np.zeros(128)
     w3 = np.zeros(128); w3[0] = w3[1] = 1.0; w3[2] = 2.0
     th = P.pack(W1, b1, W2, b2, w3, -0.5)
-    F = np.array([[0.7, 3.0, 9.0], [-2.5, 0.2, -1.0], [0.0, 1.0, 0.0]])
+    F = np.array([[0.7, 3.0, 9.0, -4.0], [-2.5, 0.2, -1.0, 8.0], [0.0, 1.0, 0.0, 1.0]])
     want = np.abs(F[:, 0]) + 2 * np.maximum(F[:, 1] - 1.0, 0.0) - 0.5
     assert np.allclose(P.forward(th, F), want, rtol=0, atol=1e-15)
 
@@ -35,13 +41,14 @@ def test_forward_hand_built_network():
 def test_backward_matches_central_differences():
     rng = np.random.default_rng(1)
     th = _theta(2)
-    F = rng.normal(size=(9, 3))
+    F = rng.normal(size=(9, 4))
     ds = rng.normal(size=9)
     g = P.backward(th, F, ds)
     f = lambda t: float(ds @ P.forward(t, F))
-    # every bias, w3 and b3 entry plus samples of both matrices
-    idx = list(range(384, 512)) + list(range(16896, 17153))
-    idx += list(rng.choice(384, 40, replace=False)) + list(384 + 128 + rng.choice(16384, 200, replace=False))
+    # every bias, w3 and b3 entry plus samples of both matrices (W1: 0..511,
+    # b1: 512..639, W2: 640..17023, b2, w3, b3: 17024..17280)
+    idx = list(range(512, 640)) + list(range(17024, 17281))
+    idx += list(rng.choice(512, 40, replace=False)) + list(640 + rng.choice(16384, 200, replace=False))
     h = 1e-6
     for i in idx:
         e = np.zeros_like(th); e[i] = h
@@ -111,7 +118,7 @@ def test_relu_derivative_at_zero_is_zero():
     b2[u] = 0.0
     w3[u] = 1.5
     th = P.pack(W1, b1, W2, b2, w3, b3)
-    F = rng.normal(size=(6, 3))
+    F = rng.normal(size=(6, 4))
     ds = rng.normal(size=6)
     _, (a1, h1, a2, h2) = P.forward(th, F, keep=True)
     assert (a2[:, u] == 0.0).all()
@@ -128,13 +135,49 @@ def test_raw_features_hand_values():
                   [-4.0, 0.0, 2.0],
                   [0.0, 0.0, -5.0],
                   [1.0, 0.0, 2.0]])
-    F = P.raw_features(X)
+    F = P.column_features(X)
     assert np.allclose(F[:, 0], [8.0, 0.0, 10.0])
     assert np.allclose(F[:, 1], [np.sqrt(26.0), 0.0, np.sqrt(34.0)])
     # lower median of 4 values: rank 1 of the sorted |x|
     assert np.array_equal(F[:, 2], [1.0, 0.0, 2.0])
-    F5 = P.raw_features(np.array([[5.0], [-1.0], [3.0], [-2.0], [4.0]]))
+    F5 = P.column_features(np.array([[5.0], [-1.0], [3.0], [-2.0], [4.0]]))
     assert F5[0, 2] == 3.0
+
+
+def test_proxy_rows_rule():
+    assert [P.proxy_rows(n) for n in (1, 200, 256, 257, 2048, 2049, 5000)] == \
+        [1, 200, 256, 256, 256, 257, 625]
+
+
+def test_heavy_rows_hand_values():
+    # row l1 norms: 4, 6, 6, 1, 9, 6; the three heaviest are rows 4 and the
+    # first two of the rows tied at 6 (rows 1 and 2, ties to the smaller index)
+    X = np.array([[1.0, -3.0], [2.0, 4.0], [-6.0, 0.0], [0.5, 0.5], [9.0, 0.0], [3.0, -3.0]])
+    assert list(P.heavy_rows(X, 3)) == [1, 2, 4]
+    assert list(P.heavy_rows(X, 1)) == [4]
+    assert list(P.heavy_rows(X, 6)) == [0, 1, 2, 3, 4, 5]
+
+
+def test_proxy_objective_on_the_toy_example():
+    """The restricted objective is Algorithm 1 on the heavy rows: the paper's
+    five toy points, hidden among light rows that the restriction must drop,
+    give Figure 1's objective lines z_jhat(lambda) (intercept + slope lambda,
+    to one unit of the last printed digit: the figure truncates 113/3)."""
+    g = json.load(open(GOLD))
+    toy = np.array(g["points"], dtype=np.float64)
+    rng = np.random.default_rng(11)
+    light = rng.uniform(-0.01, 0.01, size=(40, 4))
+    X = np.concatenate([light[:17], toy, light[17:]])
+    rows = P.heavy_rows(X, 5)
+    assert list(rows) == list(range(17, 22))
+
+    def tol(s):
+        return 10.0 ** -(len(s.split(".")[1]) if "." in s else 0)  # one unit: the figure truncates
+    for ln in g["figure1_lines"]:
+        lam = (ln["from"] + ln["to"]) / 2
+        z = P.proxy_objective(X, lam, R=5)[ln["jhat"] - 1]
+        pred = float(ln["intercept"]) + float(ln["slope"]) * lam
+        assert abs(z - pred) <= tol(ln["intercept"]) + tol(ln["slope"]) * lam + 1e-9, (ln, z)
 
 
 def test_standardise():
@@ -153,10 +196,10 @@ def test_half_rounding_known_values():
     th[1] = 1.0 + 2.0 ** -11     # exactly halfway: ties to even -> 1.0
     th[2] = 1.0 + 3 * 2.0 ** -11  # halfway, ties to even -> 1 + 2^-9
     th[3] = 65504.0              # largest finite binary16
-    th[384] = 1.0 / 3.0          # a bias: not rounded
+    th[512] = 1.0 / 3.0          # a bias: not rounded
     r = P.half_weights(th)
     assert r[0] == 0.333251953125 and r[1] == 1.0 and r[2] == 1.0 + 2.0 ** -9
-    assert r[3] == 65504.0 and r[384] == 1.0 / 3.0
+    assert r[3] == 65504.0 and r[512] == 1.0 / 3.0
 
 
 def test_topk_ties_and_nan():
