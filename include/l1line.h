@@ -69,10 +69,17 @@ enum {
     L1L_FLAG_FORCE_EXACT = 1u << 0
 };
 
-/* Largest n (rows) the shared-memory pair kernels accept, per dtype.  Larger
- * n, m > 2^31 - 1, n_lambda > 65535, or m * m * min(n_lambda, 256) > 2^31
- * (the exact path's pair list of one launch; m <= 46,340 for one lambda)
- * return L1L_ERR_UNSUPPORTED. */
+/* Largest n (rows) the shared-memory pair kernel takes, per dtype (column
+ * jhat is staged in one CTA's shared memory).  Scans and fits with larger n
+ * run the global-memory path instead: per (lambda, jhat, k) a cluster of up
+ * to 8 CTAs streams both columns from the staged copy, with a radix descent
+ * over the ratio keys and the same exact decisions (Lemma 1 puts no limit on
+ * n); the results obey the same bar.  n > 2^31 - 256, m > 2^31 - 1,
+ * n_lambda > 65535, or m * m * min(n_lambda, 256) > 2^31 (the exact path's
+ * pair list of one launch; m <= 46,340 for one lambda) return
+ * L1L_ERR_UNSUPPORTED, as do the batched call, the proposer calls (features,
+ * proposed fit) and the lambda-path calls for n beyond their own limits
+ * (l1line_path_max_rows; the others: l1line_max_rows). */
 int64_t l1line_max_rows(int dtype);
 
 /* Bytes of device workspace needed by l1line_scan_* and l1line_fit_* for the
@@ -154,8 +161,8 @@ int l1line_fit_batched_f64(int64_t batch, const double *const *Xs, const int64_t
 
 /*
  * Subset fit: Algorithm 1 restricted to the candidate jhat listed in
- * jhat_list (DEVICE int32[K], entries in [0, m); duplicates are allowed and
- * scored once each).  Every k is still scanned for each listed jhat, so the
+ * jhat_list (DEVICE int32[K], 1 <= K <= m, entries in [0, m); duplicates are
+ * allowed and scored once each; K > m returns L1L_ERR_ARG).  Every k is still scanned for each listed jhat, so the
  * scores z_jhat of the listed jhat are exactly those of l1line_fit_*, and the
  * result is the listed jhat of smallest z (smallest index on ties).  Outputs
  * as for l1line_fit_*.  Workspace: l1line_workspace_bytes(dtype, n, m,

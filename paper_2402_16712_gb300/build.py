@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libl1line.so")
 # checked; l1line.py loads it when L1LINE_LIB names it
 LIB_CHECKS = os.path.join(HERE, "libl1line_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["k_prep.cu", "k_pairs.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "k_propose.cu",
+SOURCES = ["k_prep.cu", "k_pairs.cu", "k_large.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "k_propose.cu",
            "k_path.cu", "k_solpath.cu", "k_probe.cu", "abi.cu"]
 
 

@@ -105,6 +105,9 @@ struct ProposedLayout {
     size_t rho, rows, xr, pws, pws_bytes, total;
 };
 bool make_proposed_layout(int dtype, int64_t n, int64_t m, int64_t nl, ProposedLayout &P) {
+    // the column-feature kernel holds a column's n keys in shared memory
+    if (n > (dtype == L1L_DTYPE_F32 ? max_rows_pairs<float>() : max_rows_pairs<double>()))
+        return false;
     if (!make_layout(dtype, n, m, nl, P.L)) return false;
     P.R = proposer_rows(n);
     Layout LR;
@@ -157,7 +160,7 @@ int scan_setup(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t 
     for (int64_t t = 0; t < nl; ++t)
         if (!(lambdas[t] >= 0.0) || std::isinf(lambdas[t])) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(X) % sizeof(T)) != 0) return L1L_ERR_ARG;
-    if (n > max_rows_pairs<T>()) return L1L_ERR_UNSUPPORTED;
+    if (n > large_max_rows()) return L1L_ERR_UNSUPPORTED;
     Layout &L = c.L;
     if (!make_layout(dtype_of<T>(), n, m, nl, L)) return L1L_ERR_UNSUPPORTED;
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255) != 0 || ws_bytes < L.total)
@@ -198,12 +201,38 @@ template <typename T> int scan_prep(const T *X, Scan<T> &c) {
     return L1L_OK;
 }
 
+// Steps A2-A5 for n beyond the pair kernel's shared memory: the cluster
+// kernel streaming both columns from the staged copy, then the exact path.
+template <typename T>
+int scan_pairs_large(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jlist,
+                     int64_t nj) {
+    ScanArgs<T> &a = c.a;
+    const bool prof = g_ev_start && g_ev_stop;
+    for (int64_t t0 = 0; t0 < nl; t0 += MAX_LAMBDA_PER_LAUNCH) {
+        const int nlc = (int)((nl - t0) < MAX_LAMBDA_PER_LAUNCH ? (nl - t0) : MAX_LAMBDA_PER_LAUNCH);
+        const bool last = t0 + MAX_LAMBDA_PER_LAUNCH >= nl;
+        if (cudaMemsetAsync(a.slow_count, 0, sizeof(uint32_t), c.st) != cudaSuccess)
+            return L1L_ERR_CUDA;
+        if (prof && t0 == 0 && cudaEventRecord(g_ev_start, c.st) != cudaSuccess)
+            return L1L_ERR_CUDA;
+        if (launch_large<T>(a, lambdas, (int)t0, nlc, c.st, c.launches) != cudaSuccess)
+            return L1L_ERR_CUDA;
+        if (prof && last && cudaEventRecord(g_ev_stop, c.st) != cudaSuccess) return L1L_ERR_CUDA;
+        if (launch_exact<T>(a, lambdas, (int)t0, nlc, c.sms, c.st, c.launches) != cudaSuccess)
+            return L1L_ERR_CUDA;
+    }
+    if (launch_zreduce(a.s_all, c.z, a.m, nl, jlist, nj, c.st, c.launches) != cudaSuccess)
+        return L1L_ERR_CUDA;
+    return L1L_OK;
+}
+
 // Steps A2-A5 for the jhat in jlist[0..nj) (jlist == nullptr: all m).
 template <typename T>
 int scan_pairs(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jlist, int64_t nj) {
     ScanArgs<T> &a = c.a;
     a.jlist = jlist;
     a.nj = nj;
+    if (a.n > max_rows_pairs<T>()) return scan_pairs_large<T>(c, lambdas, nl, jlist, nj);
     const PairPlan plan = plan_pairs<T>(a.n, a.m, c.sms, nj, g_tune);
     if (plan.warps == 0) return L1L_ERR_UNSUPPORTED;
     a.d0 = plan.d0;
@@ -259,7 +288,9 @@ int fit_impl(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t nl
              const int32_t *jlist, int64_t nj, T *out_v, double *out_obj, int32_t *out_jstar,
              void *ws, size_t ws_bytes, void *stream) {
     if (!out_v || !out_obj || !out_jstar) return L1L_ERR_ARG;
-    if (jlist && (nj < 1 || nj > 0x7FFFFFFF)) return L1L_ERR_ARG;
+    // at most m entries: the exact path's pair list of a launch holds m * m
+    // pairs per lambda, one per listed (jhat, k) at most
+    if (jlist && (nj < 1 || nj > m)) return L1L_ERR_ARG;
     Scan<T> c;
     L1L_TRY(scan_setup<T>(X, n, m, lambdas, nl, nullptr, nullptr, nullptr, ws, ws_bytes, stream,
                           0u, c));
@@ -831,6 +862,7 @@ extern "C" long long l1l_checks_exact(int, int *);
 extern "C" long long l1l_checks_path(int, int *);
 extern "C" long long l1l_checks_solpath(int, int *);
 extern "C" long long l1l_checks_propose(int, int *);
+extern "C" long long l1l_checks_large(int, int *);
 #endif
 
 int64_t l1line_check_hits(int reset, int *line) {
@@ -838,7 +870,7 @@ int64_t l1line_check_hits(int reset, int *line) {
     if (cudaDeviceSynchronize() != cudaSuccess) return -2;
     long long (*readers[])(int, int *) = {l1l_checks_pairs, l1l_checks_batch, l1l_checks_exact,
                                           l1l_checks_path, l1l_checks_solpath,
-                                          l1l_checks_propose};
+                                          l1l_checks_propose, l1l_checks_large};
     long long total = 0;
     for (auto r : readers) {
         const long long h = r(reset, line);

@@ -48,6 +48,17 @@ template <typename T>
 cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
                          const PairPlan &plan, cudaStream_t st, int &launches);
 
+// Largest n of any scan or fit: the global-memory path's limit (row counts
+// and the exact path's row loop are 32-bit).
+constexpr int64_t large_max_rows() { return (int64_t)0x7FFFFF00; }
+// CTAs per cluster of the global-memory path for a staged column of ldn rows.
+int large_cluster_size(int64_t ldn);
+// Steps A2-A4 for n beyond max_rows_pairs (k_large.cu): one launch for
+// lambdas[t0 .. t0+nlc), every (lambda, listed jhat, k).
+template <typename T>
+cudaError_t launch_large(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
+                         cudaStream_t st, int &launches);
+
 // Exact path for the pairs listed by the preceding pair launch (same chunk).
 template <typename T>
 cudaError_t launch_exact(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,

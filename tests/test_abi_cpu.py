@@ -80,7 +80,7 @@ def test_argument_errors_return_before_launch(lib):
     assert _scan(lib, lam=(float("nan"),)) == l1line.ERR_ARG
     assert _scan(lib, lam=(float("inf"),)) == l1line.ERR_ARG
     assert _scan(lib, X=258) == l1line.ERR_ARG  # misaligned float pointer
-    assert _scan(lib, n=10 ** 7) == l1line.ERR_UNSUPPORTED
+    assert _scan(lib, n=2 ** 31) == l1line.ERR_UNSUPPORTED  # beyond the global-memory path
     assert _scan(lib, ws=None) == l1line.ERR_WORKSPACE
     assert _scan(lib, ws=1024 + 16) == l1line.ERR_WORKSPACE  # not 256-aligned
     assert _scan(lib, wsb=16) == l1line.ERR_WORKSPACE
@@ -165,6 +165,9 @@ def test_proposer_argument_errors(lib):
                                      None) == l1line.ERR_ARG
     assert lib.l1line_fit_subset_f32(p, 10, 5, L, 1, p, 0, p, p, p, P(1024), 1 << 30,
                                      None) == l1line.ERR_ARG
+    # more entries than columns (the exact path's pair list holds m per jhat row)
+    assert lib.l1line_fit_subset_f32(p, 10, 5, L, 1, p, 6, p, p, p, P(1024), 1 << 30,
+                                     None) == l1line.ERR_ARG
     assert lib.l1line_fit_proposed_f32(p, 10, 5, L, 1, p, 6, None, p, p, p, P(1024), 1 << 30,
                                        None) == l1line.ERR_ARG
     assert lib.l1line_fit_proposed_f64(p, 10, 5, L, 1, None, 2, None, p, p, p, P(1024), 1 << 30,
@@ -201,6 +204,12 @@ def test_proposer_rows_and_workspace(lib):
             assert prop >= fit + n * 4 + R * 4 + R * m * (4 if dt == 0 else 8) + \
                 lib.l1line_workspace_bytes(dt, R, m, 1)
     assert lib.l1line_proposed_workspace_bytes(2, 10, 10, 1) == 0
+    # the proposer keeps the shared-memory row limit; plain fits go past it
+    for dt in (0, 1):
+        mr = lib.l1line_max_rows(dt)
+        assert lib.l1line_proposed_workspace_bytes(dt, mr, 10, 1) > 0
+        assert lib.l1line_proposed_workspace_bytes(dt, mr + 1, 10, 1) == 0
+        assert lib.l1line_workspace_bytes(dt, mr + 1, 10, 1) > 0
     assert lib.l1line_proposed_workspace_bytes(0, 0, 10, 1) == 0
     P = ctypes.c_void_p
     lam = np.array([0.2])

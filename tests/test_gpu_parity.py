@@ -179,13 +179,9 @@ def test_row_padding_boundaries(dtype, n):
 @pytest.mark.parametrize("dtype", DT)
 def test_largest_supported_row_count(dtype):
     # n at the pair kernel's limit (shared memory), a few columns: every pair
-    # against the oracle, and one row more is refused before any launch
+    # against the oracle (one row more takes the global-memory path,
+    # tests/test_gpu_large.py)
     n = l1line.max_rows(dtype)
     X, _, _ = datagen.planted(datagen.Planted(n, 5, 2, 0.1, 0.1, 5.0, 77, np.dtype(dtype).name))
     _, _, ref = check_scan(X, [0.0, 0.25], where=f"n=max={n}")
     check_fit(X, [0.0, 0.25], ref, where=f"n=max={n}")
-    Xd = torch.zeros((n + 1, 3), dtype=torch.float32 if dtype == np.float32 else torch.float64,
-                     device="cuda")
-    with pytest.raises(l1line.L1LineError) as e:
-        l1line.fit(Xd, [0.1], workspace=l1line.Workspace(1 << 20))
-    assert e.value.code in (l1line.ERR_UNSUPPORTED, l1line.ERR_WORKSPACE)
