@@ -17,10 +17,11 @@
 //            totals, and the first bin at which "weight at or below t exceeds
 //            W/2" (penalty point (0, lambda) included) becomes true is kept.
 //            After the last digit the surviving key is the median itself.
-//   residual sum_i |x_ik - v x_ijhat| over the rows (double sums per thread,
-//            a fixed reduction order per CTA, then rank order over the
-//            cluster; C depends on n only, so results do not depend on m or
-//            on the number of lambdas).
+//   residual sum_i |x_ik - v x_ijhat| over the rows (float input: runs of 32
+//            terms in float, the runs in double; double input: double), a
+//            fixed reduction order per CTA, then rank order over the cluster;
+//            C depends on n only, so results do not depend on m or on the
+//            number of lambdas.
 //
 // Ratios are recomputed by division in every pass rather than stored.  A
 // decision the truncated weights cannot settle lists the pair for the exact
@@ -178,10 +179,20 @@ __global__ void __launch_bounds__(LG_NT, 2)
             unsigned long long *cp = sm.copies[warp % LG_COPIES];
             int cur = -1;
             unsigned long long csum = 0;
+            // the next vectors are loaded while the current ones are processed
+            V nj{}, nk{};
+            if (v0 + tid < v1) {
+                nj = xjv[v0 + tid];
+                nk = xkv[v0 + tid];
+            }
             for (int64_t v = v0 + tid; v < v1; v += LG_NT) {
                 T xb[VW], xa[VW];
-                VT::get(xjv[v], xb);
-                VT::get(xkv[v], xa);
+                VT::get(nj, xb);
+                VT::get(nk, xa);
+                if (v + LG_NT < v1) {
+                    nj = xjv[v + LG_NT];
+                    nk = xkv[v + LG_NT];
+                }
 #pragma unroll
                 for (int u = 0; u < VW; ++u) {
                     if (xb[u] == T(0)) continue;
@@ -292,14 +303,27 @@ __global__ void __launch_bounds__(LG_NT, 2)
         }
         const T vv = state == LG_FOUND ? Tr::value(prefix) : T(0);
         // ---- residual: sum_i |x_ik - v x_ijhat| ----
+        // float input: terms summed in float over runs of 32 rows (a relative
+        // error below 2^-19 of the run's sum), runs in double; double input:
+        // every term in double
         double racc = 0.0;
+        T run = T(0);
+        int nrun = 0;
         for (int64_t v = v0 + tid; v < v1; v += LG_NT) {
             T xb[VW], xa[VW];
             VT::get(xjv[v], xb);
             VT::get(xkv[v], xa);
+            T t4 = T(0);
 #pragma unroll
-            for (int u = 0; u < VW; ++u) racc += (double)fabs(fma(-vv, xb[u], xa[u]));
+            for (int u = 0; u < VW; ++u) t4 += fabs(fma(-vv, xb[u], xa[u]));
+            run += t4;
+            if (++nrun == 32 / VW || sizeof(T) == 8) {
+                racc += (double)run;
+                run = T(0);
+                nrun = 0;
+            }
         }
+        racc += (double)run;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) racc += __shfl_xor_sync(0xFFFFFFFFu, racc, off);
         if (lane == 0) sm.wres[warp] = racc;

@@ -46,6 +46,36 @@ __device__ __forceinline__ void transpose_tile(const T *__restrict__ X, T *__res
 
 template <typename T> __device__ __forceinline__ T absval(T x) { return x < T(0) ? -x : x; }
 
+// The column statistics from its reductions (shared by the one-CTA and the
+// cluster versions below).  sigma: the scale that keeps every q_i below
+// 2^(60 - L) with L the bit length of n_valid (E = floor(log2 max |x|)).
+__device__ __forceinline__ int colprep_sigma(int nv, int E) {
+    const int Lbits = nv > 0 ? 32 - __clz(nv) : 0;
+    return nv > 0 ? 60 - E - Lbits : 0;
+}
+// 32-bit weights: drop the fewest low bits that bring the total below 2^32
+// (floor(floor(x) / 2^s) = floor(x / 2^s), so q32 = q >> s is the weight
+// rounded down at scale sigma - s, and sum q32 <= Q / 2^s < 2^32).
+__device__ __forceinline__ int colprep_shift32(long long Q) {
+    const int qbits = Q > 0 ? 64 - __clzll(Q) : 0;
+    return qbits > 32 ? qbits - 32 : 0;
+}
+template <typename T>
+__device__ __forceinline__ ColInfo colprep_make(long long Q, int sigma, int nv, int I, int Emin,
+                                                int E, long long Q32, int shift, int I32) {
+    ColInfo c;
+    c.Q = Q;
+    c.sigma = sigma;
+    c.n_valid = nv;
+    c.n_inexact = I;
+    c.flags = (nv > 0 && (Emin < WideRange<T>::lo || E > WideRange<T>::hi)) ? COL_WIDE : 0;
+    c.Q32 = (uint32_t)Q32;
+    c.shift32 = shift;
+    c.n_inexact32 = I32;
+    c.pad_ = 0;
+    return c;
+}
+
 // One block per column jhat: n_valid, sigma (from the largest |x_ijhat|), the
 // fixed-point total Q and the number of truncated weights.
 template <typename T>
@@ -82,8 +112,7 @@ __device__ __forceinline__ void colprep_column(const T *__restrict__ col, ColInf
         E = max(E, s_max[w]);
         Emin = min(Emin, s_min[w]);
     }
-    const int Lbits = nv > 0 ? 32 - __clz(nv) : 0;
-    const int sigma = nv > 0 ? 60 - E - Lbits : 0;
+    const int sigma = colprep_sigma(nv, E);
 
     long long q = 0;
     int inx = 0;
@@ -108,11 +137,7 @@ __device__ __forceinline__ void colprep_column(const T *__restrict__ col, ColInf
         Q += s_q[w];
         I += s_inx[w];
     }
-    // 32-bit weights: drop the fewest low bits that bring the total below
-    // 2^32 (floor(floor(x) / 2^s) = floor(x / 2^s), so q32 = q >> s is the
-    // weight rounded down at scale sigma - s, and sum q32 <= Q / 2^s < 2^32)
-    const int qbits = Q > 0 ? 64 - __clzll(Q) : 0;
-    const int shift = qbits > 32 ? qbits - 32 : 0;
+    const int shift = colprep_shift32(Q);
     const uint64_t lowmask = (1ull << shift) - 1ull;
     long long q32 = 0;
     int inx32 = 0;
@@ -140,17 +165,7 @@ __device__ __forceinline__ void colprep_column(const T *__restrict__ col, ColInf
             Q32 += s_q[w];
             I32 += s_inx[w];
         }
-        ColInfo c;
-        c.Q = Q;
-        c.sigma = sigma;
-        c.n_valid = nv;
-        c.n_inexact = I;
-        c.flags = (nv > 0 && (Emin < WideRange<T>::lo || E > WideRange<T>::hi)) ? COL_WIDE : 0;
-        c.Q32 = (uint32_t)Q32;
-        c.shift32 = shift;
-        c.n_inexact32 = I32;
-        c.pad_ = 0;
-        *out = c;
+        *out = colprep_make<T>(Q, sigma, nv, I, Emin, E, Q32, shift, I32);
     }
 }
 
