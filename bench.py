@@ -142,7 +142,8 @@ def _src_hash() -> str:
     """Hash of the pair kernel's code (comments and whitespace stripped, so a
     comment edit does not orphan the committed ncu summaries)."""
     h = hashlib.sha256()
-    for f in ("k_pairs.cu", "pairs.cuh", "select32.cuh", "common.cuh", "binmap.cuh"):
+    for f in ("k_pairs.cu", "k_pairs_shape.cu", "pairs.cuh", "select32.cuh", "common.cuh",
+              "binmap.cuh"):
         src = open(os.path.join(ROOT, "paper_2402_16712_gb300", "csrc", f)).read()
         src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
         src = re.sub(r"//[^\n]*", " ", src)
@@ -445,7 +446,8 @@ def run_gpu(args):
         "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT,
                 "tuning": tuning64},
         "roofline": roofline(n, pairs, kms, plan["kchunk"], plan["column"], l2_gbs,
-                             smem_gbs, _profile_traffic()),
+                             smem_gbs, _profile_traffic(),
+                             pair_shape(plan["warps"], plan["ctas_per_sm"])),
         "e2e": {"value": pairs / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": int(X.nbytes), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches_per_fit * args.steps,
@@ -478,10 +480,18 @@ def measure_ceilings(dev, stream):
     return l2 / 1e9, sm / 1e9
 
 
-def roofline(n, pairs, kms, kchunk, column, l2_gbs, smem_gbs, traffic):
+def pair_shape(warps, ctas):
+    """The library's launch shape for warps per CTA x CTAs per SM (the rule of
+    pair_shape in csrc/k_pairs.cu): 2 = 128 registers (<= 16 resident warps),
+    0 = 80 registers (17-24 resident, CTAs of <= 8 warps), 1 = 64 registers (25-32)."""
+    t = warps * ctas
+    return 2 if t <= 16 else (0 if t <= 24 else 1)
+
+
+def roofline(n, pairs, kms, kchunk, column, l2_gbs, smem_gbs, traffic, shape=0):
     """The pair kernel against its three ceilings; the binding one (the fewest
-    pairs/s) is the headline roofline.  kchunk and column are those of the
-    timed launch's plan (column 1: x_ijhat staged in shared memory)."""
+    pairs/s) is the headline roofline.  kchunk, column and shape are those of
+    the timed launch's plan (column 1: x_ijhat staged in shared memory)."""
     pps = pairs / (kms * 1e-3)
     alu_peak = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     per = {
@@ -504,7 +514,7 @@ def roofline(n, pairs, kms, kchunk, column, l2_gbs, smem_gbs, traffic):
     c = ceilings[bound]
     return {"bound": bound, "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
             "frac": c["frac"], "traffic": traffic,
-            "kernel": f"k_pairs<float, 0, {1 if column == 1 else 0}>",
+            "kernel": f"k_pairs<float, 0, {1 if column == 1 else 0}, {shape}>",
             "kernel_ms": kms, "basis": c["basis"], "ceilings": ceilings}
 
 
@@ -1021,8 +1031,10 @@ def run_profile_case(args):
     for _ in range(args.fits):
         l1line.fit(Xd, lams, workspace=ws)
     rc = l1line.status(ws)
+    plan = (l1line.plan(Xd.dtype, args.n, args.m) if args.n <= l1line.max_rows(Xd.dtype)
+            else "global-memory cluster path")
     print(f"profile case n={args.n} m={args.m} {dt} d0={args.d0 or 'planner'}: "
-          f"plan={l1line.plan(Xd.dtype, args.n, args.m)} status={l1line.status_string(rc)}")
+          f"plan={plan} status={l1line.status_string(rc)}")
     return 0 if rc == l1line.OK else 1
 
 

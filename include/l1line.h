@@ -447,8 +447,14 @@ int64_t l1line_check_hits(int reset, int *line);
  * Tuning of the pair kernel's launch (for an autotuner).  Every field 0 means
  * "the planner's choice".  Results do not depend on the tuning (every
  * decision stays exact); only the speed does.
- *   warps        warps per CTA, 1..8
- *   ctas_per_sm  CTAs per SM that the shared-memory plan is sized for, 1..3
+ *   warps        warps per CTA, 1..16
+ *   ctas_per_sm  CTAs per SM that the shared-memory plan is sized for, 1..3;
+ *                at most 32 resident warps (warps x ctas_per_sm).  The
+ *                kernel is compiled for three register budgets: 128 registers
+ *                for up to 16 resident warps, 80 for 17-24 (CTAs of at most
+ *                8 warps; 17-24 resident warps in larger CTAs is not a plan),
+ *                64 for 25-32 (planner: the most resident warps whose
+ *                candidate lists fit; on a tie the fewer CTAs)
  *   kchunk       k per CTA of single-instance calls (the batched call always
  *                gives a CTA a whole column jhat)
  *   d0           half-width, in positions of the 64 weight-proportional

@@ -84,7 +84,7 @@ def candidates(base: dict, kchunk: bool = True, classes: bool = False):
     for c in (1, 2):
         if c != base.get("column"):
             yield {"column": c}
-    for warps, ctas in ((8, 2), (6, 3), (4, 3), (4, 2), (8, 1)):
+    for warps, ctas in ((16, 2), (8, 3), (16, 1), (8, 2), (12, 1), (6, 3), (4, 3), (8, 1)):
         yield {"warps": warps, "ctas_per_sm": ctas}
 
 

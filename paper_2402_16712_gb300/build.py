@@ -23,6 +23,11 @@ LIB_CHECKS = os.path.join(HERE, "libl1line_checks.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["k_prep.cu", "k_pairs.cu", "k_large.cu", "k_exact.cu", "k_reduce.cu", "k_batch.cu", "k_propose.cu",
            "k_path.cu", "k_solpath.cu", "k_probe.cu", "abi.cu"]
+# the pair kernels once per (launch shape, kind): (source, object, defines)
+SHAPE_UNITS = [("k_pairs_shape.cu", f"k_pairs_s{sh}_p{pk}.o",
+                [f"-DL1L_SHAPE={sh}", f"-DL1L_PERSIST={pk}"])
+               for sh in range(3) for pk in range(2)]
+UNITS = [(src, src.replace(".cu", ".o"), []) for src in SOURCES] + SHAPE_UNITS
 
 
 def nvcc() -> str:
@@ -55,16 +60,19 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
     cc = nvcc()
     extra = ["-DL1L_CHECKS=1"] if checks else []
 
-    def one(src):
-        obj = os.path.join(bdir, src.replace(".cu", ".o"))
-        cmd = [cc, *_flags(verbose), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+    def one(unit):
+        src, objname, defs = unit
+        obj = os.path.join(bdir, objname)
+        cmd = [cc, *_flags(verbose), *extra, *defs, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+            raise RuntimeError(f"nvcc failed for {src} {' '.join(defs)}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=jobs or min(len(SOURCES), os.cpu_count() or 4)) as ex:
-        results = list(ex.map(one, SOURCES))
+    # the slowest units first, so that they start before the quick ones
+    units = SHAPE_UNITS + [u for u in UNITS if u not in SHAPE_UNITS]
+    with cf.ThreadPoolExecutor(max_workers=jobs or min(len(units), os.cpu_count() or 4)) as ex:
+        results = list(ex.map(one, units))
     if verbose:
         for _, err in results:
             sys.stderr.write(err)

@@ -856,7 +856,12 @@ const char *l1line_status_string(int status) {
 int l1line_last_launch_count(void) { return g_last_launches; }
 
 #if L1L_CHECKS
-extern "C" long long l1l_checks_pairs(int, int *);
+extern "C" long long l1l_checks_shape_0_0(int, int *);
+extern "C" long long l1l_checks_shape_1_0(int, int *);
+extern "C" long long l1l_checks_shape_2_0(int, int *);
+extern "C" long long l1l_checks_shape_0_1(int, int *);
+extern "C" long long l1l_checks_shape_1_1(int, int *);
+extern "C" long long l1l_checks_shape_2_1(int, int *);
 extern "C" long long l1l_checks_batch(int, int *);
 extern "C" long long l1l_checks_exact(int, int *);
 extern "C" long long l1l_checks_path(int, int *);
@@ -868,7 +873,10 @@ extern "C" long long l1l_checks_large(int, int *);
 int64_t l1line_check_hits(int reset, int *line) {
 #if L1L_CHECKS
     if (cudaDeviceSynchronize() != cudaSuccess) return -2;
-    long long (*readers[])(int, int *) = {l1l_checks_pairs, l1l_checks_batch, l1l_checks_exact,
+    long long (*readers[])(int, int *) = {l1l_checks_shape_0_0, l1l_checks_shape_1_0,
+                                          l1l_checks_shape_2_0, l1l_checks_shape_0_1,
+                                          l1l_checks_shape_1_1, l1l_checks_shape_2_1,
+                                          l1l_checks_batch, l1l_checks_exact,
                                           l1l_checks_path, l1l_checks_solpath,
                                           l1l_checks_propose, l1l_checks_large};
     long long total = 0;
@@ -890,7 +898,7 @@ int l1line_set_tuning(const l1line_tuning *t) {
         g_tune = Tune();
         return L1L_OK;
     }
-    if (t->warps < 0 || t->warps > 8 || t->ctas_per_sm < 0 || t->ctas_per_sm > 3 ||
+    if (t->warps < 0 || t->warps > 16 || t->ctas_per_sm < 0 || t->ctas_per_sm > 3 ||
         t->kchunk < 0 || t->d0 < 0 || t->d0 > 24 || t->batch_classes < 0 ||
         t->batch_classes > MAX_BATCH_CLASSES || t->column < 0 || t->column > 2)
         return L1L_ERR_ARG;

@@ -6,6 +6,7 @@
 // sequence can be captured in a CUDA graph.
 #include <algorithm>
 
+#include "batch.cuh"
 #include "common.cuh"
 #include "exact.cuh"
 #include "launch.h"
@@ -13,47 +14,6 @@
 #include "prep.cuh"
 
 namespace l1l {
-
-// Largest b with begin[b] <= x (begin is a non-decreasing prefix, begin[0] = 0).
-template <typename I>
-__device__ __forceinline__ int find_inst(const I *begin, int count, I x) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (begin[mid] <= x)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    return lo;
-}
-
-template <typename T>
-__device__ __forceinline__ ScanArgs<T> inst_args(const BatchDesc<T> &bd, int b,
-                                                 unsigned char *ws) {
-    const BatchInst<T> &in = bd.inst[b];
-    const InstLayout L = inst_layout(in.m, in.ldn, in.nl, sizeof(T));
-    unsigned char *base = ws + in.ws_off;
-    ScanArgs<T> a;
-    a.Xt = reinterpret_cast<const T *>(base + L.Xt);
-    a.Xf = reinterpret_cast<const float *>(base + L.Xf);
-    a.ci = reinterpret_cast<const ColInfo *>(base + L.ci);
-    a.n = in.n;
-    a.m = in.m;
-    a.ldn = in.ldn;
-    a.n_lambda = in.nl;
-    a.v_all = reinterpret_cast<T *>(base + L.v_all);
-    a.s_all = reinterpret_cast<double *>(base + L.s_all);
-    a.status = reinterpret_cast<uint32_t *>(ws);
-    a.slow_count = reinterpret_cast<uint32_t *>(ws + 256);
-    a.slow = reinterpret_cast<SlowEntry *>(ws + BATCH_HEAD);
-    a.force_exact = bd.force_exact;
-    a.inst = b;
-    a.jlist = nullptr;
-    a.nj = a.m;
-    a.d0 = bd.d0;
-    return a;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose_b(const __grid_constant__ BatchDesc<T> bd,
@@ -79,32 +39,6 @@ __global__ void __launch_bounds__(256) k_colprep_b(const __grid_constant__ Batch
     const T *Xt = reinterpret_cast<const T *>(ws + in.ws_off + L.Xt);
     ColInfo *ci = reinterpret_cast<ColInfo *>(ws + in.ws_off + L.ci);
     colprep_column<T>(Xt + (int64_t)j * in.ldn, ci + j, in.n);
-}
-
-// Persistent: every CTA loops, taking the next (instance, jhat) unit of units
-// [u0, u1) (one size class of the batch) from that class's counter; units are
-// numbered largest instance first.  No CTA waits on another.
-template <typename T, bool MULTI, bool CS>
-__global__ void __launch_bounds__(256, 3)
-    k_pairs_persist(const __grid_constant__ BatchDesc<T> bd, unsigned char *ws, int64_t u0,
-                    int64_t u1, int slot, int lay_npad, int cap) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Decide s_dec[NDEC];
-    __shared__ long long s_unit;
-    unsigned long long *counter = reinterpret_cast<unsigned long long *>(ws + 512) + slot;
-    for (;;) {
-        if (threadIdx.x == 0) s_unit = (long long)atomicAdd(counter, 1ull);
-        __syncthreads();
-        const int64_t u = u0 + s_unit;
-        __syncthreads();
-        if (u >= u1) break;
-        const int b = find_inst<int64_t>(bd.unit_begin, bd.count, u);
-        const BatchInst<T> &in = bd.inst[b];
-        const ScanArgs<T> a = inst_args<T>(bd, b, ws);
-        const LamView lv{bd.lam + bd.lam_begin[b], in.tl_min, in.tl_max};
-        pairs_unit<T, MULTI, CS>(a, lv, 0, in.nl, (int)(u - bd.unit_begin[b]), 0, in.m, cap,
-                             lay_npad, smem, s_dec);
-    }
 }
 
 template <typename T>
@@ -197,20 +131,13 @@ cudaError_t launch_batch(const BatchDesc<T> &bd, unsigned char *ws, T *out_v, do
     for (int c = 0; c < nclasses; ++c) {
         const BatchClass &bc = classes[c];
         if (bc.u1 <= bc.u0) continue;
-        auto kern = multi ? (bc.plan.cs ? k_pairs_persist<T, true, true>
-                                        : k_pairs_persist<T, true, false>)
-                          : (bc.plan.cs ? k_pairs_persist<T, false, true>
-                                        : k_pairs_persist<T, false, false>);
-        e = ensure_smem(reinterpret_cast<const void *>(kern), bc.plan.smem);
+        switch (bc.plan.shape) {
+            case SHAPE_R80: e = launch_persist_sh<T, SHAPE_R80>(bd, ws, bc, c, multi, num_sms, st); break;
+            case SHAPE_R64: e = launch_persist_sh<T, SHAPE_R64>(bd, ws, bc, c, multi, num_sms, st); break;
+            case SHAPE_R128: e = launch_persist_sh<T, SHAPE_R128>(bd, ws, bc, c, multi, num_sms, st); break;
+            default: e = cudaErrorInvalidConfiguration;
+        }
         if (e != cudaSuccess) return e;
-        int per_sm = 0;
-        e = blocks_per_sm(reinterpret_cast<const void *>(kern), bc.plan.warps * 32, bc.plan.smem,
-                          &per_sm);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        const int64_t grid = std::min<int64_t>((int64_t)num_sms * per_sm, bc.u1 - bc.u0);
-        kern<<<(unsigned)grid, bc.plan.warps * 32, bc.plan.smem, st>>>(
-            bd, ws, bc.u0, bc.u1, c, bc.lay_npad, bc.plan.cap);
         launches++;
     }
     k_exact_b<T><<<num_sms * 2, 128, 0, st>>>(bd, ws);

@@ -1,5 +1,6 @@
-// k_pairs.cu -- the pair kernel for one instance (grid over jhat x k-chunks)
-// and its shared-memory planner; the per-pair algorithm is in pairs.cuh.
+// k_pairs.cu -- the shared-memory planner of the pair kernels and the launch
+// of the single-instance kernel in the planned shape (the kernels themselves
+// are in k_pairs_shape.cu, the per-pair algorithm in pairs.cuh).
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -58,24 +59,6 @@ cudaError_t blocks_per_sm(const void *fn, int threads, size_t smem, int *out) {
     return cudaSuccess;
 }
 
-template <typename T, bool MULTI, bool CS>
-__global__ void __launch_bounds__(256, 3)
-    k_pairs(ScanArgs<T> a, const __grid_constant__ LambdaPack lp, int t0, int nlc, int kchunk,
-            int cap) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ Decide s_dec[NDEC];
-    const int64_t k0 = (int64_t)blockIdx.y * kchunk;
-    const int64_t k1 = min(a.m, k0 + kchunk);
-    const LamView lv{lp.lam, lp.tl_min, lp.tl_max};
-    const int64_t j = a.jlist ? (int64_t)a.jlist[blockIdx.x] : (int64_t)blockIdx.x;
-    if (j < 0 || j >= a.m) {  // uniform over the CTA
-        if (threadIdx.x == 0) atomicOr(a.status, ST_BADINDEX);
-        return;
-    }
-    pairs_unit<T, MULTI, CS>(a, lv, t0, nlc, (int)j, k0, k1, cap,
-                         ((int)a.n + ROW_PAD - 1) & ~(ROW_PAD - 1), smem, s_dec);
-}
-
 // Candidate slots per warp (a multiple of 32: 32 lanes x quota).  About 40% of
 // the rows, at least 512 (small n: every row fits).
 template <typename T> static int cap_for(int64_t npad) {
@@ -94,10 +77,23 @@ template <typename T> int64_t max_rows_pairs() {
     return n;
 }
 
+// 17-24 resident warps only in CTAs of up to 8 warps (80 registers): larger
+// CTAs there would take the 64-register budget, whose spills cost more than
+// the extra warps gain (3500 x 1000 float: 11 x 2 warps at 64 registers
+// 8.1 ms, 16 x 1 at 128 registers 7.3 ms).
+int pair_shape(int warps, int ctas) {
+    if (warps < 1 || warps > 16 || ctas < 1 || ctas > 3) return -1;
+    const int t = warps * ctas;
+    if (t <= 16) return SHAPE_R128;
+    if (t <= 24) return warps <= 8 ? SHAPE_R80 : -1;
+    if (t <= 32) return SHAPE_R64;
+    return -1;
+}
+
 // The resident-warp plan for one placement of x_ijhat (cs: shared memory).
 template <typename T>
 static PairPlan plan_placement(int64_t npad, bool cs, int d0, const Tune &tune) {
-    PairPlan p{0, 0, 0, 0, 0, 0, 0, 0};
+    PairPlan p{0, 0, 0, 0, 0, 0, 0, 0, 0};
     const size_t cb = PairSmem<T>::col_bytes(npad, cs);
     // Per-lane candidate quota wanted: the level-0 bracket (+-d0 of 64 weight
     // samples) holds ~2.5% of the rows per sample position, i.e. mu = 0.025 d0
@@ -105,18 +101,22 @@ static PairPlan plan_placement(int64_t npad, bool cs, int d0, const Tune &tune) 
     // lanes rarely overflows (an overflow costs one more pass).
     const double mu = 0.025 * (double)d0 * (double)npad / 32.0;
     const int64_t qt_need = std::min<int64_t>(npad / 32, (int64_t)ceil(mu + 3.5 * sqrt(mu) + 1.0));
-    // Up to three 8-warp CTAs per SM fit the register budget (80 registers x
-    // 256 threads).  Over 1-3 CTAs per SM and 1-8 warps per CTA (or the
-    // caller's choice), keep the plan with the most resident warps whose lists
-    // meet the quota in 228 KB of shared memory (1 KB reserved per CTA,
-    // static arrays included).
+    // Over 1-3 CTAs per SM and 1-16 warps per CTA (or the caller's choice),
+    // up to 32 resident warps in one of the launch shapes (pair_shape), keep
+    // the plan with the most resident warps whose lists meet the quota in
+    // 228 KB of shared memory (1 KB reserved per CTA, static arrays included);
+    // on a tie the fewer, larger CTAs (column jhat staged fewer times, so
+    // longer lists per warp).  Measured, 2000 x 2000 float: 16 x 2 warps
+    // (64 registers) 14.1 ms, 8 x 3 (80 registers) 14.4 ms; 5000 x 1000:
+    // 16 x 1 (128 registers, x_ijhat in shared memory) 11.0 ms, 8 x 2 with
+    // x_ijhat in global memory 13.6 ms.
     int w = 0, cap = 0, best = 0, nc = 0;
     const int c_hi = tune.ctas > 0 ? tune.ctas : 3, c_lo = tune.ctas > 0 ? tune.ctas : 1;
-    const int w_hi = tune.warps > 0 ? tune.warps : 8, w_lo = tune.warps > 0 ? tune.warps : 1;
-    for (int ctas = c_hi; ctas >= c_lo; --ctas) {
+    const int w_hi = tune.warps > 0 ? tune.warps : 16, w_lo = tune.warps > 0 ? tune.warps : 1;
+    for (int ctas = c_lo; ctas <= c_hi; ++ctas) {
         const int64_t per_cta = 233472 / ctas - 1024 - 1024;
         for (int cand = w_hi; cand >= w_lo; --cand) {
-            if (ctas * cand <= best || ctas * cand > 24) continue;
+            if (ctas * cand <= best || pair_shape(cand, ctas) < 0) continue;
             const int64_t fit = PairSmem<T>::cap_fit((per_cta - (int64_t)cb) / cand);
             const int64_t c32 = std::min<int64_t>(npad, fit) & ~int64_t(31);
             if (fit > 0 && c32 >= 32 * qt_need) {
@@ -133,21 +133,23 @@ static PairPlan plan_placement(int64_t npad, bool cs, int d0, const Tune &tune) 
     p.ctas = nc;
     p.d0 = d0;
     p.cs = cs ? 1 : 0;
+    p.shape = pair_shape(w, nc);
     p.smem = cb + (size_t)w * PairSmem<T>::warp_bytes(cap);
     return p;
 }
 
 template <typename T>
 PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune) {
-    PairPlan p{0, 0, 0, 0, 0, 0, 0, 0};
+    PairPlan p{0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t npad = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
     if (n > max_rows_pairs<T>()) return p;
     const int d0 = tune.d0 > 0 ? tune.d0 : D0_DEFAULT;
     // Where x_ijhat lives.  Shared memory saves the residual pass an L2 read
     // per row; global memory frees n * sizeof(T) bytes per CTA.  Measured:
-    // float keeps it in shared memory unless the smaller footprint admits more
-    // resident warps (2000 x 2000: equal plans, shared 3% faster; 5000 x 1000:
-    // 8 -> 14 warps per SM, global 11% faster); double reads it from global
+    // float keeps it in shared memory whenever that plan holds at least 16
+    // resident warps or as many as the global one (2000 x 2000: equal plans,
+    // shared 2-4% faster; 3500 x 1000: 16 warps in shared memory 7.3 ms, 21
+    // with x_ijhat in global memory 7.7 ms); double reads it from global
     // memory (2000 x 2000: 5% faster at equal plans).
     const PairPlan ps = tune.column == 2 ? p : plan_placement<T>(npad, true, d0, tune);
     const PairPlan pg = tune.column == 1 ? p : plan_placement<T>(npad, false, d0, tune);
@@ -158,7 +160,7 @@ PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &t
     else if (rs == 0)
         p = pg;
     else
-        p = (sizeof(T) == 8 || rg > rs) ? pg : ps;
+        p = (sizeof(T) == 8 || (rg > rs && rs < 16)) ? pg : ps;
     const int w = p.warps, nc = p.ctas;
     int64_t chunks;
     if (tune.kchunk > 0) {
@@ -191,12 +193,6 @@ PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &t
 template <typename T>
 cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
                          const PairPlan &plan, cudaStream_t st, int &launches) {
-    // separate instantiations keep the single-lambda kernel small
-    auto kern = nlc >= 3 ? (plan.cs ? k_pairs<T, true, true> : k_pairs<T, true, false>)
-                         : (plan.cs ? k_pairs<T, false, true> : k_pairs<T, false, false>);
-    cudaError_t e = ensure_smem(reinterpret_cast<const void *>(kern), plan.smem);
-    if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)a.nj, (unsigned)plan.kchunks);
     LambdaPack lp;
     lp.tl_min = lp.tl_max = 0;
     for (int q = 0; q < nlc; ++q) {
@@ -204,9 +200,15 @@ cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, in
         if (lp.lam[q] < lp.lam[lp.tl_min]) lp.tl_min = q;
         if (lp.lam[q] > lp.lam[lp.tl_max]) lp.tl_max = q;
     }
-    kern<<<grid, plan.warps * 32, plan.smem, st>>>(a, lp, t0, nlc, plan.kchunk, plan.cap);
+    cudaError_t e;
+    switch (plan.shape) {
+        case SHAPE_R80: e = launch_pairs_sh<T, SHAPE_R80>(a, lp, t0, nlc, plan, st); break;
+        case SHAPE_R64: e = launch_pairs_sh<T, SHAPE_R64>(a, lp, t0, nlc, plan, st); break;
+        case SHAPE_R128: e = launch_pairs_sh<T, SHAPE_R128>(a, lp, t0, nlc, plan, st); break;
+        default: e = cudaErrorInvalidConfiguration;
+    }
     launches++;
-    return cudaGetLastError();
+    return e;
 }
 
 template PairPlan plan_pairs<float>(int64_t, int64_t, int, int64_t, const Tune &);
@@ -218,6 +220,5 @@ template cudaError_t launch_pairs<float>(const ScanArgs<float> &, const double *
 template cudaError_t launch_pairs<double>(const ScanArgs<double> &, const double *, int, int,
                                           const PairPlan &, cudaStream_t, int &);
 
-L1L_CHECKS_READER(l1l_checks_pairs)
 
 }  // namespace l1l

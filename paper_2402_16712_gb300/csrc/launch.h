@@ -21,6 +21,18 @@ template <typename T>
 cudaError_t launch_prep(const T *X, T *Xt, float *Xf, ColInfo *ci, int64_t n, int64_t m,
                         int64_t ldn, uint32_t *status, cudaStream_t st, int &launches);
 
+// Launch shapes of the pair kernels: one compiled instantiation per register
+// budget, which follows from the resident threads it is compiled for.
+enum : int {
+    SHAPE_R80 = 0,   // <= 8 warps per CTA, <= 24 warps per SM: 80 registers
+    SHAPE_R64 = 1,   // <= 16 warps per CTA, <= 32 warps per SM: 64 registers
+    SHAPE_R128 = 2,  // <= 16 warps per CTA, <= 16 warps per SM: 128 registers
+};
+// The shape of `warps` per CTA x `ctas` per SM: up to 16 resident warps
+// SHAPE_R128, 17-24 SHAPE_R80 (CTAs of up to 8 warps only), 25-32 SHAPE_R64;
+// -1 for any other plan.
+int pair_shape(int warps, int ctas);
+
 // Shared-memory plan of the pair kernel for a given n; warps == 0 if n is too
 // large for the kernel.
 struct PairPlan {
@@ -28,10 +40,11 @@ struct PairPlan {
     size_t smem;
     int kchunk;
     int kchunks;
-    int cap;   // per-warp candidate-list capacity
-    int ctas;  // CTAs per SM the shared memory is sized for
-    int d0;    // first-bracket half-width of the selection
-    int cs;    // 1: x_ijhat staged in shared memory; 0: read from global memory
+    int cap;    // per-warp candidate-list capacity
+    int ctas;   // CTAs per SM the shared memory is sized for
+    int d0;     // first-bracket half-width of the selection
+    int cs;     // 1: x_ijhat staged in shared memory; 0: read from global memory
+    int shape;  // SHAPE_*
 };
 // Caller overrides of the planner (0 = the planner's choice).
 struct Tune {
@@ -47,6 +60,10 @@ template <typename T> int64_t max_rows_pairs();
 template <typename T>
 cudaError_t launch_pairs(const ScanArgs<T> &a, const double *lambdas, int t0, int nlc,
                          const PairPlan &plan, cudaStream_t st, int &launches);
+// The same for one shape S == plan.shape (k_pairs_shape.cu).
+template <typename T, int S>
+cudaError_t launch_pairs_sh(const ScanArgs<T> &a, const LambdaPack &lp, int t0, int nlc,
+                            const PairPlan &plan, cudaStream_t st);
 
 // Largest n of any scan or fit: the global-memory path's limit (row counts
 // and the exact path's row loop are 32-bit).
@@ -147,6 +164,13 @@ struct BatchClass {
     PairPlan plan;
 };
 constexpr int MAX_BATCH_CLASSES = 3;
+
+// The persistent pair kernel of one size class (shape S == bc.plan.shape;
+// k_pairs_shape.cu): as many CTAs as stay resident, pulling units from the
+// class's counter `slot`.
+template <typename T, int S>
+cudaError_t launch_persist_sh(const BatchDesc<T> &bd, unsigned char *ws, const BatchClass &bc,
+                              int slot, bool multi, int num_sms, cudaStream_t st);
 
 // The batched fit: staging, one persistent pair kernel per size class, exact
 // path, sums, argmin.

@@ -317,12 +317,15 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
     // The pivots sit 2G + 1 keys outside the sample keys: a sample row (or any
     // row tied with it) then lies clear of the bracket's guard bands instead of
     // always needing an exact division.
-    uint32_t P1 = pick(jx - d0, lo0);
-    uint32_t P2 = pick(jx + d0, hi0);
-    P1 = max(sat_sub(P1, 2 * G + 1), lo0);
-    P2 = min(sat_add(P2, 2 * G + 1), hi0);
-    if (P1 > P2) P1 = P2;
+    auto sample_bracket = [&](int d, uint32_t &Q1, uint32_t &Q2) {
+        Q1 = max(sat_sub(pick(jx - d, lo0), 2 * G + 1), lo0);
+        Q2 = min(sat_add(pick(jx + d, hi0), 2 * G + 1), hi0);
+        if (Q1 > Q2) Q1 = Q2;
+    };
+    uint32_t P1, P2;
+    sample_bracket(d0, P1, P2);
     bool sampled = true;
+    int dcur = d0;  // half-width of the current sample bracket
 
     const uint32_t lbase = smem_addr(lst) + (uint32_t)lane * 8u;
     const uint32_t lend = lbase + (uint32_t)qt * 256u;
@@ -355,7 +358,15 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
         cnt = (int)((sp - lbase) >> 8);
         Sb = __reduce_add_sync(FULL, Sb);  // < Q32 < 2^32
         __syncwarp();
-        if (__any_sync(FULL, cnt > qt)) return SEL_W64;  // a lane overflowed its quota
+        if (__any_sync(FULL, cnt > qt)) {
+            // a lane overflowed its quota: the bracket holds more rows than its
+            // weight share suggests (light rows); halve it around the sample
+            // estimate and pass again (the list keeps nothing of this pass)
+            if (!sampled || dcur <= 1) return SEL_W64;
+            dcur >>= 1;
+            sample_bracket(dcur, P1, P2);
+            continue;
+        }
 
         // ---- exact histogram of the candidates over the bins of [P1, P2].
         // Pass A: a candidate whose approximate key is at least G inside P1,
@@ -418,7 +429,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
         if (r1 == 1) {  // median below P1: retry under P1
             hi0 = P1 - 1;
             P2 = hi0;
-            P1 = sampled ? max(sat_sub(pick(jx - 3 * max(d0, 1) - 1, lo0), 2 * G + 1), lo0) : lo0;
+            P1 = sampled ? max(sat_sub(pick(jx - 3 * max(dcur, 1) - 1, lo0), 2 * G + 1), lo0) : lo0;
             if (P1 > P2) P1 = lo0;
             continue;
         }
@@ -430,7 +441,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
             if (P2 >= hi0) return SEL_INTERNAL;
             lo0 = P2 + 1;
             P1 = lo0;
-            P2 = sampled ? min(sat_add(pick(jx + 3 * max(d0, 1) + 1, hi0), 2 * G + 1), hi0) : hi0;
+            P2 = sampled ? min(sat_add(pick(jx + 3 * max(dcur, 1) + 1, hi0), 2 * G + 1), hi0) : hi0;
             if (P2 < P1) P2 = hi0;
             continue;
         }

@@ -44,7 +44,7 @@ def test_candidates_vary_one_knob_group():
 def test_tuning_argument_checks():
     __graft_entry__.build()
     l1line.load()
-    for bad in ({"warps": 9}, {"ctas_per_sm": 4}, {"kchunk": -1}, {"d0": 25}, {"warps": -1},
+    for bad in ({"warps": 17}, {"ctas_per_sm": 4}, {"kchunk": -1}, {"d0": 25}, {"warps": -1},
                 {"batch_classes": 4}, {"batch_classes": -1}, {"column": 3}, {"column": -1}):
         with pytest.raises(l1line.L1LineError):
             l1line.set_tuning(bad)

@@ -21,14 +21,14 @@ def test_roofline_picks_the_binding_ceiling():
     # the binding ceiling (fewest pairs/s) is shared memory here
     assert r["bound"] == "smem" and r["unit"] == "GB/s"
     assert r["frac"] == c["smem"]["frac"] and r["traffic"] is None
-    assert r["kernel"] == "k_pairs<float, 0, 1>" and r["kernel_ms"] == 20.0
+    assert r["kernel"] == "k_pairs<float, 0, 1, 0>" and r["kernel_ms"] == 20.0
 
 
 def test_roofline_names_the_timed_placement_and_binding_l2():
     import bench
     # a slow L2 makes L2 the binding ceiling; column 2 keeps x_ijhat in global memory
     r = bench.roofline(2000, 3_998_000, 20.0, 1000, 2, 1_000.0, 40_000.0, 1.7e7)
-    assert r["bound"] == "l2" and r["kernel"] == "k_pairs<float, 0, 0>"
+    assert r["bound"] == "l2" and r["kernel"] == "k_pairs<float, 0, 0, 0>"
     assert r["achieved"] == pytest.approx(1.999e8 * 4 * 2000 * 1.001 / 1e9)
     assert r["traffic"] == 1.7e7
 
@@ -270,3 +270,12 @@ def test_path_roofline_arithmetic():
     t_alu = instr / (c["alu"]["peak"] * 1e12)
     assert r["bound"] == ("hbm" if t_hbm > t_alu else "alu")
     assert r["frac"] == c[r["bound"]]["frac"]
+
+
+def test_pair_shape_label_follows_the_register_budgets():
+    import bench
+    # 128 registers up to 16 resident warps, 80 up to 24 with <= 8 warps per
+    # CTA, 64 up to 32
+    assert [bench.pair_shape(w, c) for w, c in ((16, 1), (8, 2), (4, 3), (8, 3), (7, 3),
+                                                (16, 2), (13, 2), (10, 3))] == \
+        [2, 2, 2, 0, 0, 1, 1, 1]

@@ -134,3 +134,38 @@ def test_size_classes_give_identical_results(dtype):
         for b, (a, c) in enumerate(zip(runs[1], r)):
             assert torch.equal(a[0].view(ib), c[0].view(ib)), (k, b)
             assert torch.equal(a[1], c[1]) and torch.equal(a[2], c[2]), (k, b)
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_every_launch_shape_gives_identical_results(dtype):
+    """The persistent pair kernel in each compiled register budget (128
+    registers: 4 x 2 and 16 x 1 warps; 80: 8 x 3; 64: 16 x 2) on instances
+    up to n = 1500 (every shape's lists fit): every shape matches the
+    planner's run bit for bit, and the planner's run matches the oracle."""
+    rng = np.random.default_rng(91)
+    Xs, lams = [], []
+    for b, n in enumerate((1500, 80, 1100, 700, 1400, 333)):
+        m = int(rng.integers(2, 16))
+        X, _, _ = datagen.planted(datagen.Planted(n, m, max(1, m // 4), 0.1, 0.15, 10.0,
+                                                  7000 + b, np.dtype(dtype).name))
+        Xs.append(X)
+        lams.append(np.array([0.0, 0.4]))
+    Xd = [torch.from_numpy(X).cuda() for X in Xs]
+    l1line.set_tuning(None)
+    bat = l1line.Batched(Xd, lams)
+    bat.run()
+    assert bat.status() == l1line.OK
+    ref = [tuple(t.clone() for t in r) for r in bat.results()]
+    _check(Xs, lams, ref, "planner")
+    ib = torch.int32 if dtype == np.float32 else torch.int64
+    for warps, ctas in ((4, 2), (8, 3), (16, 2), (16, 1)):
+        l1line.set_tuning({"warps": warps, "ctas_per_sm": ctas, "batch_classes": 1})
+        try:
+            b2 = l1line.Batched(Xd, lams)
+            b2.run()
+        finally:
+            l1line.set_tuning(None)
+        assert b2.status() == l1line.OK
+        for b, (a, c) in enumerate(zip(ref, b2.results())):
+            assert torch.equal(a[0].view(ib), c[0].view(ib)), (warps, ctas, b)
+            assert torch.equal(a[1], c[1]) and torch.equal(a[2], c[2]), (warps, ctas, b)
