@@ -12,6 +12,8 @@
 #include <numeric>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/l1line.h"
 #include "batch_split.h"
 #include "checks.cuh"
@@ -21,6 +23,20 @@
 using namespace l1l;
 
 namespace {
+
+// NVTX range over a scope (a no-op unless a profiler is attached): every
+// entry point that enqueues work and each stage of a fit (staging, pair
+// kernel with its exact path and sums, argmin) is one range on the calling
+// thread, so ncu/nsys timelines show which library call a kernel came from.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define L1L_RANGE_CAT2(a, b) a##b
+#define L1L_RANGE_CAT(a, b) L1L_RANGE_CAT2(a, b)
+#define L1L_RANGE(name) NvtxRange L1L_RANGE_CAT(nvtx_range_, __LINE__)(name)
 
 thread_local int g_last_launches = 0;
 thread_local Tune g_tune;  // l1line_set_tuning
@@ -192,6 +208,7 @@ int scan_setup(const T *X, int64_t n, int64_t m, const double *lambdas, int64_t 
 }
 
 template <typename T> int scan_prep(const T *X, Scan<T> &c) {
+    L1L_RANGE("l1l::stage");
     ScanArgs<T> &a = c.a;
     if (cudaMemsetAsync(a.status, 0, sizeof(uint32_t), c.st) != cudaSuccess) return L1L_ERR_CUDA;
     if (launch_prep<T>(X, const_cast<T *>(a.Xt), const_cast<float *>(a.Xf),
@@ -206,6 +223,7 @@ template <typename T> int scan_prep(const T *X, Scan<T> &c) {
 template <typename T>
 int scan_pairs_large(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jlist,
                      int64_t nj) {
+    L1L_RANGE("l1l::pairs_global_memory");
     ScanArgs<T> &a = c.a;
     const bool prof = g_ev_start && g_ev_stop;
     for (int64_t t0 = 0; t0 < nl; t0 += MAX_LAMBDA_PER_LAUNCH) {
@@ -229,6 +247,7 @@ int scan_pairs_large(Scan<T> &c, const double *lambdas, int64_t nl, const int32_
 // Steps A2-A5 for the jhat in jlist[0..nj) (jlist == nullptr: all m).
 template <typename T>
 int scan_pairs(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jlist, int64_t nj) {
+    L1L_RANGE("l1l::pairs");
     ScanArgs<T> &a = c.a;
     a.jlist = jlist;
     a.nj = nj;
@@ -257,6 +276,7 @@ int scan_pairs(Scan<T> &c, const double *lambdas, int64_t nl, const int32_t *jli
 
 template <typename T>
 int scan_argmin(Scan<T> &c, int64_t nl, T *out_v, double *out_obj, int32_t *out_jstar) {
+    L1L_RANGE("l1l::argmin");
     if (launch_argmin<T>(c.z, c.a.v_all, c.a.m, nl, c.a.jlist, c.a.nj, out_v, out_obj, out_jstar,
                          c.st, c.launches) != cudaSuccess)
         return L1L_ERR_CUDA;
@@ -479,6 +499,7 @@ size_t l1line_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t n_lambda)
 int l1line_scan_ex_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                        int64_t n_lambda, float *v_all, double *s_all, double *z_all,
                        void *workspace, size_t workspace_bytes, void *stream, uint32_t flags) {
+    L1L_RANGE("l1line_scan_ex_f32");
     return scan_impl<float>(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                             workspace_bytes, stream, flags);
 }
@@ -486,6 +507,7 @@ int l1line_scan_ex_f32(const float *X, int64_t n, int64_t m, const double *lambd
 int l1line_scan_ex_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                        int64_t n_lambda, double *v_all, double *s_all, double *z_all,
                        void *workspace, size_t workspace_bytes, void *stream, uint32_t flags) {
+    L1L_RANGE("l1line_scan_ex_f64");
     return scan_impl<double>(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                              workspace_bytes, stream, flags);
 }
@@ -493,6 +515,7 @@ int l1line_scan_ex_f64(const double *X, int64_t n, int64_t m, const double *lamb
 int l1line_scan_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                     int64_t n_lambda, float *v_all, double *s_all, double *z_all,
                     void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_scan_f32");
     return l1line_scan_ex_f32(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                               workspace_bytes, stream, 0u);
 }
@@ -500,6 +523,7 @@ int l1line_scan_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
 int l1line_scan_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                     int64_t n_lambda, double *v_all, double *s_all, double *z_all,
                     void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_scan_f64");
     return l1line_scan_ex_f64(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                               workspace_bytes, stream, 0u);
 }
@@ -507,6 +531,7 @@ int l1line_scan_f64(const double *X, int64_t n, int64_t m, const double *lambdas
 int l1line_fit_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, float *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_fit_f32");
     return fit_impl<float>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar,
                            workspace, workspace_bytes, stream);
 }
@@ -514,6 +539,7 @@ int l1line_fit_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
 int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, double *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_fit_f64");
     return fit_impl<double>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar,
                             workspace, workspace_bytes, stream);
 }
@@ -522,6 +548,7 @@ int l1line_fit_subset_f32(const float *X, int64_t n, int64_t m, const double *la
                           int64_t n_lambda, const int32_t *jhat_list, int64_t K, float *out_v,
                           double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_fit_subset_f32");
     if (!jhat_list) return L1L_ERR_ARG;
     return fit_impl<float>(X, n, m, lambdas, n_lambda, jhat_list, K, out_v, out_obj, out_jstar,
                            workspace, workspace_bytes, stream);
@@ -531,6 +558,7 @@ int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *l
                           int64_t n_lambda, const int32_t *jhat_list, int64_t K, double *out_v,
                           double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_fit_subset_f64");
     if (!jhat_list) return L1L_ERR_ARG;
     return fit_impl<double>(X, n, m, lambdas, n_lambda, jhat_list, K, out_v, out_obj, out_jstar,
                             workspace, workspace_bytes, stream);
@@ -547,18 +575,21 @@ size_t l1line_proposed_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t 
 
 int l1line_features_f32(const float *X, int64_t n, int64_t m, double lambda, float *out_raw,
                         float *out_std, void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_features_f32");
     return features_impl<float>(X, n, m, lambda, out_raw, out_std, workspace, workspace_bytes,
                                 stream);
 }
 
 int l1line_features_f64(const double *X, int64_t n, int64_t m, double lambda, float *out_raw,
                         float *out_std, void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_features_f64");
     return features_impl<double>(X, n, m, lambda, out_raw, out_std, workspace, workspace_bytes,
                                  stream);
 }
 
 int l1line_mlp_forward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
                        float *scores, void *stream) {
+    L1L_RANGE("l1line_mlp_forward");
     g_last_launches = 0;
     if (!feat || !mlp || !scores || N < 1) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
@@ -579,6 +610,7 @@ size_t l1line_mlp_workspace_bytes(int64_t N) {
 int l1line_mlp_backward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
                         const float *dscores, float *grad, void *workspace,
                         size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_mlp_backward");
     g_last_launches = 0;
     if (!feat || !mlp || !dscores || !grad || N < 1) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
@@ -598,6 +630,7 @@ int l1line_mlp_backward(const float *feat, const int32_t *rows, int64_t N, const
 int l1line_rank_loss(const float *scores, const float *targets, const int32_t *rows,
                      const int64_t *offsets, int64_t n_inst, float *dscores, float *loss,
                      void *stream) {
+    L1L_RANGE("l1line_rank_loss");
     g_last_launches = 0;
     if (!scores || !targets || !offsets || !dscores || !loss || n_inst < 1) return L1L_ERR_ARG;
     if (n_inst > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
@@ -612,6 +645,7 @@ int l1line_rank_loss(const float *scores, const float *targets, const int32_t *r
 int l1line_adam_step(float *theta, const float *grad, float *m1, float *m2, int64_t step,
                      float lr, float beta1, float beta2, float eps, l1line_mlp *mlp,
                      void *stream) {
+    L1L_RANGE("l1line_adam_step");
     g_last_launches = 0;
     if (!theta || !grad || !m1 || !m2 || step < 1) return L1L_ERR_ARG;
     if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
@@ -630,6 +664,7 @@ int l1line_adam_step(float *theta, const float *grad, float *m1, float *m2, int6
 }
 
 int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream) {
+    L1L_RANGE("l1line_mlp_pack");
     g_last_launches = 0;
     if (!theta || !mlp || (reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
     int launches = 0;
@@ -640,6 +675,7 @@ int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream) {
 }
 
 int l1line_topk(const float *scores, int64_t m, int64_t K, int32_t *out_idx, void *stream) {
+    L1L_RANGE("l1line_topk");
     g_last_launches = 0;
     if (!scores || !out_idx || m < 1 || K < 1 || K > m) return L1L_ERR_ARG;
     if (m > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
@@ -655,6 +691,7 @@ int l1line_fit_proposed_f32(const float *X, int64_t n, int64_t m, const double *
                             int64_t n_lambda, const l1line_mlp *mlp, int64_t K, int32_t *out_idx,
                             float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
                             size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_fit_proposed_f32");
     return proposed_impl<float>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
                                 out_jstar, workspace, workspace_bytes, stream);
 }
@@ -664,6 +701,7 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
                             int32_t *out_idx, double *out_v, double *out_obj,
                             int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                             void *stream) {
+    L1L_RANGE("l1line_fit_proposed_f64");
     return proposed_impl<double>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
                                  out_jstar, workspace, workspace_bytes, stream);
 }
@@ -683,17 +721,20 @@ size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m) {
 
 int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets,
                           void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_path_count_f32");
     return path_count_impl<float>(X, n, m, offsets, workspace, workspace_bytes, stream);
 }
 
 int l1line_path_count_f64(const double *X, int64_t n, int64_t m, int64_t *offsets,
                           void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_path_count_f64");
     return path_count_impl<double>(X, n, m, offsets, workspace, workspace_bytes, stream);
 }
 
 int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *offsets,
                           double *out_lambda, float *out_v, double *out_resid, int32_t *out_len,
                           void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_path_write_f32");
     return path_write_impl<float>(X, n, m, offsets, out_lambda, out_v, out_resid, out_len,
                                   workspace, workspace_bytes, stream);
 }
@@ -701,6 +742,7 @@ int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *o
 int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *offsets,
                           double *out_lambda, double *out_v, double *out_resid, int32_t *out_len,
                           void *workspace, size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_path_write_f64");
     return path_write_impl<double>(X, n, m, offsets, out_lambda, out_v, out_resid, out_len,
                                    workspace, workspace_bytes, stream);
 }
@@ -747,6 +789,7 @@ int l1line_solution_path_f32(int64_t m, const int64_t *offsets, const double *la
                              double *out_intercept, double *out_slope, float *out_v,
                              int64_t *out_count, int64_t cap, void *workspace,
                              size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_solution_path_f32");
     return solution_path_impl<float>(m, offsets, lambda, v, resid, len, entries, out_start,
                                      out_jhat, out_intercept, out_slope, out_v, out_count, cap,
                                      workspace, workspace_bytes, stream);
@@ -758,6 +801,7 @@ int l1line_solution_path_f64(int64_t m, const int64_t *offsets, const double *la
                              double *out_intercept, double *out_slope, double *out_v,
                              int64_t *out_count, int64_t cap, void *workspace,
                              size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_solution_path_f64");
     return solution_path_impl<double>(m, offsets, lambda, v, resid, len, entries, out_start,
                                       out_jhat, out_intercept, out_slope, out_v, out_count, cap,
                                       workspace, workspace_bytes, stream);
@@ -814,6 +858,7 @@ extern "C" {
 int l1line_components_f32(const float *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
                           float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_components_f32");
     return components_impl<float>(X, n, m, lambda, ncomp, out_v, out_obj, out_jstar, workspace,
                                   workspace_bytes, stream);
 }
@@ -821,11 +866,13 @@ int l1line_components_f32(const float *X, int64_t n, int64_t m, double lambda, i
 int l1line_components_f64(const double *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
                           double *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
+    L1L_RANGE("l1line_components_f64");
     return components_impl<double>(X, n, m, lambda, ncomp, out_v, out_obj, out_jstar, workspace,
                                    workspace_bytes, stream);
 }
 
 int l1line_status(void *workspace, void *stream) {
+    L1L_RANGE("l1line_status");
     if (!workspace) return L1L_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(st) != cudaSuccess) return L1L_ERR_CUDA;
@@ -930,6 +977,7 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
 
 int l1line_probe(int kind, const void *buf, size_t bytes, int reps, void *sink, void *stream,
                  double *bytes_read) {
+    L1L_RANGE("l1line_probe");
     g_last_launches = 0;
     if (!sink || !bytes_read || reps < 1 || (reinterpret_cast<uintptr_t>(sink) & 3) != 0)
         return L1L_ERR_ARG;
@@ -1177,6 +1225,7 @@ int l1line_fit_batched_f32(int64_t batch, const float *const *Xs, const int64_t 
                            const int64_t *lambda_offsets, float *out_v, double *out_obj,
                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                            void *stream) {
+    L1L_RANGE("l1line_fit_batched_f32");
     return fit_batched_impl<float>(batch, Xs, ns, ms, lambdas, lambda_offsets, out_v, out_obj,
                                    out_jstar, workspace, workspace_bytes, stream, 0u);
 }
@@ -1186,6 +1235,7 @@ int l1line_fit_batched_f64(int64_t batch, const double *const *Xs, const int64_t
                            const int64_t *lambda_offsets, double *out_v, double *out_obj,
                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                            void *stream) {
+    L1L_RANGE("l1line_fit_batched_f64");
     return fit_batched_impl<double>(batch, Xs, ns, ms, lambdas, lambda_offsets, out_v, out_obj,
                                     out_jstar, workspace, workspace_bytes, stream, 0u);
 }
@@ -1225,6 +1275,7 @@ int noalloc_scratch_address(void **out) {
 extern "C" int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m,
                                       const double *lambdas, int64_t n_lambda, float *out_v,
                                       double *out_obj, int32_t *out_jstar, void *stream) {
+    L1L_RANGE("l1line_fit_noalloc_f32");
     if (!X || !lambdas || !out_v || !out_obj || !out_jstar || n < 1 || m < 1 || n_lambda < 1)
         return L1L_ERR_ARG;
     const size_t need = l1line_workspace_bytes(L1L_DTYPE_F32, n, m, n_lambda);

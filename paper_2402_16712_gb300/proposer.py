@@ -149,25 +149,75 @@ def _recall(data, mlp, K):
 # ---------------------------------------------------------------------------
 # training
 # ---------------------------------------------------------------------------
+CHECKPOINT = "checkpoint.npz"
+
+
+def save_checkpoint(path, config, epoch, step, theta, m1, m2, rng_state, history, best):
+    """Training state after `epoch` epochs: parameters, Adam moments, step,
+    the permutation generator's state, the history and the best epoch so far.
+    Written to a temporary file and renamed, so a crash mid-write leaves the
+    previous checkpoint intact."""
+    tmp = f"{path}.tmp{os.getpid()}.npz"
+    np.savez(tmp, theta=np.asarray(theta, dtype=np.float32), m1=np.asarray(m1, dtype=np.float32),
+             m2=np.asarray(m2, dtype=np.float32),
+             best_theta=np.asarray(best[2] if best else theta, dtype=np.float32),
+             meta=np.array(json.dumps({
+                 "config": config, "epoch": int(epoch), "step": int(step),
+                 "rng_state": rng_state, "history": history,
+                 "best": [best[0], best[1]] if best else None})))
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path, config):
+    """The state save_checkpoint wrote, checked against this run's config
+    (a checkpoint of another run raises ValueError)."""
+    with np.load(path) as d:
+        meta = json.loads(str(d["meta"]))
+        if meta["config"] != config:
+            raise ValueError(f"checkpoint {path} was written by another run: "
+                             f"{meta['config']} != {config}")
+        best = None
+        if meta["best"] is not None:
+            best = (meta["best"][0], meta["best"][1], d["best_theta"].copy())
+        return {"epoch": meta["epoch"], "step": meta["step"], "theta": d["theta"].copy(),
+                "m1": d["m1"].copy(), "m2": d["m2"].copy(), "rng_state": meta["rng_state"],
+                "history": meta["history"], "best": best}
+
+
 def train(out_dir, n_train=None, epochs=24, batch_instances=16, lr=2e-3, seed=0, device=None,
-          log=print):
+          log=print, resume=False, n_val=None, stop_after=None):
+    """Train the proposer network; after every epoch the state goes to
+    out_dir/checkpoint.npz.  resume: continue from that checkpoint (same
+    configuration), giving the parameters an uninterrupted run gives.
+    stop_after: return after that many epochs of this call (for tests)."""
     import torch
     device = device or "cuda"
     os.makedirs(out_dir, exist_ok=True)
     s0, s1 = TRAIN_SEEDS
     if n_train is not None:
         s1 = s0 + n_train - 1
+    v0, v1 = VAL_SEEDS
+    if n_val is not None:
+        v1 = v0 + n_val - 1
+    config = {"train_seeds": [s0, s1], "val_seeds": [v0, v1], "epochs": epochs,
+              "batch_instances": batch_instances, "lr": lr, "seed": seed}
+    ckpt = os.path.join(out_dir, CHECKPOINT)
+    state = load_checkpoint(ckpt, config) if resume and os.path.exists(ckpt) else None
     t_start = time.time()
     log(f"labelling {s1 - s0 + 1} training instances with exact fits")
     tr = build_dataset(range(s0, s1 + 1), device, log)
     t_label = time.time() - t_start
-    va = build_dataset(range(VAL_SEEDS[0], VAL_SEEDS[1] + 1), device)
+    va = build_dataset(range(v0, v1 + 1), device)
     n_inst = len(tr["offs"]) - 1
     N = int(tr["offs"][-1])
     log(f"{n_inst} instances, {N} candidate rows, labelled in {t_label:.0f} s")
 
     theta = torch.from_numpy(init_theta(seed)).to(device)
     m1, m2 = torch.zeros_like(theta), torch.zeros_like(theta)
+    if state is not None:
+        theta.copy_(torch.from_numpy(state["theta"]))
+        m1.copy_(torch.from_numpy(state["m1"]))
+        m2.copy_(torch.from_numpy(state["m2"]))
     mlp = l1line.mlp_pack(theta)
     score = torch.empty(N, dtype=torch.float32, device=device)
     dscore = torch.empty(N, dtype=torch.float32, device=device)
@@ -180,9 +230,15 @@ def train(out_dir, n_train=None, epochs=24, batch_instances=16, lr=2e-3, seed=0,
     steps_per_epoch = (n_inst + batch_instances - 1) // batch_instances
     total_steps = epochs * steps_per_epoch
     history, best = [], None
-    step = 0
+    step, ep0 = 0, 0
+    if state is not None:
+        rng.bit_generator.state = state["rng_state"]
+        history, best, step, ep0 = state["history"], state["best"], state["step"], state["epoch"]
+        log(f"resuming after epoch {ep0} (step {step})")
     t_train = time.time()
-    for ep in range(epochs):
+    for ep in range(ep0, epochs):
+        if stop_after is not None and ep - ep0 >= stop_after:
+            return None
         perm = rng.permutation(n_inst)
         rows = np.concatenate([np.arange(tr["offs"][b], tr["offs"][b + 1]) for b in perm])
         eoff = np.concatenate([[0], np.cumsum(sizes[perm])]).astype(np.int64)
@@ -209,10 +265,12 @@ def train(out_dir, n_train=None, epochs=24, batch_instances=16, lr=2e-3, seed=0,
             f"{rec:.4f}")
         if best is None or rec >= best[0]:
             best = (rec, ep + 1, theta.detach().cpu().numpy().copy())
+        save_checkpoint(ckpt, config, ep + 1, step, theta.cpu().numpy(), m1.cpu().numpy(),
+                        m2.cpu().numpy(), rng.bit_generator.state, history, best)
     t_train = time.time() - t_train
     th = best[2]
     th.astype("<f4").tofile(os.path.join(out_dir, "proposer_theta.f32"))
-    info = {"train_seeds": [s0, s1], "val_seeds": list(VAL_SEEDS), "instances": n_inst,
+    info = {"train_seeds": [s0, s1], "val_seeds": [v0, v1], "instances": n_inst,
             "rows": N, "epochs": epochs, "batch_instances": batch_instances, "lr": lr,
             "temperature": TEMPERATURE, "top": TOP, "label_seconds": t_label,
             "train_seconds": t_train, "kept_epoch": best[1], "val_recall_top32": best[0],
@@ -355,6 +413,8 @@ def main(argv=None):
     t.add_argument("--instances", type=int, default=None)
     t.add_argument("--epochs", type=int, default=24)
     t.add_argument("--eval-count", type=int, default=200)
+    t.add_argument("--resume", action="store_true",
+                   help="continue from OUT/checkpoint.npz (written after every epoch)")
     e = sub.add_parser("eval")
     e.add_argument("--theta", default=THETA_PATH)
     e.add_argument("--count", type=int, default=200)
@@ -365,7 +425,7 @@ def main(argv=None):
     build.build()
     log = lambda s: print(s, flush=True)
     if a.cmd == "train":
-        info = train(a.out, n_train=a.instances, epochs=a.epochs, log=log)
+        info = train(a.out, n_train=a.instances, epochs=a.epochs, log=log, resume=a.resume)
         log(json.dumps({k: v for k, v in info.items() if k != "history"}))
         if a.eval_count:
             res = evaluate(os.path.join(a.out, "proposer_theta.f32"), count=a.eval_count, log=log)

@@ -279,3 +279,22 @@ def test_trained_network_gain_over_the_method_without_it():
     assert l1line.status(ws) == l1line.OK
     t_full, t_prop = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
     assert t_prop * 3 < t_full, (t_full, t_prop)
+
+
+def test_training_resumes_from_its_checkpoint(tmp_path):
+    """Two epochs in one run against one epoch, a stop, and a resumed run:
+    the same parameters, Adam moments and kept network, bit for bit."""
+    from paper_2402_16712_gb300 import proposer
+    kw = dict(n_train=6, epochs=2, batch_instances=4, n_val=3, log=lambda s: None)
+    full = proposer.train(str(tmp_path / "full"), **kw)
+    assert proposer.train(str(tmp_path / "split"), stop_after=1, **kw) is None
+    resumed = proposer.train(str(tmp_path / "split"), resume=True, **kw)
+    assert resumed["kept_epoch"] == full["kept_epoch"]
+    for name in ("proposer_theta.f32",):
+        assert (tmp_path / "full" / name).read_bytes() == (tmp_path / "split" / name).read_bytes()
+    with np.load(tmp_path / "full" / proposer.CHECKPOINT) as f, \
+            np.load(tmp_path / "split" / proposer.CHECKPOINT) as g:
+        for k in ("theta", "m1", "m2", "best_theta"):
+            assert np.array_equal(f[k], g[k]), k
+    assert [h["train_loss"] for h in full["history"]] == \
+        [h["train_loss"] for h in resumed["history"]]
