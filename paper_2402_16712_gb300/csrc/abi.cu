@@ -1043,7 +1043,7 @@ std::vector<int64_t> batch_classes(int64_t batch, const int64_t *ns, const int64
         const int b = byn[p];
         S[p + 1] = S[p] + (double)ns[b] * ms[b] * ms[b] * (loff[b + 1] - loff[b]);
         if (p == 0 || ns[b] != ns[byn[p - 1]]) {
-            const PairPlan pl = plan_pairs<T>(ns[b], 1, sms, 1, tb);
+            const PairPlan pl = plan_pairs<T>(ns[b], 1, sms, 1, tb, false);
             rate[p] = (double)pl.warps * (double)pl.ctas;  // 0 marks no cut here
         }
     }
@@ -1126,7 +1126,7 @@ int fit_batched_impl(int64_t batch, const T *const *Xs, const int64_t *ns, const
         int64_t mx = 0;
         for (int64_t p = p0; p < p1; ++p) mx = std::max(mx, ns[sh.order[(size_t)p]]);
         BatchClass &c = cls[nclasses++];
-        c.plan = plan_pairs<T>(mx, 1, sms, 1, tb);
+        c.plan = plan_pairs<T>(mx, 1, sms, 1, tb, false);
         if (c.plan.warps == 0) return L1L_ERR_UNSUPPORTED;
         c.lay_npad = (int)((mx + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1));
         c.u0 = p0;  // instance range for now; converted to units below

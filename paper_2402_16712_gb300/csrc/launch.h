@@ -53,7 +53,10 @@ struct Tune {
 };
 // nj: number of jhat scored (m for a full scan).
 template <typename T>
-PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune = Tune());
+// single: a single-instance call (false for the batched call's size classes,
+// whose persistent CTAs take whole columns).
+PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune = Tune(),
+                    bool single = true);
 template <typename T> int64_t max_rows_pairs();
 
 // One launch of the pair kernel for lambdas[t0 .. t0+nlc) (nlc <= MAX_LAMBDA_PER_LAUNCH).
