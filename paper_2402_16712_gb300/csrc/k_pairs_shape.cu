@@ -6,6 +6,30 @@
 // and -DL1L_PERSIST=0 (the single-instance kernel, grid over jhat x k-chunks)
 // or 1 (the batched persistent kernel).  The build compiles this file once
 // per (shape, kind), so the instantiations compile in parallel.
+#ifndef L1L_SHAPE
+#error "compile with -DL1L_SHAPE=0|1|2"
+#endif
+// Loop unrolling of the 32-bit selection per shape (select32.cuh); measured
+// on the planner's launches, kernel time: 2000 x 2000 (64 registers)
+// level-0 loop unrolled by two 14.18 -> 13.51 ms, 1000 x 500 0.70 -> 0.67 ms;
+// 5000 x 1000 (128 registers) level-0 unroll 11.00 -> 11.46 ms (kept at one),
+// list loops unrolled by two 11.00 -> 10.88 ms.
+#if L1L_SHAPE == 2
+#ifndef L1L_L0_UNROLL
+#define L1L_L0_UNROLL 1
+#endif
+#ifndef L1L_LIST_UNROLL
+#define L1L_LIST_UNROLL 2
+#endif
+#else
+#ifndef L1L_L0_UNROLL
+#define L1L_L0_UNROLL 2
+#endif
+#ifndef L1L_LIST_UNROLL
+#define L1L_LIST_UNROLL 1
+#endif
+#endif
+
 #include <algorithm>
 
 #include "batch.cuh"
@@ -14,9 +38,6 @@
 #include "launch.h"
 #include "pairs.cuh"
 
-#ifndef L1L_SHAPE
-#error "compile with -DL1L_SHAPE=0|1|2"
-#endif
 #ifndef L1L_PERSIST
 #error "compile with -DL1L_PERSIST=0|1"
 #endif

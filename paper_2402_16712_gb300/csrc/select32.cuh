@@ -24,6 +24,19 @@
 #include "checks.cuh"
 #include "common.cuh"
 
+// Unroll factors of the level-0 row loop and of the candidate-list loops,
+// set per launch shape by the file that instantiates the kernels (measured:
+// unrolling the level-0 loop by two helps the 64- and 80-register shapes and
+// hurts the 128-register one, unrolling the list loops the reverse).
+#ifndef L1L_L0_UNROLL
+#define L1L_L0_UNROLL 1
+#endif
+#ifndef L1L_LIST_UNROLL
+#define L1L_LIST_UNROLL 1
+#endif
+#define L1L_PRAGMA(x) _Pragma(#x)
+#define L1L_UNROLL(n) L1L_PRAGMA(unroll n)
+
 namespace l1l {
 
 // Candidate entry: x = float bits of the approximate ratio, or (KEYED) its
@@ -255,7 +268,7 @@ __device__ __forceinline__ int list32_keep(uint2 *__restrict__ lst, int cnt, uin
     const int cmax = __reduce_max_sync(0xFFFFFFFFu, (unsigned)cnt);
     const uint32_t base = smem_addr(lst) + 8u * (uint32_t)lane;
     int w = 0;
-#pragma unroll 1
+    L1L_UNROLL(L1L_LIST_UNROLL)
     for (int j = 0; j < cmax; ++j) {
         const bool act = j < cnt;
         const uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];
@@ -346,6 +359,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
         const float4 *xp = xk4 + lane;
         uint32_t ainv = ainv0, aq = aq0, i0 = 4u * (uint32_t)lane;
         float4 xn = __ldg(xp);
+        L1L_UNROLL(L1L_L0_UNROLL)
         for (int g = 0; g < ng; ++g) {
             const float4 xc = xn;
             xp += 32;
@@ -387,7 +401,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
             const int cmax = __reduce_max_sync(FULL, (unsigned)cnt);
             const uint32_t ebase = smem_addr(lst) + 8u * (uint32_t)lane;
             const int nb1 = bm.nneg + bm.npos - 1, nneg1 = bm.nneg - 1, npos1 = bm.npos - 1;
-#pragma unroll 1
+            L1L_UNROLL(L1L_LIST_UNROLL)
             for (int j = 0; j < cmax; ++j) {
                 const bool act = j < cnt;
                 const uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];  // fresh: (ratio bits, row)
