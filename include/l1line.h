@@ -408,11 +408,10 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
  *    Serialise them (one stream, or events).  Each call resets the parts of
  *    the scratch that must start at zero and overwrites the rest.
  *  - Its return value carries only the host-side codes (L1L_ERR_ARG,
- *    L1L_ERR_UNSUPPORTED, L1L_ERR_CUDA, L1L_OK).  The device-side status of
- *    l1line_fit_f32 (read by l1line_status) stays in the scratch, which is
- *    not exposed, so L1L_ERR_NONFINITE is never reported: a NaN or infinity
- *    in X returns L1L_OK with meaningless results.  Check X first where that
- *    can happen.
+ *    L1L_ERR_UNSUPPORTED, L1L_ERR_CUDA, L1L_OK): the call does not wait for
+ *    its kernels.  The device-side status of the fit (a NaN or infinity in X,
+ *    an internal error) stays in the scratch until the next call on that
+ *    device; l1line_noalloc_status reads it.
  * X, out_v, out_obj and out_jstar are device pointers as for l1line_fit_f32;
  * lambdas is a host pointer.  Nothing is allocated or freed.
  */
@@ -420,6 +419,12 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
 int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                            int64_t n_lambda, float *out_v, double *out_obj,
                            int32_t *out_jstar, void *stream);
+
+/* Synchronise `stream` and return the device-side status that the last
+ * l1line_fit_noalloc_f32 call on the current device left in its scratch, with
+ * the codes of l1line_status (L1L_OK before any call); L1L_ERR_CUDA if the
+ * synchronisation or the read fails.  Allocates nothing. */
+int l1line_noalloc_status(void *stream);
 
 /* Synchronise `stream` and return the device-side status recorded in the
  * workspace by the last call that used it (L1L_OK, L1L_ERR_NONFINITE,

@@ -44,6 +44,10 @@ thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
 
 size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// The status word at the start of a workspace, decoded (the stream is
+// synchronised first).
+int status_of(void *workspace, void *stream);
+
 bool mul_ok(int64_t a, int64_t b, int64_t &out) {
     if (a < 0 || b < 0) return false;
     if (a != 0 && b > INT64_MAX / a) return false;
@@ -873,6 +877,13 @@ int l1line_components_f64(const double *X, int64_t n, int64_t m, double lambda, 
 
 int l1line_status(void *workspace, void *stream) {
     L1L_RANGE("l1line_status");
+    return status_of(workspace, stream);
+}
+
+}  // extern "C"
+
+namespace {
+int status_of(void *workspace, void *stream) {
     if (!workspace) return L1L_ERR_WORKSPACE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(st) != cudaSuccess) return L1L_ERR_CUDA;
@@ -885,6 +896,9 @@ int l1line_status(void *workspace, void *stream) {
     if (w & ST_BADINDEX) return L1L_ERR_ARG;
     return L1L_OK;
 }
+}  // namespace
+
+extern "C" {
 
 const char *l1line_status_string(int status) {
     switch (status) {
@@ -1271,6 +1285,14 @@ int noalloc_scratch_address(void **out) {
 }
 
 }  // namespace
+
+extern "C" int l1line_noalloc_status(void *stream) {
+    L1L_RANGE("l1line_noalloc_status");
+    void *ws = nullptr;
+    const int rc = noalloc_scratch_address(&ws);
+    if (rc != L1L_OK) return rc;
+    return status_of(ws, stream);
+}
 
 extern "C" int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m,
                                       const double *lambdas, int64_t n_lambda, float *out_v,

@@ -42,6 +42,7 @@ SIGNATURES = {
     "l1line_path_max_rows": (_I64, [_I]),
     "l1line_probe": (_I, [_I, _P, _SZ, _I, _P, _P, _P]),
     "l1line_fit_noalloc_f32": (_I, [_P, _I64, _I64, _P, _I64, _P, _P, _P, _P]),
+    "l1line_noalloc_status": (_I, [_P]),
     "l1line_batched_workspace_bytes": (_SZ, [_I, _I64, _P, _P, _P]),
     "l1line_fit_batched_f32": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     "l1line_fit_batched_f64": (_I, [_I64, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ, _P]),

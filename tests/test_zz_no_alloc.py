@@ -55,6 +55,25 @@ def test_noalloc_fit_matches_fit_twice_in_a_row():
         assert np.all(np.abs(obj - robj) <= 1e-5 * np.abs(robj))
 
 
+@pytest.mark.gpu
+def test_noalloc_status_reports_a_nonfinite_input():
+    """The call returns before its kernels run; l1line_noalloc_status reads the
+    device-side status the fit left in the scratch: NaN in X is reported,
+    and the next clean call clears it."""
+    import torch
+    __graft_entry__.build()
+    lib = l1line.load()
+    lams = np.array([0.2], dtype=np.float64)
+    X, _, _ = datagen.planted(datagen.Planted(200, 12, 3, 0.1, 0.1, 5.0, 9, "float32"))
+    bad = X.copy()
+    bad[17, 5] = np.nan
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    _call_noalloc(lib, torch.from_numpy(bad).cuda(), lams, 0)
+    assert lib.l1line_noalloc_status(stream) == l1line.ERR_NONFINITE
+    _call_noalloc(lib, torch.from_numpy(X).cuda(), lams, 0)
+    assert lib.l1line_noalloc_status(stream) == l1line.OK
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     __graft_entry__.build()
     lib = l1line.load()
