@@ -139,22 +139,7 @@ static PairPlan plan_placement(int64_t npad, bool cs, int d0, const Tune &tune) 
 }
 
 template <typename T>
-PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune_in,
-                    bool single) {
-    // A single-instance call whose pairs fit in one wave at 16 warps per SM
-    // is bound by the latency of one pair, not by throughput: one CTA per SM
-    // at 128 registers, 8-16 warps per CTA (fewer CTAs stage column jhat
-    // fewer times) spreading the pairs over the SMs.  Small 200 x 20 double
-    // fit, CUDA graph: 16 x 2 warps 36.4 us, 3 x 1 34.4 us, 8 x 3 (the
-    // earlier 80-register plan) 32.7 us.
-    Tune tune = tune_in;
-    if (single && tune.warps == 0 && tune.ctas == 0 && nj > 0 &&
-        nj * m <= (int64_t)num_sms * 16) {
-        const int64_t per_col = std::max<int64_t>(1, num_sms / nj);  // CTAs per column jhat
-        const int64_t w = std::max<int64_t>(std::min<int64_t>(m, 8), (m + per_col - 1) / per_col);
-        tune.warps = (int)std::min<int64_t>(16, std::max<int64_t>(1, w));
-        tune.ctas = 1;
-    }
+static PairPlan plan_pairs_for(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune) {
     PairPlan p{0, 0, 0, 0, 0, 0, 0, 0, 0};
     const int64_t npad = (n + ROW_PAD - 1) & ~int64_t(ROW_PAD - 1);
     if (n > max_rows_pairs<T>()) return p;
@@ -203,6 +188,27 @@ PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &t
     p.kchunk = (int)((m + chunks - 1) / chunks);
     p.kchunks = (int)((m + p.kchunk - 1) / p.kchunk);
     return p;
+}
+
+template <typename T>
+PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune, bool single) {
+    // A single-instance call whose pairs fit in one wave at 16 warps per SM
+    // is bound by the latency of one pair, not by throughput: one CTA per SM
+    // at 128 registers, 8-16 warps per CTA (fewer CTAs stage column jhat
+    // fewer times) spreading the pairs over the SMs; the throughput plan when
+    // that many warps' lists do not fit.  Small 200 x 20 double fit, CUDA
+    // graph: 16 x 2 warps 36.4 us, 3 x 1 and 8 x 1 34.4 us.
+    if (single && tune.warps == 0 && tune.ctas == 0 && nj > 0 &&
+        nj * m <= (int64_t)num_sms * 16) {
+        const int64_t per_col = std::max<int64_t>(1, num_sms / nj);  // CTAs per column jhat
+        const int64_t w = std::max<int64_t>(std::min<int64_t>(m, 8), (m + per_col - 1) / per_col);
+        Tune lt = tune;
+        lt.warps = (int)std::min<int64_t>(16, std::max<int64_t>(1, w));
+        lt.ctas = 1;
+        const PairPlan p = plan_pairs_for<T>(n, m, num_sms, nj, lt);
+        if (p.warps > 0) return p;
+    }
+    return plan_pairs_for<T>(n, m, num_sms, nj, tune);
 }
 
 template <typename T>

@@ -223,6 +223,101 @@ __device__ __forceinline__ float4 ldg_f4(const float *p) {
     return __ldg(reinterpret_cast<const float4 *>(p));
 }
 
+// One slot of the candidate histogram's pass A (select_w32, float input:
+// guard band G = 8 keys), zero-crossing bin layout (BinMapA, cross: bins of
+// 2^21 keys): entry (ratio bits, row) at eaddr; act: the slot holds a
+// candidate of this lane.  A candidate whose approximate key lies G inside
+// [g1 - G, g2 + G] and G inside its bin's edges adds its weight q32[row] to
+// its bin; any other candidate is flagged pending.  pend |= 1 for a pending
+// candidate.  Branch-free, about 30 instructions.
+__device__ __forceinline__ void passa_slot_cross(uint32_t eaddr, int act, uint32_t g1, uint32_t g2,
+                                                 int tp1, int tp2, int nneg1, int npos1, int nb1,
+                                                 uint32_t aq, uint32_t ahist, int &pend) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred pa, pc, pj, pn;\n\t"
+        ".reg .b32 ex, ey, s, kk, a, b, t, dn, dp, bn, q, qa, ha, ey2, row;\n\t"
+        "setp.ne.b32 pa, %1, 0;\n\t"
+        "ld.shared.v2.u32 {ex, ey}, [%2];\n\t"
+        "shr.s32 s, ex, 31;\n\t"
+        "or.b32 s, s, 0x80000000;\n\t"
+        "xor.b32 kk, ex, s;\n\t"
+        "setp.ge.and.u32 pc, kk, %3, pa;\n\t"
+        "setp.le.and.u32 pc, kk, %4, pc;\n\t"
+        "sub.u32 a, kk, 8;\n\t"
+        "add.u32 b, kk, 8;\n\t"
+        "shr.u32 a, a, 21;\n\t"
+        "shr.u32 b, b, 21;\n\t"
+        "setp.eq.and.u32 pc, a, b, pc;\n\t"
+        "shr.u32 t, kk, 21;\n\t"
+        "sub.s32 dn, t, %5;\n\t"
+        "min.s32 dn, dn, %7;\n\t"
+        "sub.s32 dp, %6, t;\n\t"
+        "min.s32 dp, dp, %8;\n\t"
+        "sub.s32 bn, %9, dp;\n\t"
+        "setp.lt.u32 pn, kk, 0x80000000;\n\t"
+        "selp.b32 bn, dn, bn, pn;\n\t"
+        "selp.b32 row, ey, 0, pa;\n\t"
+        "shl.b32 qa, row, 2;\n\t"
+        "add.u32 qa, qa, %10;\n\t"
+        "ld.shared.u32 q, [qa];\n\t"
+        "shl.b32 ha, bn, 2;\n\t"
+        "add.u32 ha, ha, %11;\n\t"
+        "@pc red.shared.add.u32 [ha], q;\n\t"
+        "not.pred pj, pc;\n\t"
+        "and.pred pj, pj, pa;\n\t"
+        "or.b32 ey2, ey, 0x20000000;\n\t"
+        "@pj st.shared.u32 [%2+4], ey2;\n\t"
+        "selp.b32 s, 1, 0, pj;\n\t"
+        "or.b32 %0, %0, s;\n\t"
+        "}"
+        : "+r"(pend)
+        : "r"(act), "r"(eaddr), "r"(g1), "r"(g2), "r"(tp1), "r"(tp2), "r"(nneg1), "r"(npos1),
+          "r"(nb1), "r"(aq), "r"(ahist)
+        : "memory");
+}
+
+// The same for the uniform layout: bin (kk - base) >> sh.
+__device__ __forceinline__ void passa_slot_unif(uint32_t eaddr, int act, uint32_t g1, uint32_t g2,
+                                                uint32_t base, uint32_t sh, uint32_t aq,
+                                                uint32_t ahist, int &pend) {
+    asm volatile(
+        "{\n\t"
+        ".reg .pred pa, pc, pj;\n\t"
+        ".reg .b32 ex, ey, s, kk, a, b, d, q, qa, ha, ey2, row;\n\t"
+        "setp.ne.b32 pa, %1, 0;\n\t"
+        "ld.shared.v2.u32 {ex, ey}, [%2];\n\t"
+        "shr.s32 s, ex, 31;\n\t"
+        "or.b32 s, s, 0x80000000;\n\t"
+        "xor.b32 kk, ex, s;\n\t"
+        "setp.ge.and.u32 pc, kk, %3, pa;\n\t"
+        "setp.le.and.u32 pc, kk, %4, pc;\n\t"
+        "sub.u32 d, kk, %5;\n\t"
+        "sub.u32 a, d, 8;\n\t"
+        "add.u32 b, d, 8;\n\t"
+        "shr.u32 a, a, %6;\n\t"
+        "shr.u32 b, b, %6;\n\t"
+        "setp.eq.and.u32 pc, a, b, pc;\n\t"
+        "shr.u32 d, d, %6;\n\t"
+        "selp.b32 row, ey, 0, pa;\n\t"
+        "shl.b32 qa, row, 2;\n\t"
+        "add.u32 qa, qa, %7;\n\t"
+        "ld.shared.u32 q, [qa];\n\t"
+        "shl.b32 ha, d, 2;\n\t"
+        "add.u32 ha, ha, %8;\n\t"
+        "@pc red.shared.add.u32 [ha], q;\n\t"
+        "not.pred pj, pc;\n\t"
+        "and.pred pj, pj, pa;\n\t"
+        "or.b32 ey2, ey, 0x20000000;\n\t"
+        "@pj st.shared.u32 [%2+4], ey2;\n\t"
+        "selp.b32 s, 1, 0, pj;\n\t"
+        "or.b32 %0, %0, s;\n\t"
+        "}"
+        : "+r"(pend)
+        : "r"(act), "r"(eaddr), "r"(g1), "r"(g2), "r"(base), "r"(sh), "r"(aq), "r"(ahist)
+        : "memory");
+}
+
 // First bin of [base, top] (bins of 2^sh keys) whose upper key passes the
 // exact test with S = Sbase + weight of bins <= b, over 32-bit bins.
 // Returns the bin (-1: none passes, -2: undecidable) and the weight below it.
@@ -400,6 +495,8 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
             // lane's own count are read but not used, their row clamped to 0)
             const int cmax = __reduce_max_sync(FULL, (unsigned)cnt);
             const uint32_t ebase = smem_addr(lst) + 8u * (uint32_t)lane;
+#if L1L_CHECKS
+            // the bounds-checked build keeps the loop in C++, where every index is checked
             const int nb1 = bm.nneg + bm.npos - 1, nneg1 = bm.nneg - 1, npos1 = bm.npos - 1;
             L1L_UNROLL(L1L_LIST_UNROLL)
             for (int j = 0; j < cmax; ++j) {
@@ -419,6 +516,25 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
                 st_shared_u32_if(pj, ebase + 256u * (uint32_t)j + 4u, e.y | E32_PEND);
                 pend |= pj;
             }
+#else
+            // one predicated PTX block per slot (measured 2.8% faster than the same loop in C++)
+            static_assert(G == 8 && BinMapA::QSH == 21, "the PTX blocks hold G = 8 and 2^21-key bins");
+            const uint32_t aq = smem_addr(q32);
+            int pendi = 0;
+            if (bm.cross) {
+                const int nb1 = bm.nneg + bm.npos - 1, nneg1 = bm.nneg - 1, npos1 = bm.npos - 1;
+                L1L_UNROLL(L1L_LIST_UNROLL)
+                for (int j = 0; j < cmax; ++j)
+                    passa_slot_cross(ebase + 256u * (uint32_t)j, j < cnt, g1, g2, bm.tp1, bm.tp2,
+                                     nneg1, npos1, nb1, aq, ahist, pendi);
+            } else {
+                L1L_UNROLL(L1L_LIST_UNROLL)
+                for (int j = 0; j < cmax; ++j)
+                    passa_slot_unif(ebase + 256u * (uint32_t)j, j < cnt, g1, g2, bm.base,
+                                    (uint32_t)bm.sh, aq, ahist, pendi);
+            }
+            pend = pendi != 0;
+#endif
         }
         uint32_t Sb2 = 0;
         if (__any_sync(FULL, pend)) {
