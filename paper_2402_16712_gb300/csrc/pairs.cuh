@@ -81,29 +81,27 @@ constexpr int HIST_WORDS = 4 * 64;  // per-warp exact histogram (4 chunks x 64 b
 template <typename T> struct PairSmem {
     // per CTA: x_ijhat (T; only when `cs`, else it is read from the column
     // copy in global memory), 1/x_ijhat (float, NaN marks x_ijhat == 0), the
-    // weights (double input: 64-bit q_i; float input: 32-bit q32_i), the 64
-    // sample rows (uint16)
+    // 32-bit weights q32_i, the 64 sample rows (uint16)
     __host__ __device__ static size_t col_bytes(int64_t npad, bool cs) {
-        return (cs ? al16(npad * sizeof(T)) : 0) + al16(npad * 4) +
-               al16(npad * (sizeof(T) == 4 ? 4 : 8)) + al16(NSAMP * 2);
+        return (cs ? al16(npad * sizeof(T)) : 0) + al16(npad * 4) + al16(npad * 4) +
+               al16(NSAMP * 2);
     }
     // per warp, 64-bit selection: candidate keys (uint32), row indices
     // (uint16; bit 15 = exact key) and the histogram (4 x 64 uint32)
     __host__ __device__ static size_t bytes64(int64_t cap) {
         return al16(cap * 4) + al16(cap * 2) + al16(HIST_WORDS * 4);
     }
-    // per warp, 32-bit selection (float input): 8-byte entries and a 64-word
-    // histogram, overlaid by the arrays of its 64-bit fallback
+    // per warp, 32-bit selection: 8-byte entries and a 64-word histogram,
+    // overlaid by the arrays of its 64-bit fallback
     __host__ __device__ static size_t bytes32(int64_t cap) { return al16(cap * 8) + al16(64 * 4); }
     __host__ __device__ static size_t warp_bytes(int64_t cap) {
-        if (sizeof(T) == 8) return bytes64(cap);
         const size_t a = bytes32(cap), b = bytes64(cap);
         return a > b ? a : b;
     }
     // the largest capacity (a multiple of 32) whose per-warp region fits `bytes`
     __host__ __device__ static int64_t cap_fit(int64_t bytes) {
         const int64_t c64 = (bytes - HIST_WORDS * 4 - 32) / 6;
-        const int64_t c32 = sizeof(T) == 8 ? c64 : (bytes - 64 * 4 - 16) / 8;
+        const int64_t c32 = (bytes - 64 * 4 - 16) / 8;
         int64_t c = (c64 < c32 ? c64 : c32) & ~int64_t(31);
         while (c > 0 && warp_bytes(c) > (size_t)bytes) c -= 32;
         return c;
@@ -333,14 +331,9 @@ __device__ __forceinline__ int hist_cross_map(const uint32_t *h, const BinMap &b
     return bsel;
 }
 
-// Sources of the 64-bit fixed-point weight q_i of row i.  WqSmem: the staged
-// array (double input).  WqFly: computed from x_ijhat on the spot (float
-// input, whose fast path stages 32-bit weights; the 64-bit selection is its
-// rare fallback).
-struct WqSmem {
-    const int64_t *__restrict__ q;
-    __device__ __forceinline__ int64_t operator()(int i) const { return q[i]; }
-};
+// The 64-bit fixed-point weight q_i of row i for the 64-bit selection,
+// computed from x_ijhat on the spot (the fast path stages 32-bit weights;
+// the 64-bit selection is its rare fallback).
 template <typename T> struct WqFly {
     const T *colb;
     int sigma;
@@ -753,39 +746,30 @@ struct LamView {
 };
 
 // Everything one warp needs to solve the pairs of its CTA's column jhat.
-// The fast path's weights are colq (double input, 64-bit) or q32 (float
-// input, 32-bit); s_dec and decide_for use the same scale.
+// The fast path's weights are the 32-bit q32 (both input types); s_dec and
+// decide_for use the same scale.
 template <typename T> struct WarpCtx {
     const T *colb;
     const float *inv;
-    const int64_t *colq;   // double input
-    const uint32_t *q32;   // float input
+    const uint32_t *q32;
     const uint16_t *samp;
-    uint32_t *lk;          // 64-bit selection's lists and histogram
+    uint32_t *lk;          // 64-bit fallback's lists and histogram
     uint16_t *li;
     uint32_t *hist;
-    uint2 *lst;            // 32-bit selection's list and histogram (float input)
+    uint2 *lst;            // 32-bit selection's list and histogram
     uint32_t *hist32;
     const Decide *s_dec;  // per-lambda thresholds for the first NDEC lambdas
     int qt, n;
     int d0;               // first-bracket half-width in sample positions
     ColInfo cinfo;
-    __device__ __forceinline__ int64_t q(int i) const {
-        if constexpr (sizeof(T) == 4)
-            return (int64_t)q32[i];
-        else
-            return colq[i];
-    }
+    __device__ __forceinline__ int64_t q(int i) const { return (int64_t)q32[i]; }
 };
 constexpr int NDEC = 32;
 
-// The exact test of lambda tl on the fast path's weight scale.
+// The exact test of lambda tl on the fast path's weight scale (q32).
 template <typename T>
 __device__ __forceinline__ void decide_init(Decide &dc, const ColInfo &ci, double lam) {
-    if constexpr (sizeof(T) == 4)
-        dc.init32(ci, lam);
-    else
-        dc.init(ci, lam);
+    dc.init32(ci, lam);
 }
 template <typename T>
 __device__ __forceinline__ Decide decide_for(const WarpCtx<T> &w, const LamView &lp, int tl) {
@@ -797,51 +781,47 @@ __device__ __forceinline__ Decide decide_for(const WarpCtx<T> &w, const LamView 
     return dc;
 }
 
-// The 64-bit selection of a float pair that the 32-bit weights could not
-// settle (rare): a separate, not inlined function, so that its code stays out
-// of the hot loop's instruction stream.
+// The 64-bit selection of a pair that the 32-bit weights could not settle
+// (rare): a separate, not inlined function, so that its code stays out of the
+// hot loop's instruction stream.  Weights are computed from x_ijhat.
 template <typename T>
 __device__ __noinline__ int select_fallback64(const T *xk, const float *xf, const T *colb,
                                               const float *inv, const uint16_t *samp,
                                               uint32_t *lk, uint16_t *li, uint32_t *hist,
                                               int qt, int n, int d0, int64_t Q, int sigma,
-                                              int inexact, double lam, uint32_t *ts, int lane) {
+                                              int inexact, double lam,
+                                              typename Traits<T>::K *ts, int lane) {
     Decide d64;
     d64.init_at(Q, sigma, inexact, lam);
     typename Traits<T>::K k = 0;
     const int st = select_v2<T>(xk, xf, colb, inv, WqFly<T>{colb, sigma}, samp, lk, li, hist, qt,
                                 n, d0, d64, k, lane);
-    *ts = (uint32_t)k;
+    *ts = k;
     return st;
 }
 
-// The full selection of one (lambda, pair): float input tries 32-bit weights
-// and repeats the pair on 64-bit weights (computed from x_ijhat) when those
-// cannot settle it; double input selects on its staged 64-bit weights.
+// The full selection of one (lambda, pair): the 32-bit weights first, and the
+// pair again on 64-bit weights (computed from x_ijhat) when those cannot
+// settle it.
 template <typename T>
 __device__ __forceinline__ int select_pair(const T *xk, const float *xf, const WarpCtx<T> &w,
                                            const LamView &lp, int tl,
                                            typename Traits<T>::K &ts, int lane) {
     const Decide dc = decide_for(w, lp, tl);
-    if constexpr (sizeof(T) == 4) {
-        uint32_t t32 = 0;
-        const int st = select_w32(xk, w.colb, w.inv, w.q32, w.samp, w.lst, w.hist32, w.qt, w.n,
-                                  w.d0, dc, t32, lane);
-        if (st != SEL_W64) {
-            ts = t32;
-            return st;
-        }
-        __syncwarp();
-        uint32_t t64 = 0;
-        const int st64 = select_fallback64<T>(xk, xf, w.colb, w.inv, w.samp, w.lk, w.li, w.hist,
-                                              w.qt, w.n, w.d0, w.cinfo.Q, w.cinfo.sigma,
-                                              w.cinfo.n_inexact, lp.lam[tl], &t64, lane);
-        ts = t64;
-        return st64;
-    } else {
-        return select_v2<T>(xk, xf, w.colb, w.inv, WqSmem{w.colq}, w.samp, w.lk, w.li, w.hist,
-                            w.qt, w.n, w.d0, dc, ts, lane);
+    typename Traits<T>::K t32 = 0;
+    const int st = select_w32<T>(xf, xk, w.colb, w.inv, w.q32, w.samp, w.lst, w.hist32, w.qt,
+                                 w.n, w.d0, dc, t32, lane);
+    if (st != SEL_W64) {
+        ts = t32;
+        return st;
     }
+    __syncwarp();
+    typename Traits<T>::K t64 = 0;
+    const int st64 = select_fallback64<T>(xk, xf, w.colb, w.inv, w.samp, w.lk, w.li, w.hist, w.qt,
+                                          w.n, w.d0, w.cinfo.Q, w.cinfo.sigma, w.cinfo.n_inexact,
+                                          lp.lam[tl], &t64, lane);
+    ts = t64;
+    return st64;
 }
 
 // Residual of one pair (CS: x_ijhat staged in shared memory).
@@ -1050,10 +1030,9 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     size_t off = CS ? al16((size_t)npad * sizeof(T)) : 0;
     float *inv = reinterpret_cast<float *>(smem + off);
     off += al16((size_t)npad * 4);
-    // fast-path weights: 64-bit q_i (double input) or 32-bit q32_i (float input)
-    int64_t *colq = reinterpret_cast<int64_t *>(smem + off);
+    // fast-path weights: 32-bit q32_i
     uint32_t *q32 = reinterpret_cast<uint32_t *>(smem + off);
-    off += al16((size_t)npad * (sizeof(T) == 4 ? 4 : 8));
+    off += al16((size_t)npad * 4);
     uint16_t *samp = reinterpret_cast<uint16_t *>(smem + off);
     unsigned char *wbase =
         smem + PairSmem<T>::col_bytes(npad, CS) + (size_t)warp * PairSmem<T>::warp_bytes(cap);
@@ -1078,10 +1057,7 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         inv[i] = b != T(0) ? Approx<T>::inv_of(b) : __int_as_float(0x7FFFFFFF);
         int e = 0;
         const int64_t qi = b != T(0) ? fixq(b < T(0) ? -b : b, cinfo.sigma, e) : 0;
-        if constexpr (sizeof(T) == 4)
-            q32[i] = (uint32_t)((uint64_t)qi >> cinfo.shift32);
-        else
-            colq[i] = qi;
+        q32[i] = (uint32_t)((uint64_t)qi >> cinfo.shift32);
     }
     for (int q = threadIdx.x; q < NSAMP; q += blockDim.x) samp[q] = 0;  // always a valid row
     __syncthreads();
@@ -1091,12 +1067,7 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         const int nt = blockDim.x;
         const int chunk = (n + nt - 1) / nt;
         const int r0 = min(n, threadIdx.x * chunk), r1 = min(n, r0 + chunk);
-        auto wq = [&](int r) -> long long {
-            if constexpr (sizeof(T) == 4)
-                return (long long)q32[r];
-            else
-                return colq[r];
-        };
+        auto wq = [&](int r) -> long long { return (long long)q32[r]; };
         long long mine = 0;
         for (int r = r0; r < r1; ++r) mine += wq(r);
         long long incl = warp_scan_add(mine, lane);
@@ -1104,8 +1075,7 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
         __syncthreads();
         long long before = incl - mine;
         for (int w = 0; w < warp; ++w) before += s_wsum[w];
-        const double per =
-            (double)NSAMP / (double)(sizeof(T) == 4 ? (long long)cinfo.Q32 : cinfo.Q);
+        const double per = (double)NSAMP / (double)cinfo.Q32;
         for (int r = r0; r < r1; ++r) {
             const long long after = before + wq(r);
             const double x0 = (double)before * per - 0.5, x1 = (double)after * per - 0.5;
@@ -1124,7 +1094,6 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     WarpCtx<T> wc;
     wc.colb = colb;
     wc.inv = inv;
-    wc.colq = colq;
     wc.q32 = q32;
     wc.samp = samp;
     wc.lk = lk;

@@ -223,13 +223,14 @@ __device__ __forceinline__ float4 ldg_f4(const float *p) {
     return __ldg(reinterpret_cast<const float4 *>(p));
 }
 
-// One slot of the candidate histogram's pass A (select_w32, float input:
-// guard band G = 8 keys), zero-crossing bin layout (BinMapA, cross: bins of
-// 2^21 keys): entry (ratio bits, row) at eaddr; act: the slot holds a
+// One slot of the candidate histogram's pass A (select_w32; G: the guard
+// band in keys), zero-crossing bin layout (BinMapA, cross: bins of 2^21
+// keys): entry (ratio bits, row) at eaddr; act: the slot holds a
 // candidate of this lane.  A candidate whose approximate key lies G inside
 // [g1 - G, g2 + G] and G inside its bin's edges adds its weight q32[row] to
 // its bin; any other candidate is flagged pending.  pend |= 1 for a pending
 // candidate.  Branch-free, about 30 instructions.
+template <uint32_t G>
 __device__ __forceinline__ void passa_slot_cross(uint32_t eaddr, int act, uint32_t g1, uint32_t g2,
                                                  int tp1, int tp2, int nneg1, int npos1, int nb1,
                                                  uint32_t aq, uint32_t ahist, int &pend) {
@@ -244,8 +245,8 @@ __device__ __forceinline__ void passa_slot_cross(uint32_t eaddr, int act, uint32
         "xor.b32 kk, ex, s;\n\t"
         "setp.ge.and.u32 pc, kk, %3, pa;\n\t"
         "setp.le.and.u32 pc, kk, %4, pc;\n\t"
-        "sub.u32 a, kk, 8;\n\t"
-        "add.u32 b, kk, 8;\n\t"
+        "sub.u32 a, kk, %12;\n\t"
+        "add.u32 b, kk, %12;\n\t"
         "shr.u32 a, a, 21;\n\t"
         "shr.u32 b, b, 21;\n\t"
         "setp.eq.and.u32 pc, a, b, pc;\n\t"
@@ -273,11 +274,12 @@ __device__ __forceinline__ void passa_slot_cross(uint32_t eaddr, int act, uint32
         "}"
         : "+r"(pend)
         : "r"(act), "r"(eaddr), "r"(g1), "r"(g2), "r"(tp1), "r"(tp2), "r"(nneg1), "r"(npos1),
-          "r"(nb1), "r"(aq), "r"(ahist)
+          "r"(nb1), "r"(aq), "r"(ahist), "n"(G)
         : "memory");
 }
 
 // The same for the uniform layout: bin (kk - base) >> sh.
+template <uint32_t G>
 __device__ __forceinline__ void passa_slot_unif(uint32_t eaddr, int act, uint32_t g1, uint32_t g2,
                                                 uint32_t base, uint32_t sh, uint32_t aq,
                                                 uint32_t ahist, int &pend) {
@@ -293,8 +295,8 @@ __device__ __forceinline__ void passa_slot_unif(uint32_t eaddr, int act, uint32_
         "setp.ge.and.u32 pc, kk, %3, pa;\n\t"
         "setp.le.and.u32 pc, kk, %4, pc;\n\t"
         "sub.u32 d, kk, %5;\n\t"
-        "sub.u32 a, d, 8;\n\t"
-        "add.u32 b, d, 8;\n\t"
+        "sub.u32 a, d, %9;\n\t"
+        "add.u32 b, d, %9;\n\t"
         "shr.u32 a, a, %6;\n\t"
         "shr.u32 b, b, %6;\n\t"
         "setp.eq.and.u32 pc, a, b, pc;\n\t"
@@ -314,7 +316,8 @@ __device__ __forceinline__ void passa_slot_unif(uint32_t eaddr, int act, uint32_
         "or.b32 %0, %0, s;\n\t"
         "}"
         : "+r"(pend)
-        : "r"(act), "r"(eaddr), "r"(g1), "r"(g2), "r"(base), "r"(sh), "r"(aq), "r"(ahist)
+        : "r"(act), "r"(eaddr), "r"(g1), "r"(g2), "r"(base), "r"(sh), "r"(aq), "r"(ahist),
+          "n"(G)
         : "memory");
 }
 
@@ -375,20 +378,33 @@ __device__ __forceinline__ int list32_keep(uint2 *__restrict__ lst, int cnt, uin
     return w;
 }
 
-// Weighted median of pair (jhat, k), float input.  xk: column k (global, rows
-// padded to a multiple of 128 with zeros); colb: x_ijhat (shared or global);
-// inv, q32: the staged column jhat (shared, padded; inv NaN where x_ijhat = 0
-// and on padding rows, q32 0 there); lst: this warp's candidate list (qt
-// entries per lane, lane l's j-th entry at j*32 + l); hist: XB32 words.
-// Returns SEL_OK with the exact coarse key of v_k in tstar, SEL_INTERNAL, or
-// SEL_W64.
-__device__ __forceinline__ int select_w32(const float *__restrict__ xk, const float *__restrict__ colb,
-                          const float *__restrict__ inv, const uint32_t *__restrict__ q32,
-                          const uint16_t *__restrict__ samp, uint2 *__restrict__ lst,
-                          uint32_t *__restrict__ hist, int qt, int n, int d0, const Decide &dc,
-                          uint32_t &tstar, int lane) {
-    constexpr uint32_t G = 8;  // guard band of the approximate keys (float input)
+// Weighted median of pair (jhat, k).  xf: column k as float (global, rows
+// padded to a multiple of 128 with zeros; the column itself for float input,
+// its float copy for double input), read for the approximate keys; xk, colb:
+// column k and x_ijhat in the input type (colb shared or global), read for
+// the exact divisions; inv, q32: the staged column jhat (shared, padded; inv
+// NaN where x_ijhat = 0 and on padding rows, q32 0 there); lst: this warp's
+// candidate list (qt entries per lane, lane l's j-th entry at j*32 + l); hist:
+// XB32 words.  Keys up to the final step are coarse keys (of the ratio
+// rounded to float; the exact key for float input).  Returns SEL_OK with the
+// exact key of v_k in tstar, SEL_INTERNAL, or SEL_W64.
+template <typename T>
+__device__ __forceinline__ int select_w32(const float *__restrict__ xf, const T *__restrict__ xk,
+                                          const T *__restrict__ colb,
+                                          const float *__restrict__ inv,
+                                          const uint32_t *__restrict__ q32,
+                                          const uint16_t *__restrict__ samp,
+                                          uint2 *__restrict__ lst, uint32_t *__restrict__ hist,
+                                          int qt, int n, int d0, const Decide &dc,
+                                          typename Traits<T>::K &tstar, int lane) {
+    using Tr = Traits<T>;
+    using K = typename Tr::K;
+    constexpr uint32_t G = Approx<T>::G;  // guard band of the approximate keys
     const unsigned FULL = 0xFFFFFFFFu;
+    // exact coarse key of row i
+    auto exact_ck = [&](uint32_t i) -> uint32_t {
+        return Approx<T>::exact_ck(__ldg(xk + i), colb[i]);
+    };
     const float Qf = (float)dc.Q;
     const float hneg0 = 0.5f * (Qf + (float)dc.Lf), hpos0 = 0.5f * (Qf - (float)dc.Lc);
     const int ng = (n + 127) >> 7;  // 128-row groups (rows are padded to them)
@@ -400,7 +416,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int i = L1L_CHK((int)samp[e * 32 + lane], nrow);
-        sk[e] = akey(__fmul_rn(__ldg(xk + i), inv[i]));
+        sk[e] = akey(__fmul_rn(__ldg(xf + i), inv[i]));
     }
     warp_sort64(sk, lane);
     int jx;
@@ -437,7 +453,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
 
     const uint32_t lbase = smem_addr(lst) + (uint32_t)lane * 8u;
     const uint32_t lend = lbase + (uint32_t)qt * 256u;
-    const float4 *xk4 = reinterpret_cast<const float4 *>(xk);
+    const float4 *xk4 = reinterpret_cast<const float4 *>(xf);
     const uint32_t ainv0 = smem_addr(inv) + 16u * (uint32_t)lane;
     const uint32_t aq0 = smem_addr(q32) + 16u * (uint32_t)lane;
 
@@ -518,19 +534,19 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
             }
 #else
             // one predicated PTX block per slot (measured 2.8% faster than the same loop in C++)
-            static_assert(G == 8 && BinMapA::QSH == 21, "the PTX blocks hold G = 8 and 2^21-key bins");
+            static_assert(BinMapA::QSH == 21, "the PTX blocks hold bins of 2^21 keys");
             const uint32_t aq = smem_addr(q32);
             int pendi = 0;
             if (bm.cross) {
                 const int nb1 = bm.nneg + bm.npos - 1, nneg1 = bm.nneg - 1, npos1 = bm.npos - 1;
                 L1L_UNROLL(L1L_LIST_UNROLL)
                 for (int j = 0; j < cmax; ++j)
-                    passa_slot_cross(ebase + 256u * (uint32_t)j, j < cnt, g1, g2, bm.tp1, bm.tp2,
+                    passa_slot_cross<G>(ebase + 256u * (uint32_t)j, j < cnt, g1, g2, bm.tp1, bm.tp2,
                                      nneg1, npos1, nb1, aq, ahist, pendi);
             } else {
                 L1L_UNROLL(L1L_LIST_UNROLL)
                 for (int j = 0; j < cmax; ++j)
-                    passa_slot_unif(ebase + 256u * (uint32_t)j, j < cnt, g1, g2, bm.base,
+                    passa_slot_unif<G>(ebase + 256u * (uint32_t)j, j < cnt, g1, g2, bm.base,
                                     (uint32_t)bm.sh, aq, ahist, pendi);
             }
             pend = pendi != 0;
@@ -542,7 +558,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
                 const uint2 e = lst[L1L_CHK(j * 32 + lane, nslot)];
                 if (e.y & E32_PEND) {
                     const uint32_t id = L1L_CHK(e.y & E32_ROW, (uint32_t)nrow);
-                    const uint32_t kk = ckey(__fdiv_rn(__ldg(xk + id), colb[id]));
+                    const uint32_t kk = exact_ck(id);
                     lst[j * 32 + lane] = make_uint2(kk, id | E32_EXACT | E32_KEYED);
                     const uint32_t q = q32[id];
                     if (kk < P1)
@@ -605,7 +621,7 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
             uint32_t kk = e.x;
             const uint32_t off = (kk - lo) & bmask;
             if (!(e.y & E32_EXACT) && (off < G || off + G > bmask)) {
-                kk = ckey(__fdiv_rn(__ldg(xk + id), colb[id]));
+                kk = exact_ck(id);
                 lst[j * 32 + lane] = make_uint2(kk, id | E32_EXACT | E32_KEYED);
             }
             red_shared_add(ahist + 4u * L1L_CHK((kk - lo) >> sh, (uint32_t)XB32), q32[id]);
@@ -627,11 +643,18 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
     }
 
     // ---------------- final: exact keys of the <= 31 candidates -----------
-    if (lo == hi) {  // coarse keys are the exact keys for float input
-        tstar = lo;
-        return SEL_OK;
+    if constexpr (sizeof(T) == 4) {
+        if (lo == hi) {  // coarse keys are the exact keys for float input
+            tstar = lo;
+            return SEL_OK;
+        }
     }
-    if (c > 31) return SEL_INTERNAL;  // lo < hi and the levels stopped: cannot happen
+    if (c > 31) {
+        // float: lo < hi and the levels stopped, which cannot happen; double:
+        // more than 31 rows share one coarse key (the 64-bit selection sorts
+        // them out)
+        return sizeof(T) == 4 ? SEL_INTERNAL : SEL_W64;
+    }
     {
         const int excl = warp_scan_add(cnt, lane) - cnt;
         uint32_t *stage = hist;
@@ -640,13 +663,14 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
     }
     __syncwarp();
     const bool zero_in = lo <= CK0 && CK0 <= hi;
-    uint32_t fk = CKNONE, fq = 0;
+    K fk = Tr::NONE;
+    uint32_t fq = 0;
     if (lane < c) {
         const uint32_t row = L1L_CHK(hist[lane], (uint32_t)nrow);
-        fk = ckey(__fdiv_rn(__ldg(xk + row), colb[row]));
+        fk = Tr::key(Tr::div_rn(__ldg(xk + row), colb[row]));
         fq = q32[row];
     } else if (lane == c && zero_in) {
-        fk = CK0;  // the penalty point (0, lambda); lambda sits in the test
+        fk = Tr::KEY0;  // the penalty point (0, lambda); lambda sits in the test
     }
     __syncwarp();
     // each candidate's cumulative weight: the weight of candidates with a key
@@ -654,14 +678,23 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xk, const fl
     const int nv = c + (zero_in ? 1 : 0);
     uint32_t S = 0;
     for (int u = 0; u < nv; ++u) {
-        const uint32_t ku = __shfl_sync(FULL, fk, u);
+        const K ku = __shfl_sync(FULL, fk, u);
         const uint32_t qu = __shfl_sync(FULL, fq, u);
         S += ku <= fk ? qu : 0u;
     }
     int r = 0;
-    if (lane < nv) r = dc.cond(L + (int64_t)S, fk >= CK0);
-    const uint32_t kmin = __reduce_min_sync(FULL, r != 0 ? fk : CKNONE);
-    if (kmin == CKNONE) return SEL_INTERNAL;
+    if (lane < nv) r = dc.cond(L + (int64_t)S, fk >= Tr::KEY0);
+    K kmin = r != 0 ? fk : Tr::NONE;
+    if constexpr (sizeof(T) == 4) {
+        kmin = __reduce_min_sync(FULL, kmin);
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const K y = __shfl_xor_sync(FULL, kmin, o);
+            kmin = y < kmin ? y : kmin;
+        }
+    }
+    if (kmin == Tr::NONE) return SEL_INTERNAL;
     if (__any_sync(FULL, r == -1 && fk == kmin)) return SEL_W64;
     tstar = kmin;
     return SEL_OK;
