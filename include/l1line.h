@@ -48,6 +48,10 @@
 extern "C" {
 #endif
 
+/* Every entry point that enqueues work first clears a non-sticky CUDA error
+ * left by an earlier, unrelated runtime call (cudaGetLastError), so that its
+ * L1L_ERR_CUDA reports only its own failures; a sticky error (a lost
+ * context) stays and is reported. */
 typedef enum {
     L1L_OK = 0,
     L1L_ERR_ARG = -1,         /* bad argument (null, size, lambda < 0 / NaN / inf) */

@@ -38,6 +38,15 @@ struct NvtxRange {
 #define L1L_RANGE_CAT(a, b) L1L_RANGE_CAT2(a, b)
 #define L1L_RANGE(name) NvtxRange L1L_RANGE_CAT(nvtx_range_, __LINE__)(name)
 
+// An entry point's range.  It also clears a non-sticky CUDA error that an
+// earlier, unrelated runtime call left behind (an invalidated stream capture,
+// say): the launch checks below read cudaGetLastError and must see only this
+// call's own failures.  A sticky error (a lost context) stays and is reported.
+struct EntryRange : NvtxRange {
+    explicit EntryRange(const char *name) : NvtxRange(name) { (void)cudaGetLastError(); }
+};
+#define L1L_ENTRY(name) EntryRange L1L_RANGE_CAT(nvtx_entry_, __LINE__)(name)
+
 thread_local int g_last_launches = 0;
 thread_local Tune g_tune;  // l1line_set_tuning
 thread_local cudaEvent_t g_ev_start = nullptr, g_ev_stop = nullptr;
@@ -503,7 +512,7 @@ size_t l1line_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t n_lambda)
 int l1line_scan_ex_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                        int64_t n_lambda, float *v_all, double *s_all, double *z_all,
                        void *workspace, size_t workspace_bytes, void *stream, uint32_t flags) {
-    L1L_RANGE("l1line_scan_ex_f32");
+    L1L_ENTRY("l1line_scan_ex_f32");
     return scan_impl<float>(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                             workspace_bytes, stream, flags);
 }
@@ -511,7 +520,7 @@ int l1line_scan_ex_f32(const float *X, int64_t n, int64_t m, const double *lambd
 int l1line_scan_ex_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                        int64_t n_lambda, double *v_all, double *s_all, double *z_all,
                        void *workspace, size_t workspace_bytes, void *stream, uint32_t flags) {
-    L1L_RANGE("l1line_scan_ex_f64");
+    L1L_ENTRY("l1line_scan_ex_f64");
     return scan_impl<double>(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                              workspace_bytes, stream, flags);
 }
@@ -519,7 +528,7 @@ int l1line_scan_ex_f64(const double *X, int64_t n, int64_t m, const double *lamb
 int l1line_scan_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                     int64_t n_lambda, float *v_all, double *s_all, double *z_all,
                     void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_scan_f32");
+    L1L_ENTRY("l1line_scan_f32");
     return l1line_scan_ex_f32(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                               workspace_bytes, stream, 0u);
 }
@@ -527,7 +536,7 @@ int l1line_scan_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
 int l1line_scan_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                     int64_t n_lambda, double *v_all, double *s_all, double *z_all,
                     void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_scan_f64");
+    L1L_ENTRY("l1line_scan_f64");
     return l1line_scan_ex_f64(X, n, m, lambdas, n_lambda, v_all, s_all, z_all, workspace,
                               workspace_bytes, stream, 0u);
 }
@@ -535,7 +544,7 @@ int l1line_scan_f64(const double *X, int64_t n, int64_t m, const double *lambdas
 int l1line_fit_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, float *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_fit_f32");
+    L1L_ENTRY("l1line_fit_f32");
     return fit_impl<float>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar,
                            workspace, workspace_bytes, stream);
 }
@@ -543,7 +552,7 @@ int l1line_fit_f32(const float *X, int64_t n, int64_t m, const double *lambdas,
 int l1line_fit_f64(const double *X, int64_t n, int64_t m, const double *lambdas,
                    int64_t n_lambda, double *out_v, double *out_obj, int32_t *out_jstar,
                    void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_fit_f64");
+    L1L_ENTRY("l1line_fit_f64");
     return fit_impl<double>(X, n, m, lambdas, n_lambda, nullptr, 0, out_v, out_obj, out_jstar,
                             workspace, workspace_bytes, stream);
 }
@@ -552,7 +561,7 @@ int l1line_fit_subset_f32(const float *X, int64_t n, int64_t m, const double *la
                           int64_t n_lambda, const int32_t *jhat_list, int64_t K, float *out_v,
                           double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_fit_subset_f32");
+    L1L_ENTRY("l1line_fit_subset_f32");
     if (!jhat_list) return L1L_ERR_ARG;
     return fit_impl<float>(X, n, m, lambdas, n_lambda, jhat_list, K, out_v, out_obj, out_jstar,
                            workspace, workspace_bytes, stream);
@@ -562,7 +571,7 @@ int l1line_fit_subset_f64(const double *X, int64_t n, int64_t m, const double *l
                           int64_t n_lambda, const int32_t *jhat_list, int64_t K, double *out_v,
                           double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_fit_subset_f64");
+    L1L_ENTRY("l1line_fit_subset_f64");
     if (!jhat_list) return L1L_ERR_ARG;
     return fit_impl<double>(X, n, m, lambdas, n_lambda, jhat_list, K, out_v, out_obj, out_jstar,
                             workspace, workspace_bytes, stream);
@@ -579,21 +588,21 @@ size_t l1line_proposed_workspace_bytes(int dtype, int64_t n, int64_t m, int64_t 
 
 int l1line_features_f32(const float *X, int64_t n, int64_t m, double lambda, float *out_raw,
                         float *out_std, void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_features_f32");
+    L1L_ENTRY("l1line_features_f32");
     return features_impl<float>(X, n, m, lambda, out_raw, out_std, workspace, workspace_bytes,
                                 stream);
 }
 
 int l1line_features_f64(const double *X, int64_t n, int64_t m, double lambda, float *out_raw,
                         float *out_std, void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_features_f64");
+    L1L_ENTRY("l1line_features_f64");
     return features_impl<double>(X, n, m, lambda, out_raw, out_std, workspace, workspace_bytes,
                                  stream);
 }
 
 int l1line_mlp_forward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
                        float *scores, void *stream) {
-    L1L_RANGE("l1line_mlp_forward");
+    L1L_ENTRY("l1line_mlp_forward");
     g_last_launches = 0;
     if (!feat || !mlp || !scores || N < 1) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
@@ -614,7 +623,7 @@ size_t l1line_mlp_workspace_bytes(int64_t N) {
 int l1line_mlp_backward(const float *feat, const int32_t *rows, int64_t N, const l1line_mlp *mlp,
                         const float *dscores, float *grad, void *workspace,
                         size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_mlp_backward");
+    L1L_ENTRY("l1line_mlp_backward");
     g_last_launches = 0;
     if (!feat || !mlp || !dscores || !grad || N < 1) return L1L_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
@@ -634,7 +643,7 @@ int l1line_mlp_backward(const float *feat, const int32_t *rows, int64_t N, const
 int l1line_rank_loss(const float *scores, const float *targets, const int32_t *rows,
                      const int64_t *offsets, int64_t n_inst, float *dscores, float *loss,
                      void *stream) {
-    L1L_RANGE("l1line_rank_loss");
+    L1L_ENTRY("l1line_rank_loss");
     g_last_launches = 0;
     if (!scores || !targets || !offsets || !dscores || !loss || n_inst < 1) return L1L_ERR_ARG;
     if (n_inst > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
@@ -649,7 +658,7 @@ int l1line_rank_loss(const float *scores, const float *targets, const int32_t *r
 int l1line_adam_step(float *theta, const float *grad, float *m1, float *m2, int64_t step,
                      float lr, float beta1, float beta2, float eps, l1line_mlp *mlp,
                      void *stream) {
-    L1L_RANGE("l1line_adam_step");
+    L1L_ENTRY("l1line_adam_step");
     g_last_launches = 0;
     if (!theta || !grad || !m1 || !m2 || step < 1) return L1L_ERR_ARG;
     if (!(lr >= 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
@@ -668,7 +677,7 @@ int l1line_adam_step(float *theta, const float *grad, float *m1, float *m2, int6
 }
 
 int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream) {
-    L1L_RANGE("l1line_mlp_pack");
+    L1L_ENTRY("l1line_mlp_pack");
     g_last_launches = 0;
     if (!theta || !mlp || (reinterpret_cast<uintptr_t>(mlp) & 15) != 0) return L1L_ERR_ARG;
     int launches = 0;
@@ -679,7 +688,7 @@ int l1line_mlp_pack(const float *theta, l1line_mlp *mlp, void *stream) {
 }
 
 int l1line_topk(const float *scores, int64_t m, int64_t K, int32_t *out_idx, void *stream) {
-    L1L_RANGE("l1line_topk");
+    L1L_ENTRY("l1line_topk");
     g_last_launches = 0;
     if (!scores || !out_idx || m < 1 || K < 1 || K > m) return L1L_ERR_ARG;
     if (m > 0x7FFFFFFF) return L1L_ERR_UNSUPPORTED;
@@ -695,7 +704,7 @@ int l1line_fit_proposed_f32(const float *X, int64_t n, int64_t m, const double *
                             int64_t n_lambda, const l1line_mlp *mlp, int64_t K, int32_t *out_idx,
                             float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
                             size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_fit_proposed_f32");
+    L1L_ENTRY("l1line_fit_proposed_f32");
     return proposed_impl<float>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
                                 out_jstar, workspace, workspace_bytes, stream);
 }
@@ -705,7 +714,7 @@ int l1line_fit_proposed_f64(const double *X, int64_t n, int64_t m, const double 
                             int32_t *out_idx, double *out_v, double *out_obj,
                             int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                             void *stream) {
-    L1L_RANGE("l1line_fit_proposed_f64");
+    L1L_ENTRY("l1line_fit_proposed_f64");
     return proposed_impl<double>(X, n, m, lambdas, n_lambda, mlp, K, out_idx, out_v, out_obj,
                                  out_jstar, workspace, workspace_bytes, stream);
 }
@@ -725,20 +734,20 @@ size_t l1line_path_workspace_bytes(int dtype, int64_t n, int64_t m) {
 
 int l1line_path_count_f32(const float *X, int64_t n, int64_t m, int64_t *offsets,
                           void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_path_count_f32");
+    L1L_ENTRY("l1line_path_count_f32");
     return path_count_impl<float>(X, n, m, offsets, workspace, workspace_bytes, stream);
 }
 
 int l1line_path_count_f64(const double *X, int64_t n, int64_t m, int64_t *offsets,
                           void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_path_count_f64");
+    L1L_ENTRY("l1line_path_count_f64");
     return path_count_impl<double>(X, n, m, offsets, workspace, workspace_bytes, stream);
 }
 
 int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *offsets,
                           double *out_lambda, float *out_v, double *out_resid, int32_t *out_len,
                           void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_path_write_f32");
+    L1L_ENTRY("l1line_path_write_f32");
     return path_write_impl<float>(X, n, m, offsets, out_lambda, out_v, out_resid, out_len,
                                   workspace, workspace_bytes, stream);
 }
@@ -746,7 +755,7 @@ int l1line_path_write_f32(const float *X, int64_t n, int64_t m, const int64_t *o
 int l1line_path_write_f64(const double *X, int64_t n, int64_t m, const int64_t *offsets,
                           double *out_lambda, double *out_v, double *out_resid, int32_t *out_len,
                           void *workspace, size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_path_write_f64");
+    L1L_ENTRY("l1line_path_write_f64");
     return path_write_impl<double>(X, n, m, offsets, out_lambda, out_v, out_resid, out_len,
                                    workspace, workspace_bytes, stream);
 }
@@ -793,7 +802,7 @@ int l1line_solution_path_f32(int64_t m, const int64_t *offsets, const double *la
                              double *out_intercept, double *out_slope, float *out_v,
                              int64_t *out_count, int64_t cap, void *workspace,
                              size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_solution_path_f32");
+    L1L_ENTRY("l1line_solution_path_f32");
     return solution_path_impl<float>(m, offsets, lambda, v, resid, len, entries, out_start,
                                      out_jhat, out_intercept, out_slope, out_v, out_count, cap,
                                      workspace, workspace_bytes, stream);
@@ -805,7 +814,7 @@ int l1line_solution_path_f64(int64_t m, const int64_t *offsets, const double *la
                              double *out_intercept, double *out_slope, double *out_v,
                              int64_t *out_count, int64_t cap, void *workspace,
                              size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_solution_path_f64");
+    L1L_ENTRY("l1line_solution_path_f64");
     return solution_path_impl<double>(m, offsets, lambda, v, resid, len, entries, out_start,
                                       out_jhat, out_intercept, out_slope, out_v, out_count, cap,
                                       workspace, workspace_bytes, stream);
@@ -862,7 +871,7 @@ extern "C" {
 int l1line_components_f32(const float *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
                           float *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_components_f32");
+    L1L_ENTRY("l1line_components_f32");
     return components_impl<float>(X, n, m, lambda, ncomp, out_v, out_obj, out_jstar, workspace,
                                   workspace_bytes, stream);
 }
@@ -870,13 +879,13 @@ int l1line_components_f32(const float *X, int64_t n, int64_t m, double lambda, i
 int l1line_components_f64(const double *X, int64_t n, int64_t m, double lambda, int64_t ncomp,
                           double *out_v, double *out_obj, int32_t *out_jstar, void *workspace,
                           size_t workspace_bytes, void *stream) {
-    L1L_RANGE("l1line_components_f64");
+    L1L_ENTRY("l1line_components_f64");
     return components_impl<double>(X, n, m, lambda, ncomp, out_v, out_obj, out_jstar, workspace,
                                    workspace_bytes, stream);
 }
 
 int l1line_status(void *workspace, void *stream) {
-    L1L_RANGE("l1line_status");
+    L1L_ENTRY("l1line_status");
     return status_of(workspace, stream);
 }
 
@@ -991,7 +1000,7 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
 
 int l1line_probe(int kind, const void *buf, size_t bytes, int reps, void *sink, void *stream,
                  double *bytes_read) {
-    L1L_RANGE("l1line_probe");
+    L1L_ENTRY("l1line_probe");
     g_last_launches = 0;
     if (!sink || !bytes_read || reps < 1 || (reinterpret_cast<uintptr_t>(sink) & 3) != 0)
         return L1L_ERR_ARG;
@@ -1239,7 +1248,7 @@ int l1line_fit_batched_f32(int64_t batch, const float *const *Xs, const int64_t 
                            const int64_t *lambda_offsets, float *out_v, double *out_obj,
                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                            void *stream) {
-    L1L_RANGE("l1line_fit_batched_f32");
+    L1L_ENTRY("l1line_fit_batched_f32");
     return fit_batched_impl<float>(batch, Xs, ns, ms, lambdas, lambda_offsets, out_v, out_obj,
                                    out_jstar, workspace, workspace_bytes, stream, 0u);
 }
@@ -1249,7 +1258,7 @@ int l1line_fit_batched_f64(int64_t batch, const double *const *Xs, const int64_t
                            const int64_t *lambda_offsets, double *out_v, double *out_obj,
                            int32_t *out_jstar, void *workspace, size_t workspace_bytes,
                            void *stream) {
-    L1L_RANGE("l1line_fit_batched_f64");
+    L1L_ENTRY("l1line_fit_batched_f64");
     return fit_batched_impl<double>(batch, Xs, ns, ms, lambdas, lambda_offsets, out_v, out_obj,
                                     out_jstar, workspace, workspace_bytes, stream, 0u);
 }
@@ -1287,7 +1296,7 @@ int noalloc_scratch_address(void **out) {
 }  // namespace
 
 extern "C" int l1line_noalloc_status(void *stream) {
-    L1L_RANGE("l1line_noalloc_status");
+    L1L_ENTRY("l1line_noalloc_status");
     void *ws = nullptr;
     const int rc = noalloc_scratch_address(&ws);
     if (rc != L1L_OK) return rc;
@@ -1297,7 +1306,7 @@ extern "C" int l1line_noalloc_status(void *stream) {
 extern "C" int l1line_fit_noalloc_f32(const float *X, int64_t n, int64_t m,
                                       const double *lambdas, int64_t n_lambda, float *out_v,
                                       double *out_obj, int32_t *out_jstar, void *stream) {
-    L1L_RANGE("l1line_fit_noalloc_f32");
+    L1L_ENTRY("l1line_fit_noalloc_f32");
     if (!X || !lambdas || !out_v || !out_obj || !out_jstar || n < 1 || m < 1 || n_lambda < 1)
         return L1L_ERR_ARG;
     const size_t need = l1line_workspace_bytes(L1L_DTYPE_F32, n, m, n_lambda);
