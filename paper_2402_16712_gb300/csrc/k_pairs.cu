@@ -193,18 +193,19 @@ static PairPlan plan_pairs_for(int64_t n, int64_t m, int num_sms, int64_t nj, co
 template <typename T>
 PairPlan plan_pairs(int64_t n, int64_t m, int num_sms, int64_t nj, const Tune &tune, bool single) {
     // A single-instance call whose pairs fit in one wave at 16 warps per SM
-    // is bound by the latency of one pair, not by throughput: one CTA per SM
-    // at 128 registers, 8-16 warps per CTA (fewer CTAs stage column jhat
-    // fewer times) spreading the pairs over the SMs; the throughput plan when
-    // that many warps' lists do not fit.  Small 200 x 20 double fit, CUDA
-    // graph: 16 x 2 warps 36.4 us, 3 x 1 and 8 x 1 34.4 us.
+    // is bound by the latency of one pair, not by throughput: 8-16 warps per
+    // CTA (fewer CTAs stage column jhat fewer times) spreading the pairs over
+    // the SMs, in the 80-register shape up to 8 warps (its lists sized for 3
+    // CTAs per SM) and the 128-register one above; the throughput plan when
+    // those lists do not fit.  Small 200 x 20 double fit, CUDA graph: 16 x 2
+    // warps 36.4 us, 3 x 1 and 8 x 1 34.4 us, 8 x 3 32.9 us.
     if (single && tune.warps == 0 && tune.ctas == 0 && nj > 0 &&
         nj * m <= (int64_t)num_sms * 16) {
         const int64_t per_col = std::max<int64_t>(1, num_sms / nj);  // CTAs per column jhat
         const int64_t w = std::max<int64_t>(std::min<int64_t>(m, 8), (m + per_col - 1) / per_col);
         Tune lt = tune;
         lt.warps = (int)std::min<int64_t>(16, std::max<int64_t>(1, w));
-        lt.ctas = 1;
+        lt.ctas = lt.warps <= 8 ? 3 : 1;
         const PairPlan p = plan_pairs_for<T>(n, m, num_sms, nj, lt);
         if (p.warps > 0) return p;
     }
