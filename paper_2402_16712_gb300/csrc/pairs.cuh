@@ -634,7 +634,7 @@ __device__ int select_v2(const T *__restrict__ xk, const float *__restrict__ xf,
             const int p = L1L_CHK(j * 32 + lane, nslot);
             uint32_t kk = lk[p];
             uint16_t id = li[p];
-            L1L_CHK((int)(id & ROW_MASK), nrow);
+            (void)L1L_CHK((int)(id & ROW_MASK), nrow);  // counted in the checked build
             const uint32_t off = (kk - lo) & bmask;
             if (!(id & EXACT_BIT) && (off < G || off + G > bmask)) {
                 const int row = id & ROW_MASK;

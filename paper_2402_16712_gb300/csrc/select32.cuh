@@ -410,6 +410,8 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xf, const T 
     const int ng = (n + 127) >> 7;  // 128-row groups (rows are padded to them)
     const int nrow = ng * 128;      // rows every staged or copied column holds
     const int nslot = qt * 32;      // candidate slots of this warp's list
+    (void)nrow;                     // read by the bounds checks only
+    (void)nslot;
 
     // ---------------- sample bracket ------------------------------------
     uint32_t sk[2];
