@@ -444,7 +444,7 @@ def run_gpu(args):
                    "tuning": {"applied": tuning, "plan": plan}},
         "fits_per_s": world * args.steps / (tot_ms * 1e-3),
         "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT,
-                "tuning": tuning64},
+                "tuning": tuning64, "roofline": f64_roofline(n, pairs, ms64)},
         "roofline": roofline(n, pairs, kms, plan["kchunk"], plan["column"], l2_gbs,
                              smem_gbs, _profile_traffic(),
                              pair_shape(plan["warps"], plan["ctas_per_sm"])),
@@ -478,6 +478,22 @@ def measure_ceilings(dev, stream):
         l1line.probe_bandwidth(l1line.PROBE_SMEM, 16, None, stream)
         sm = max(l1line.probe_bandwidth(l1line.PROBE_SMEM, 4000, None, stream) for _ in range(3))
     return l2 / 1e9, sm / 1e9
+
+
+FP64_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64, nominal (no measured FP64 peak is recorded)
+
+
+def f64_roofline(n, pairs, ms):
+    """The double fit against the FP64 pipe: its residual does one FMA (2
+    flops) and one add (1 flop) in double per (pair, row), the algorithmic
+    FP64 work; the selection's double divisions come on top.  Peak: the
+    nominal dense FP64 rate (MEASURED_PEAKS.json records none)."""
+    flops = 3.0 * n * pairs
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"bound": "fp64", "achieved": achieved, "peak": FP64_TFLOPS_NOMINAL,
+            "unit": "TFLOP/s", "frac": achieved / FP64_TFLOPS_NOMINAL,
+            "basis": "3 FP64 flops per (pair,row) (the residual's FMA and add in double) / whole "
+                     "fit time; peak = nominal dense FP64 (none measured)"}
 
 
 def pair_shape(warps, ctas):

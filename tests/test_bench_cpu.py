@@ -279,3 +279,11 @@ def test_pair_shape_label_follows_the_register_budgets():
     assert [bench.pair_shape(w, c) for w, c in ((16, 1), (8, 2), (4, 3), (8, 3), (7, 3),
                                                 (16, 2), (13, 2), (10, 3))] == \
         [2, 2, 2, 0, 0, 1, 1, 1]
+
+
+def test_f64_roofline_arithmetic():
+    import bench
+    r = bench.f64_roofline(2000, 3_998_000, 36.0)
+    # 3 flops per pair-row: 2000 * 3,998,000 * 3 / 36 ms = 0.6663 TFLOP/s
+    assert r["achieved"] == pytest.approx(2000 * 3_998_000 * 3 / 0.036 / 1e12)
+    assert r["bound"] == "fp64" and r["frac"] == pytest.approx(r["achieved"] / 1.25)
