@@ -79,6 +79,24 @@ def test_wide_exponent_columns(dtype):
     check_scan(Y, [0.0, 0.2], where="tiny entries")
 
 
+@pytest.mark.parametrize("cluster", [12, 31, 32, 200])
+def test_double_ratios_equal_in_float(cluster):
+    """Double input whose median lies among ratios that differ in double but
+    round to one float (one coarse key): up to 31 such rows are decided on
+    their 64-bit keys in the final step, more go to the 64-bit selection."""
+    rng = np.random.default_rng(cluster)
+    n, m = 400, 5
+    X = rng.standard_normal((n, m))
+    # column 0 / column 1 = 1 + i 2^-45 on the cluster rows: distinct doubles,
+    # one float; those rows carry most of the weight of column 1
+    rows = rng.choice(n, size=cluster, replace=False)
+    X[rows, 1] = 50.0 + rng.random(cluster)
+    X[rows, 0] = X[rows, 1] * (1.0 + np.arange(cluster) * 2.0 ** -45)
+    X[rows, 2] = -X[rows, 1] * (3.0 - np.arange(cluster)[::-1] * 2.0 ** -44)
+    _, _, ref = check_scan(X, [0.0, 0.5, 40.0], where=f"coarse ties {cluster}")
+    check_fit(X, [0.0, 0.5, 40.0], ref, where=f"coarse ties {cluster}")
+
+
 @pytest.mark.parametrize("dtype", DT)
 def test_lambda_batch(dtype):
     X, lams, _ = datagen.lambda_path(np.dtype(dtype).name, n=300, m=24, n_lambda=40)
