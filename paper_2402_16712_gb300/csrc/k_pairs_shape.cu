@@ -29,6 +29,13 @@
 #define L1L_LIST_UNROLL 1
 #endif
 #endif
+// Lane balancing of the candidate lists (list32_balance), measured on the
+// 2000 x 2000 float fit, kernel time: 8 x 3 warps (80 registers) 14.36 ->
+// 13.86 ms, 16 x 2 warps (64 registers) 13.11 -> 13.61 ms, 16 x 1 warps (128
+// registers) 16.82 -> 16.80 ms; so only the 80-register shape balances.
+#ifndef L1L_BALANCE
+#define L1L_BALANCE (L1L_SHAPE == 0)
+#endif
 
 #include <algorithm>
 

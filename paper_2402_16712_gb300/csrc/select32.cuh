@@ -34,6 +34,11 @@
 #ifndef L1L_LIST_UNROLL
 #define L1L_LIST_UNROLL 1
 #endif
+// Lane balancing of the candidate lists after each level-0 pass
+// (list32_balance), chosen per launch shape like the unroll factors.
+#ifndef L1L_BALANCE
+#define L1L_BALANCE 0
+#endif
 #define L1L_PRAGMA(x) _Pragma(#x)
 #define L1L_UNROLL(n) L1L_PRAGMA(unroll n)
 
@@ -378,6 +383,45 @@ __device__ __forceinline__ int list32_keep(uint2 *__restrict__ lst, int cnt, uin
     return w;
 }
 
+// Evens out the lanes' candidate counts in place after a level-0 pass.  The
+// rows fall to the lanes by position, so one lane often holds nearly twice
+// the warp's mean; pass A, pass B and the keep loop run to the busiest
+// lane's count.  With C candidates in the warp and T = ceil(C / 32), a lane
+// holding more than T hands its last entries to lanes holding fewer: excess
+// entry e (numbered across the lanes in lane order) fills hole e (the free
+// slots below T, numbered the same way), so every lane then holds at most T.
+// Holes lie below slot T and handed entries at or above it, so no slot is
+// both read and written.  tab (XB32 words, free at this point) maps a hole
+// to its slot; at most XB32 entries move (the rest stay where they are).
+// The order of a lane's entries carries no meaning.  Returns the lane's new
+// count.
+__device__ __forceinline__ int list32_balance(uint2 *__restrict__ lst, uint32_t *__restrict__ tab,
+                                              int cnt, int lane, int nslot) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int C = (int)__reduce_add_sync(FULL, (unsigned)cnt);
+    const int T = (C + 31) >> 5;
+    const int E = max(cnt - T, 0), D = max(T - cnt, 0);
+    // excess in the high half, holes in the low half: both sums stay below
+    // 2^16 (at most 32 qt slots)
+    const uint32_t pk = ((uint32_t)E << 16) | (uint32_t)D;
+    const uint32_t inc = warp_scan_add(pk, lane);
+    const int M = min((int)(__shfl_sync(FULL, inc, 31) >> 16), XB32);  // entries that move
+    if (M == 0) return cnt;
+    const uint32_t ex = inc - pk;
+    const int Epre = (int)(ex >> 16), Dpre = (int)(ex & 0xFFFFu);
+    const int got = min(max(M - Dpre, 0), D);   // holes of this lane that are filled
+    const int gave = min(max(M - Epre, 0), E);  // entries this lane hands over
+    for (int u = 0; u < got; ++u)
+        tab[L1L_CHK(Dpre + u, XB32)] = (uint32_t)((cnt + u) * 32 + lane);
+    __syncwarp();
+    for (int t = 0; t < gave; ++t) {
+        const uint32_t dst = tab[L1L_CHK(Epre + t, XB32)];
+        lst[L1L_CHK((int)dst, nslot)] = lst[L1L_CHK((cnt - 1 - t) * 32 + lane, nslot)];
+    }
+    __syncwarp();
+    return cnt + got - gave;
+}
+
 // Weighted median of pair (jhat, k).  xf: column k as float (global, rows
 // padded to a multiple of 128 with zeros; the column itself for float input,
 // its float copy for double input), read for the approximate keys; xk, colb:
@@ -494,6 +538,9 @@ __device__ __forceinline__ int select_w32(const float *__restrict__ xf, const T 
             sample_bracket(dcur, P1, P2);
             continue;
         }
+#if L1L_BALANCE
+        cnt = list32_balance(lst, hist, cnt, lane, nslot);
+#endif
 
         // ---- exact histogram of the candidates over the bins of [P1, P2].
         // Pass A: a candidate whose approximate key is at least G inside P1,
