@@ -399,6 +399,7 @@ def run_gpu(args):
         e1.record(stream)
     stream.synchronize()
     ms64 = e0.elapsed_time(e1) / k64
+    plan64 = l1line.plan(torch.float64, n, m)  # the launch the double steps ran
     l1line.set_tuning(None)
 
     # ---- end to end through the ABI with host buffers ----------------------
@@ -444,7 +445,11 @@ def run_gpu(args):
                    "tuning": {"applied": tuning, "plan": plan}},
         "fits_per_s": world * args.steps / (tot_ms * 1e-3),
         "f64": {"ms_per_step": ms64, "value": pairs / (ms64 * 1e-3), "unit": UNIT,
-                "tuning": tuning64, "roofline": f64_roofline(n, pairs, ms64)},
+                "tuning": {"applied": tuning64, "plan": plan64},
+                "roofline": roofline(n, pairs, ms64, plan64["kchunk"], plan64["column"], l2_gbs,
+                                     smem_gbs, None,
+                                     pair_shape(plan64["warps"], plan64["ctas_per_sm"]),
+                                     dtype="double", timed="whole fit")},
         "roofline": roofline(n, pairs, kms, plan["kchunk"], plan["column"], l2_gbs,
                              smem_gbs, _profile_traffic(),
                              pair_shape(plan["warps"], plan["ctas_per_sm"])),
@@ -480,22 +485,6 @@ def measure_ceilings(dev, stream):
     return l2 / 1e9, sm / 1e9
 
 
-FP64_TFLOPS_NOMINAL = 1.25  # GB300 dense FP64, nominal (no measured FP64 peak is recorded)
-
-
-def f64_roofline(n, pairs, ms):
-    """The double fit against the FP64 pipe: its residual does one FMA (2
-    flops) and one add (1 flop) in double per (pair, row), the algorithmic
-    FP64 work; the selection's double divisions come on top.  Peak: the
-    nominal dense FP64 rate (MEASURED_PEAKS.json records none)."""
-    flops = 3.0 * n * pairs
-    achieved = flops / (ms * 1e-3) / 1e12
-    return {"bound": "fp64", "achieved": achieved, "peak": FP64_TFLOPS_NOMINAL,
-            "unit": "TFLOP/s", "frac": achieved / FP64_TFLOPS_NOMINAL,
-            "basis": "3 FP64 flops per (pair,row) (the residual's FMA and add in double) / whole "
-                     "fit time; peak = nominal dense FP64 (none measured)"}
-
-
 def pair_shape(warps, ctas):
     """The library's launch shape for warps per CTA x CTAs per SM (the rule of
     pair_shape in csrc/k_pairs.cu): 2 = 128 registers (<= 16 resident warps),
@@ -504,10 +493,14 @@ def pair_shape(warps, ctas):
     return 2 if t <= 16 else (0 if t <= 24 else 1)
 
 
-def roofline(n, pairs, kms, kchunk, column, l2_gbs, smem_gbs, traffic, shape=0):
+def roofline(n, pairs, kms, kchunk, column, l2_gbs, smem_gbs, traffic, shape=0,
+             dtype="float", timed="pair kernel"):
     """The pair kernel against its three ceilings; the binding one (the fewest
     pairs/s) is the headline roofline.  kchunk, column and shape are those of
-    the timed launch's plan (column 1: x_ijhat staged in shared memory)."""
+    the timed launch's plan (column 1: x_ijhat staged in shared memory).  The
+    double fit has the same ceilings: it selects on the same 32-bit weights
+    and staged arrays, and its residual runs in float-float arithmetic; kms
+    is then the whole fit's time (timed says which)."""
     pps = pairs / (kms * 1e-3)
     alu_peak = SMS * LANES_PER_SM_CLK * SM_MAX_MHZ * 1e6 / 1e12
     per = {
@@ -530,8 +523,8 @@ def roofline(n, pairs, kms, kchunk, column, l2_gbs, smem_gbs, traffic, shape=0):
     c = ceilings[bound]
     return {"bound": bound, "achieved": c["achieved"], "peak": c["peak"], "unit": c["unit"],
             "frac": c["frac"], "traffic": traffic,
-            "kernel": f"k_pairs<float, 0, {1 if column == 1 else 0}, {shape}>",
-            "kernel_ms": kms, "basis": c["basis"], "ceilings": ceilings}
+            "kernel": f"k_pairs<{dtype}, 0, {1 if column == 1 else 0}, {shape}>",
+            "kernel_ms": kms, "timed": timed, "basis": c["basis"], "ceilings": ceilings}
 
 
 def _replay_ms(g, stream, steps, flush=None):

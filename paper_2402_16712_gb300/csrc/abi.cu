@@ -93,10 +93,10 @@ bool make_layout(int dtype, int64_t n, int64_t m, int64_t nl, Layout &L) {
     off = al256(off + (size_t)m * sizeof(ColInfo));
     L.Xt = off;
     off = al256(off + (size_t)xt * es);
-    L.Xf = L.Xt;  // double input: a float copy for the approximate keys
-    if (es == 8) {
+    L.Xf = L.Xt;  // double input: a float copy for the approximate keys and
+    if (es == 8) {  // the remainders x - fl(x) for the float-float residual
         L.Xf = off;
-        off = al256(off + (size_t)xt * 4);
+        off = al256(off + (size_t)xt * 8);
     }
     L.v_all = off;
     off = al256(off + (size_t)pairs * es);

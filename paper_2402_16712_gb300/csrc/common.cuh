@@ -84,7 +84,9 @@ struct ColInfo {
     uint32_t Q32;
     int32_t shift32;
     int32_t n_inexact32;
-    int32_t pad_;
+    // sum_i |x_i| bounded above, as a float: (Q + n_inexact) 2^-sigma rounded up
+    // (the certificate of the float-float residual of double pairs reads it)
+    float l1_up;
 };
 
 // A column is "wide" when some nonzero |x| lies outside the range in which the
@@ -235,7 +237,8 @@ struct SlowEntry {
 // Shapes and device pointers of one scan, passed by value to every kernel.
 template <typename T> struct ScanArgs {
     const T *Xt;       // [m][ldn] column-major copy of X
-    const float *Xf;   // the same rounded to float (== Xt for float input)
+    const float *Xf;   // the same rounded to float (== Xt for float input); double
+                       // input: [2][m][ldn], the remainders x - fl(x) second
     const ColInfo *ci;  // [m]
     int64_t n, m, ldn;
     int32_t n_lambda;
@@ -313,8 +316,8 @@ __host__ __device__ inline InstLayout inst_layout(int64_t m, int64_t ldn, int64_
     o = al256b(o + (size_t)m * sizeof(ColInfo));
     L.Xt = o;
     o = al256b(o + (size_t)m * (size_t)ldn * es);
-    L.Xf = es == 8 ? o : L.Xt;  // float copy for double input
-    if (es == 8) o = al256b(o + (size_t)m * (size_t)ldn * 4);
+    L.Xf = es == 8 ? o : L.Xt;  // double input: float copy, then its remainders
+    if (es == 8) o = al256b(o + (size_t)m * (size_t)ldn * 8);
     L.v_all = o;
     o = al256b(o + (size_t)nl * (size_t)m * (size_t)m * es);
     L.s_all = o;

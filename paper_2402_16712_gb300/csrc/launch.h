@@ -16,7 +16,8 @@ cudaError_t ensure_smem(const void *fn, size_t bytes);
 // Resident blocks per SM for (kernel, threads, dynamic shared memory), cached.
 cudaError_t blocks_per_sm(const void *fn, int threads, size_t smem, int *out);
 
-// Xf: the float copy of Xt for double input (unused for float input).
+// Xf: the float copy of Xt for double input, followed by the remainders
+// x - fl(x) at Xf + m ldn (unused for float input).
 template <typename T>
 cudaError_t launch_prep(const T *X, T *Xt, float *Xf, ColInfo *ci, int64_t n, int64_t m,
                         int64_t ldn, uint32_t *status, cudaStream_t st, int &launches);

@@ -824,13 +824,124 @@ __device__ __forceinline__ int select_pair(const T *xk, const float *xf, const W
     return st64;
 }
 
-// Residual of one pair (CS: x_ijhat staged in shared memory).
+// ---------------------------------------------------------------------------
+// Residual of a double pair in float-float arithmetic (the double pipe of
+// this GPU runs at 1/64 of the float rate; summed in double, the residual's
+// two double operations per row made that pipe the bound of the double fit).  Each double x is held as two floats, x1 = fl(x) and
+// x2 = fl(x - x1) (the staged copies Xf and Xlo), so |x - x1 - x2| <= u^2|x|
+// with u = 2^-24; v likewise.  Per row, with K = |v||x_ijhat|:
+//   p1 = fl(v1 b1), e1 = fma(v1, b1, -p1) (exact), c = fma(v1, b2, fma(v2, b1, e1));
+//   (s, t) = TwoSum(a1, -p1) (exact), d = fl(fl(a2 - c) + t);
+// then s + d = x_ik - v x_ijhat within u^2 (4.04|x_ik| + 15.12 K) + 8 eta
+// (eta = 2^-150, the products' underflow), and |s + d| is the pair negated
+// when fl(s + d) < 0.  A lane sums its rows in blocks of 8: (H, e) =
+// TwoSum(H, s'), L = fl(L + fl(d' + e)), error <= 9.02 u sum|d| + 72.1 u^2
+// T_block with |d| <= u (2.04|x_ik| + 4.06 K); each block goes to a double
+// accumulator (two roundings of 2^-53 per block), the lanes' sums are added
+// in double.  In all, with C_k = sum_i |x_ik|, W = sum_i |x_ijhat|, T the
+// exact residual and ldn the padded rows,
+//   |T_ff - T| <= E = u^2 (24 C_k + 56 |v| W + (76 + ldn/4096) T) + ldn 2^-146.
+// ff_certified accepts T_ff when E (with 77 T_ff in place of 76 T, and C_k, W
+// bounded above from the fixed-point column totals) is at most 2^-40 T_ff,
+// i.e. a relative error of at most 9.1e-13; any other pair (a near-exact
+// fit, v outside [2^-60, 2^60]) is summed again in double.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ff_row(float a1, float a2, float b1, float b2, float v1, float v2,
+                                       float &H, float &L) {
+    const float p1 = __fmul_rn(v1, b1);
+    const float e1 = __fmaf_rn(v1, b1, -p1);
+    const float c = __fmaf_rn(v1, b2, __fmaf_rn(v2, b1, e1));
+    const float s = __fsub_rn(a1, p1);
+    const float sb = __fsub_rn(s, a1);
+    const float t = __fadd_rn(__fsub_rn(a1, __fsub_rn(s, sb)), __fsub_rn(-p1, sb));
+    const float d = __fadd_rn(__fsub_rn(a2, c), t);
+    // |s + d|: both halves take the sign of fl(s + d)
+    const uint32_t sg = __float_as_uint(__fadd_rn(s, d)) & 0x80000000u;
+    const float sp = __uint_as_float(__float_as_uint(s) ^ sg);
+    const float dp = __uint_as_float(__float_as_uint(d) ^ sg);
+    const float h = __fadd_rn(H, sp);
+    const float hb = __fsub_rn(h, H);
+    const float e = __fadd_rn(__fsub_rn(H, __fsub_rn(h, hb)), __fsub_rn(sp, hb));
+    H = h;
+    L = __fadd_rn(L, __fadd_rn(dp, e));
+}
+__device__ __forceinline__ void ff_group(const float4 &a1, const float4 &a2, const float4 &b1,
+                                         const float4 &b2, float v1, float v2, float &H, float &L) {
+    ff_row(a1.x, a2.x, b1.x, b2.x, v1, v2, H, L);
+    ff_row(a1.y, a2.y, b1.y, b2.y, v1, v2, H, L);
+    ff_row(a1.z, a2.z, b1.z, b2.z, v1, v2, H, L);
+    ff_row(a1.w, a2.w, b1.w, b2.w, v1, v2, H, L);
+}
+// The sum over the ldn padded rows (zero in both columns past n); a1p, a2p:
+// column k's float pair, b1p, b2p: column jhat's.  Every lane returns it.
+__device__ __forceinline__ double residual_ff(const float *__restrict__ a1p,
+                                              const float *__restrict__ a2p,
+                                              const float *__restrict__ b1p,
+                                              const float *__restrict__ b2p, int64_t ldn,
+                                              float v1, float v2, int lane) {
+    const float4 *A1 = reinterpret_cast<const float4 *>(a1p) + lane;
+    const float4 *A2 = reinterpret_cast<const float4 *>(a2p) + lane;
+    const float4 *B1 = reinterpret_cast<const float4 *>(b1p) + lane;
+    const float4 *B2 = reinterpret_cast<const float4 *>(b2p) + lane;
+    const int ng = (int)(ldn >> 7);  // 128-row groups; a lane takes 4 rows of each
+    const float4 z4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    double D = 0.0;
+    for (int g = 0; g < ng; g += 2) {  // blocks of 8 rows per lane
+        // an odd last group is paired with zero rows, which add exactly 0
+        const bool two = g + 1 < ng;
+        const int o0 = g * 32, o1 = (g + 1) * 32;
+        const float4 xa = __ldg(A1 + o0), xb = two ? __ldg(A1 + o1) : z4;
+        const float4 la = __ldg(A2 + o0), lb = two ? __ldg(A2 + o1) : z4;
+        const float4 ya = __ldg(B1 + o0), yb = two ? __ldg(B1 + o1) : z4;
+        const float4 ma = __ldg(B2 + o0), mb = two ? __ldg(B2 + o1) : z4;
+        float H = 0.0f, L = 0.0f;
+        ff_group(xa, la, ya, ma, v1, v2, H, L);
+        ff_group(xb, lb, yb, mb, v1, v2, H, L);
+        D = __dadd_rn(D, (double)H);
+        D = __dadd_rn(D, (double)L);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) D = __dadd_rn(D, __shfl_xor_sync(0xFFFFFFFFu, D, o));
+    return D;
+}
+// The certificate, divided by 2^-48 and evaluated in float (off the double
+// pipe): accept T_ff when
+//   24 C_k + 56 |v| W + (77 + ldn/4096) T_ff + ldn 2^-98 <= 256 T_ff,
+// with C_k, W rounded up, |v| from its float rounding and both sides given a
+// 2^-20 relative margin for the float roundings of this test.  A huge,
+// infinite or NaN sum is not accepted.
+__device__ __forceinline__ bool ff_certified(double Tff, float Ck, float W, float av,
+                                             int64_t ldn) {
+    const float T = (float)Tff;
+    if (!(T < 0x1p100f)) return false;
+    const float ln = (float)ldn;
+    const float lhs = 24.0f * Ck + 56.0f * av * W + (77.0f + ln * (1.0f / 4096.0f)) * T +
+                      ln * 0x1p-98f;
+    return lhs * (1.0f + 0x1p-20f) <= 256.0f * T * (1.0f - 0x1p-20f);
+}
+
+// Residual of one pair (CS: x_ijhat staged in shared memory); j, k: the
+// pair's columns in a (double input reads their float pairs and totals).
 template <typename T, bool CS>
-__device__ __forceinline__ T pair_residual(const T *xk, const T *colb, int n, T v, int lane) {
-    if constexpr (sizeof(T) == 4)
+__device__ __forceinline__ T pair_residual(const ScanArgs<T> &a, int64_t j, int64_t k,
+                                           const T *xk, const T *colb, int n, T v, int lane) {
+    if constexpr (sizeof(T) == 4) {
+        (void)a, (void)j, (void)k;
         return warp_residual_f4<CS>(xk, colb, n, v, lane);
-    else
+    } else {
+        const ColInfo &ck = a.ci[k], &cj = a.ci[j];
+        const float v1 = (float)v;
+        const float av = fabsf(v1);
+        if (((ck.flags | cj.flags) & COL_WIDE) == 0 &&
+            (av == 0.0f || (av >= 0x1p-60f && av <= 0x1p60f))) {
+            const float v2 = (float)(v - (double)v1);
+            const int64_t ldn = a.ldn, lo = a.m * ldn;  // Xlo follows Xf
+            const double Tff = residual_ff(a.Xf + k * ldn, a.Xf + lo + k * ldn, a.Xf + j * ldn,
+                                           a.Xf + lo + j * ldn, ldn, v1, v2, lane);
+            if (ff_certified(Tff, ck.l1_up, cj.l1_up, av, ldn)) return Tff;
+        }
         return warp_residual_pad<T>(xk, colb, n, v, lane);
+    }
 }
 
 // Writes v and s of (lambda t0+tl, jhat, k), or lists the pair for the exact path.
@@ -863,7 +974,7 @@ __device__ void emit_pair(const ScanArgs<T> &a, int t, int64_t j, int64_t k, int
         return;
     }
     const T v = Tr::value(ts);
-    const T res = pair_residual<T, CS>(xk, colb, n, v, lane);
+    const T res = pair_residual<T, CS>(a, j, k, xk, colb, n, v, lane);
     if (lane == 0) {
         a.v_all[o] = v;
         a.s_all[o] = (double)res + lam * (double)fabs(v);
@@ -995,7 +1106,7 @@ __device__ bool lambda_path(const ScanArgs<T> &a, const LamView &lp, int t0, int
         const K ts = __shfl_sync(FULL, fk, first);
         const T v = Tr::value(ts);
         if (ts != prev) {
-            prev_res = pair_residual<T, CS>(xk, w.colb, n, v, lane);
+            prev_res = pair_residual<T, CS>(a, j, k, xk, w.colb, n, v, lane);
             prev = ts;
         }
         if (lane == 0) {

@@ -9,7 +9,8 @@ namespace l1l {
 // X (n x m, row-major, rows = points) -> Xt (m x ldn, column-major, rows
 // n..ldn-1 zero), and for double input also Xf, the same copy rounded to float
 // (the pair kernel's approximate keys read it, so they need no conversion on
-// the narrow double pipe).  32x32 tiles through shared memory so both the read
+// the narrow double pipe), followed by Xlo = Xf + m ldn, the rounding
+// remainders (the float-float residual reads both).  32x32 tiles through shared memory so both the read
 // and the write are coalesced.  Any NaN/inf sets ST_NONFINITE.
 template <typename T>
 __device__ __forceinline__ void transpose_tile(const T *__restrict__ X, T *__restrict__ Xt,
@@ -39,7 +40,13 @@ __device__ __forceinline__ void transpose_tile(const T *__restrict__ X, T *__res
         if (c < m && r < ldn) {
             const T v = tile[tx][ty + 8 * q];
             Xt[c * ldn + r] = v;
-            if (sizeof(T) == 8) Xf[c * ldn + r] = (float)v;
+            if constexpr (sizeof(T) == 8) {
+                // the float pair of the double residual: hi, then (at m ldn
+                // further) lo = fl(v - hi), where v - hi is exact in double
+                const float hi = (float)v;
+                Xf[c * ldn + r] = hi;
+                Xf[(m + c) * ldn + r] = (float)(v - (double)hi);
+            }
         }
     }
 }
@@ -72,7 +79,9 @@ __device__ __forceinline__ ColInfo colprep_make(long long Q, int sigma, int nv, 
     c.Q32 = (uint32_t)Q32;
     c.shift32 = shift;
     c.n_inexact32 = I32;
-    c.pad_ = 0;
+    // each q_i = floor(|x_i| 2^sigma) is short of |x_i| 2^sigma by less than
+    // one, and only for the n_inexact truncated rows
+    c.l1_up = __double2float_ru((double)(Q + I) * ldexp(1.0, -sigma) * (1.0 + 0x1p-50));
     return c;
 }
 

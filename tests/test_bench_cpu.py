@@ -281,9 +281,12 @@ def test_pair_shape_label_follows_the_register_budgets():
         [2, 2, 2, 0, 0, 1, 1, 1]
 
 
-def test_f64_roofline_arithmetic():
+def test_f64_line_uses_the_pair_kernel_ceilings():
     import bench
-    r = bench.f64_roofline(2000, 3_998_000, 36.0)
-    # 3 flops per pair-row: 2000 * 3,998,000 * 3 / 36 ms = 0.6663 TFLOP/s
-    assert r["achieved"] == pytest.approx(2000 * 3_998_000 * 3 / 0.036 / 1e12)
-    assert r["bound"] == "fp64" and r["frac"] == pytest.approx(r["achieved"] / 1.25)
+    r = bench.roofline(2000, 3_998_000, 26.0, 667, 0, 17_870.0, 40_000.0, None, 1,
+                       dtype="double", timed="whole fit")
+    assert r["kernel"] == "k_pairs<double, 0, 0, 1>" and r["timed"] == "whole fit"
+    # shared memory binds: 16 n bytes per pair at 3,998,000 pairs / 26 ms
+    assert r["bound"] == "smem"
+    assert r["achieved"] == pytest.approx(16 * 2000 * 3_998_000 / 0.026 / 1e9)
+    assert r["traffic"] is None
