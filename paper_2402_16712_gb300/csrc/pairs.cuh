@@ -929,10 +929,13 @@ __device__ __forceinline__ T pair_residual(const ScanArgs<T> &a, int64_t j, int6
         (void)a, (void)j, (void)k;
         return warp_residual_f4<CS>(xk, colb, n, v, lane);
     } else {
+        // one 128-row group: the double sum's 8 double operations per lane
+        // cost less than the float-float sum's fixed part (measured: 100 x 100
+        // double fits 30% slower in float-float)
         const ColInfo &ck = a.ci[k], &cj = a.ci[j];
         const float v1 = (float)v;
         const float av = fabsf(v1);
-        if (((ck.flags | cj.flags) & COL_WIDE) == 0 &&
+        if (a.ldn > ROW_PAD && ((ck.flags | cj.flags) & COL_WIDE) == 0 &&
             (av == 0.0f || (av >= 0x1p-60f && av <= 0x1p60f))) {
             const float v2 = (float)(v - (double)v1);
             const int64_t ldn = a.ldn, lo = a.m * ldn;  // Xlo follows Xf

@@ -97,6 +97,26 @@ def test_double_ratios_equal_in_float(cluster):
     check_fit(X, [0.0, 0.5, 40.0], ref, where=f"coarse ties {cluster}")
 
 
+@pytest.mark.parametrize("outliers", [False, True])
+@pytest.mark.parametrize("noise", [0.0, 1e-13, 1e-9, 1e-3])
+def test_double_near_exact_fits(noise, outliers):
+    """Double columns that are (nearly) multiples of one another.  Without
+    outlier rows the residuals lie far below the columns' size, where the
+    float-float residual's error bound (~2^-48 of the columns) cannot be
+    certified, so the pairs are summed again in double; with outliers most
+    are certified.  Either way every s meets the 1e-12 bar term by term."""
+    rng = np.random.default_rng(int(noise * 1e15) % 1000 + (7 if outliers else 3))
+    n, m = 300, 6
+    base = rng.standard_normal(n)
+    scale = rng.standard_normal(m) * (1 + 2.0 ** -30)
+    X = base[:, None] * scale[None, :] + noise * rng.standard_normal((n, m))
+    if outliers:
+        X[rng.choice(n, 15, replace=False)] += rng.standard_normal((15, m)) * 5
+    where = f"near-exact {noise} outliers={outliers}"
+    _, _, ref = check_scan(X, [0.0, 0.1], where=where)
+    check_fit(X, [0.0, 0.1], ref, where=where)
+
+
 @pytest.mark.parametrize("dtype", DT)
 def test_lambda_batch(dtype):
     X, lams, _ = datagen.lambda_path(np.dtype(dtype).name, n=300, m=24, n_lambda=40)
