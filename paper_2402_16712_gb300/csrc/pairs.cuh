@@ -1204,6 +1204,10 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     // per-lambda thresholds of the exact test depend on (jhat, lambda) only
     for (int tl = threadIdx.x; tl < min(nlc, NDEC); tl += blockDim.x)
         decide_init<T>(s_dec[tl], cinfo, lp.lam[tl]);
+#if L1L_DYNAMIC_K
+    __shared__ int s_knext;  // next k of this unit (offset from k0)
+    if (threadIdx.x == 0) s_knext = 0;
+#endif
     __syncthreads();
     WarpCtx<T> wc;
     wc.colb = colb;
@@ -1222,7 +1226,19 @@ __device__ void pairs_unit(const ScanArgs<T> &a, const LamView &lp, int t0, int 
     wc.cinfo = cinfo;
 
     const bool jwide = (cinfo.flags & COL_WIDE) != 0;
+#if L1L_DYNAMIC_K
+    // a warp takes the next k when it is done with its pair: pairs cost
+    // different times (bracket misses, overflows), and a fixed share per warp
+    // leaves the CTA waiting for its slowest warp
+    (void)nw;
+    for (;;) {
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(&s_knext, 1);
+        const int64_t k = k0 + __shfl_sync(0xFFFFFFFFu, idx, 0);
+        if (k >= k1) break;
+#else
     for (int64_t k = k0 + warp; k < k1; k += nw) {
+#endif
         if (k == j) {  // v_jhat = 1: zero residual, penalty lambda * 1
             for (int tl = lane; tl < nlc; tl += 32) {
                 int64_t o = L1L_CHK(((int64_t)(t0 + tl) * m + j) * m + k,

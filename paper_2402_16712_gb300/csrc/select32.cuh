@@ -39,6 +39,11 @@
 #ifndef L1L_BALANCE
 #define L1L_BALANCE 0
 #endif
+// Warps of a CTA take their pairs from a shared counter (pairs_unit); 0: a
+// fixed share per warp.
+#ifndef L1L_DYNAMIC_K
+#define L1L_DYNAMIC_K 1
+#endif
 #define L1L_PRAGMA(x) _Pragma(#x)
 #define L1L_UNROLL(n) L1L_PRAGMA(unroll n)
 
