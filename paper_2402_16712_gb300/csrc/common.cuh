@@ -336,32 +336,3 @@ struct LambdaPack {
 };
 
 }  // namespace l1l
-
-namespace l1l {
-
-// ---------------------------------------------------------------------------
-// Per-pair residual of Algorithm 1's objective line, one warp:
-//   sum_i |x_ik - v x_ijhat|   (all rows; rows with x_ijhat = 0 give |x_ik|)
-// computed as |fma(-v, x_ijhat, x_ik)| (one rounding per term) and summed in
-// the input precision with two accumulators per lane, then across the warp.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T warp_residual(const T *__restrict__ xk, const T *xj, int n, T v,
-                                           int lane) {
-    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
-    int i = lane;
-    for (; i + 96 < n; i += 128) {
-        const T a0 = xk[i], a1 = xk[i + 32], a2 = xk[i + 64], a3 = xk[i + 96];
-        acc0 += fabs(fma(-v, xj[i], a0));
-        acc1 += fabs(fma(-v, xj[i + 32], a1));
-        acc2 += fabs(fma(-v, xj[i + 64], a2));
-        acc3 += fabs(fma(-v, xj[i + 96], a3));
-    }
-    for (; i < n; i += 32) acc0 += fabs(fma(-v, xj[i], xk[i]));
-    T s = (acc0 + acc1) + (acc2 + acc3);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-    return s;
-}
-
-}  // namespace l1l

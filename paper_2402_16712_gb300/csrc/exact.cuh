@@ -7,6 +7,7 @@
 #pragma once
 #include "checks.cuh"
 #include "common.cuh"
+#include "pairs.cuh"
 
 namespace l1l {
 
@@ -136,7 +137,10 @@ __device__ void exact_entry(const ScanArgs<T> &a, const SlowEntry &en, double la
         ts = lo;
     }
     const T v = Tr::value(ts);
-    const T res = warp_residual<T>(xk, xj, n, v, lane);
+    // the pair kernel's residual routine (x_ijhat read from the column copy):
+    // the same sum in the same order, so s does not depend on which path a
+    // pair took
+    const T res = pair_residual<T, false>(a, en.j, en.k, xk, xj, n, v, lane);
     if (lane == 0) {
         const int64_t o =
             L1L_CHK(((int64_t)en.t * m + en.j) * m + en.k, (int64_t)a.n_lambda * m * m);
