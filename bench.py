@@ -1047,6 +1047,25 @@ def run_profile_case(args):
     return 0 if rc == l1line.OK else 1
 
 
+def run_profile_batch(args):
+    """A plain run of the 256-instance uneven batch (no timing, no graph), for
+    a launch list: one persistent pair launch per size class."""
+    import torch
+
+    from paper_2402_16712_gb300 import datagen, l1line
+    import __graft_entry__
+    __graft_entry__.build()
+    batch = datagen.uneven_batch(256)
+    Xs = [torch.from_numpy(Xb).cuda() for Xb, _ in batch]
+    bat = l1line.Batched(Xs, [lb for _, lb in batch])
+    for _ in range(args.fits):
+        bat.run()
+    rc = bat.status()
+    print(f"profile batch: 256 instances, launches per call {l1line.last_launch_count()}, "
+          f"status={l1line.status_string(rc)}")
+    return 0 if rc == l1line.OK else 1
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1060,6 +1079,8 @@ def main():
     ap.add_argument("--sharded", action="store_true",
                     help="headline = one 2000 x 2000 fit split over the ranks by jhat (strong "
                          "scaling, NCCL argmin), checked bit for bit against the one-GPU fit")
+    ap.add_argument("--profile-batch", action="store_true",
+                    help="run --fits plain calls of the 256-instance uneven batch (for ncu)")
     ap.add_argument("--profile-case", action="store_true",
                     help="run --fits plain fits of an n x m instance (for ncu), no timing")
     ap.add_argument("--n", type=int, default=N_ROWS)
@@ -1071,6 +1092,8 @@ def main():
     args = ap.parse_args()
     if args.profile_case:
         return run_profile_case(args)
+    if args.profile_batch:
+        return run_profile_batch(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
