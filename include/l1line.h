@@ -497,6 +497,14 @@ typedef struct l1line_tuning {
 } l1line_tuning;
 int l1line_set_tuning(const l1line_tuning *t);
 int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out);
+/* The same plan for a GPU of `sms` streaming multiprocessors, computed on the
+ * host without touching a device (the planner is host code; l1line_plan
+ * passes the current device's count).  For tests and for planning ahead of a
+ * launch.  No passage of the paper: a launch heuristic.  Returns L1L_OK,
+ * L1L_ERR_ARG (NULL out, n, m, nj or sms < 1, unknown dtype) or
+ * L1L_ERR_UNSUPPORTED (n beyond the pair kernel's shared memory; such fits
+ * take the global-memory path). */
+int l1line_plan_for(int dtype, int64_t n, int64_t m, int64_t nj, int sms, l1line_tuning *out);
 
 /* Measurement hook: when both are non-NULL (cudaEvent_t), later scan and fit
  * calls from this thread record `start` on their stream just before the pair

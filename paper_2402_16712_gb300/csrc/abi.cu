@@ -986,6 +986,12 @@ int l1line_plan(int dtype, int64_t n, int64_t m, int64_t nj, l1line_tuning *out)
     if (dtype != L1L_DTYPE_F32 && dtype != L1L_DTYPE_F64) return L1L_ERR_ARG;
     const int sms = num_sms();
     if (sms <= 0) return L1L_ERR_CUDA;
+    return l1line_plan_for(dtype, n, m, nj, sms, out);
+}
+
+int l1line_plan_for(int dtype, int64_t n, int64_t m, int64_t nj, int sms, l1line_tuning *out) {
+    if (!out || n < 1 || m < 1 || nj < 1 || sms < 1) return L1L_ERR_ARG;
+    if (dtype != L1L_DTYPE_F32 && dtype != L1L_DTYPE_F64) return L1L_ERR_ARG;
     const PairPlan p = dtype == L1L_DTYPE_F32 ? plan_pairs<float>(n, m, sms, nj, g_tune)
                                               : plan_pairs<double>(n, m, sms, nj, g_tune);
     if (p.warps == 0) return L1L_ERR_UNSUPPORTED;

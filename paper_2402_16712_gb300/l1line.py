@@ -81,6 +81,7 @@ SIGNATURES = {
                                    _P]),
     "l1line_set_tuning": (_I, [_P]),
     "l1line_plan": (_I, [_I, _I64, _I64, _I64, _P]),
+    "l1line_plan_for": (_I, [_I, _I64, _I64, _I64, _I, _P]),
 }
 MLP_FEATURES = 4     # L1L_MLP_FEATURES
 MLP_PARAMS = 17281   # L1L_MLP_PARAMS
@@ -502,6 +503,14 @@ def plan(dtype, n: int, m: int, nj: Optional[int] = None) -> dict:
     t = Tuning()
     _check(load().l1line_plan(_dt(dtype), n, m, m if nj is None else nj, ctypes.byref(t)),
            "l1line_plan")
+    return t.as_dict()
+
+
+def plan_for(dtype, n: int, m: int, sms: int, nj: Optional[int] = None) -> dict:
+    """The plan for a GPU of `sms` SMs, computed on the host (no device)."""
+    t = Tuning()
+    _check(load().l1line_plan_for(_dt(dtype), n, m, m if nj is None else nj, sms,
+                                  ctypes.byref(t)), "l1line_plan_for")
     return t.as_dict()
 
 
