@@ -140,3 +140,37 @@ def test_certification_rejects_exact_fits_and_keeps_noisy_ones():
     a = rng.standard_normal(256)
     Tff, ldn = residual_ff(a, b, v)
     assert bound(a, b, v, Tff, ldn) <= 2.0 ** -40 * Tff
+
+
+def random_cases(count=40, seed=16712):
+    """Random columns: n from 1 to 300, magnitudes over +-50 binades per row,
+    v from the data's own ratios (a near fit) or random, zero rows, sign mixes."""
+    rng = np.random.default_rng(seed)
+    for c in range(count):
+        n = int(rng.integers(1, 301))
+        ea = rng.integers(-50, 51, n) if c % 3 == 0 else np.zeros(n, int)
+        eb = rng.integers(-50, 51, n) if c % 4 == 0 else np.zeros(n, int)
+        b = rng.standard_normal(n) * np.exp2(eb)
+        if c % 2 == 0:  # a near fit: a ~ v b plus noise of random size
+            v = float(rng.standard_normal()) * (1 + 2.0 ** -int(rng.integers(20, 50)))
+            a = v * b + rng.standard_normal(n) * 10.0 ** float(rng.uniform(-14, 0)) * np.exp2(ea)
+        else:
+            a = rng.standard_normal(n) * np.exp2(ea)
+            v = float(np.median(a / np.where(b == 0, 1, b)))
+        a[rng.random(n) < 0.05] = 0.0
+        b[rng.random(n) < 0.05] = 0.0
+        yield f"random {c}", a, b, v
+
+
+def test_ff_residual_bound_on_random_columns():
+    accepted = 0
+    for name, a, b, v in random_cases():
+        Tff, ldn = residual_ff(a, b, v)
+        T = exact_T(a, b, v)
+        err = abs(Fraction(Tff) - T)
+        E = bound(a, b, v, Tff, ldn)
+        assert err <= Fraction(E), (name, float(err), E)
+        if E <= 2.0 ** -40 * Tff:
+            accepted += 1
+            assert err <= Fraction(9.1e-13) * T, (name, float(err / T))
+    assert 5 <= accepted < 40  # both outcomes of the certificate occur
