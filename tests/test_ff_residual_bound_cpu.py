@@ -174,3 +174,46 @@ def test_ff_residual_bound_on_random_columns():
             accepted += 1
             assert err <= Fraction(9.1e-13) * T, (name, float(err / T))
     assert 5 <= accepted < 40  # both outcomes of the certificate occur
+
+
+def certified_in_float(Tff, Ck_up, W_up, v, ldn):
+    """The kernel's certificate as it evaluates it: float operations, the
+    column totals rounded up, |v| from its float rounding, 2^-20 margins."""
+    T = F32(Tff)
+    if not T < F32(2.0 ** 100):
+        return False
+    ln = F32(ldn)
+    av = abs(F32(v))
+    lhs = F32(F32(F32(F32(24.0) * Ck_up) + F32(F32(F32(56.0) * av) * W_up))
+              + F32(F32(F32(77.0) + F32(ln * F32(1.0 / 4096.0))) * T))
+    lhs = F32(lhs + F32(ln * F32(2.0 ** -98)))
+    return bool(F32(lhs * F32(1.0 + 2.0 ** -20)) <= F32(F32(F32(256.0) * T) * F32(1.0 - 2.0 ** -20)))
+
+
+def round_up32(x: float) -> np.float32:
+    f = F32(x)
+    return f if float(f) >= x else np.nextafter(f, F32(np.inf))
+
+
+def test_float_certificate_implies_the_exact_inequality():
+    """Whenever the float evaluation accepts, the inequality holds in exact
+    arithmetic on the true totals, |v| and T_ff (the margins cover the float
+    roundings of the test itself); and it accepts the plainly certifiable."""
+    rng = np.random.default_rng(3)
+    hits = 0
+    for _ in range(20000):
+        ldn = int(rng.integers(1, 200)) * 128
+        T = float(np.exp2(rng.uniform(-60, 60)))
+        Ck = T * float(np.exp2(rng.uniform(-8, 4)))
+        W = float(np.exp2(rng.uniform(-60, 60)))
+        v = float(rng.choice([-1, 1]) * np.exp2(rng.uniform(-59, 59)))
+        ok = certified_in_float(T, round_up32(Ck), round_up32(W), v, ldn)
+        exact = (24 * Fraction(Ck) + 56 * abs(Fraction(v)) * Fraction(W)
+                 + (77 + Fraction(ldn, 4096)) * Fraction(T) + ldn * Fraction(2) ** -98
+                 <= 256 * Fraction(T))
+        if ok:
+            hits += 1
+            assert exact, (T, Ck, W, v, ldn)
+    assert hits > 1000
+    assert certified_in_float(100.0, round_up32(100.0), round_up32(50.0), 0.01, 2048)
+    assert not certified_in_float(0.0, round_up32(100.0), round_up32(50.0), 0.01, 2048)
